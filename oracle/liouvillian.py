@@ -1,0 +1,163 @@
+"""The Liouvillian in the standard batch representation (Sec. 2.4), FP64, written out.
+
+A batch vector x = {x_{vk}} holds one lattice-periodic orbital per occupied band v and
+k-point k, expanded on the sphere of k+Q; here it is a list over k of (nbnd, npw_kq[k])
+complex arrays.  Scalar product of batches (the one the Lanczos recursions use):
+    (a, b) = (1/N_k) sum_k sum_v sum_G conj(a_{vk}(G)) b_{vk}(G).
+
+Operators (Eqs. 18-22, Hartree units):
+    D x = { P_c^{k+Q} (H_{k+Q} - eps_{vk}) x_{vk} }                      (Eq. 19)
+    K x = { P_c^{k+Q} v'_HXC[n'](r) u_{vk}(r) }                          (Eq. 20)
+    n'(r) = 4 sum_{vk} w_k u*_{vk}(r) x_{vk}(r),  w_k = 1/N_k            (Eq. 21)
+    v'_H(G) = 4 pi n'(G) / |Q+G|^2  on every grid frequency               (Eq. 10)
+    v'_XC(r) = f_xc(n0(r)) n'(r)  (ALDA; RPA drops it; IPA drops K)      (Sec. 3.2)
+    y = { P_c^{k+Q} u_{vk} }  (perturbation e^{iQ.r} with Q kept unfolded)  (Eq. 22)
+    P_c^{k} = 1 - sum_v |u_{vk}><u_{vk}|                                  (Eq. 14)
+    L (q, p) = (D p, (D + K) q)                                           (Eq. 18)
+
+Readings: P_c is applied to the whole output of D and K (projecting H x as well keeps
+every Lanczos vector in the conduction manifold); H_{k+Q} = kinetic + V_KS(r) + KB
+projectors; the Hartree kernel runs over every frequency of the FFT box.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import basis, xc
+
+
+class System:
+    """Everything the operators need, derived from a ground-state bundle."""
+
+    def __init__(self, bundle, approx: str | None = None):
+        spec = bundle.spec
+        self.spec = spec
+        self.n = spec.nfft
+        self.omega = spec.omega
+        self.nks = bundle.nks
+        self.nbnd = spec.nbnd
+        self.approx = approx or spec.approx
+        assert self.approx in ("ipa", "rpa", "tddft")
+        self.q = np.asarray(spec.q_cart, dtype=np.float64)
+        self.bvec = spec.bvec
+        self.kcart = bundle.kcart
+        self.mk = bundle.miller_k
+        self.mkq = bundle.miller_kq
+        self.uk = bundle.u_k
+        self.ukq = bundle.u_kq
+        self.eps = bundle.eps_k
+        self.vloc = bundle.vloc_r
+        self.rho = bundle.rho_r
+        self.beta = bundle.beta_kq
+        self.dij = bundle.dij
+        n = self.n
+        # kinetic energy 1/2 |k+Q+G|^2 on each sphere of k+Q
+        self.kin = []
+        for k in range(self.nks):
+            kg = self.kcart[k] + self.q + self.mkq[k] @ self.bvec
+            self.kin.append(0.5 * np.einsum("ij,ij->i", kg, kg))
+        # Hartree weights 4 pi / |Q+G|^2 over the FFT box (frequencies in fftfreq order)
+        f = np.fft.fftfreq(n, 1.0 / n)
+        m = np.stack(np.meshgrid(f, f, f, indexing="ij"), axis=-1)
+        qg = self.q + m @ self.bvec
+        qg2 = np.einsum("...i,...i->...", qg, qg)
+        if np.min(qg2) <= 0:
+            raise ValueError("Q + G = 0 on the grid: Q must not be a reciprocal lattice vector")
+        self.whart = 4 * np.pi / qg2
+        self.fxc = xc.fxc(self.rho) if self.approx == "tddft" else np.zeros_like(self.rho)
+        # ground-state orbitals u_{vk}(r) (times sqrt(Omega)) on the grid
+        self.ur = [basis.to_grid(self.uk[k], self.mk[k], n) for k in range(self.nks)]
+        self.map_k_kq = [basis.intersection_map(self.mk[k], self.mkq[k]) for k in range(self.nks)]
+
+    # ----- batches -------------------------------------------------------------------
+    def zeros(self):
+        return [np.zeros((self.nbnd, len(m)), dtype=np.complex128) for m in self.mkq]
+
+    def inner(self, a, b) -> complex:
+        return sum(np.vdot(ak, bk) for ak, bk in zip(a, b)) / self.nks
+
+    def project_c(self, x):
+        """P_c^{k+Q} x = x - U (U^H x) with U the occupied states at k+Q (Eq. 14)."""
+        out = []
+        for k, xk in enumerate(x):
+            u = self.ukq[k]
+            out.append(xk - (u.T @ (u.conj() @ xk.T)).T)
+        return out
+
+    def starting_vector(self):
+        """y_{vk} = P_c^{k+Q} u_{vk}: u_{vk}'s coefficient at each Miller of sphere(k+Q), or 0."""
+        y = []
+        for k in range(self.nks):
+            mp = self.map_k_kq[k]
+            yk = np.zeros((self.nbnd, len(mp)), dtype=np.complex128)
+            hit = mp >= 0
+            yk[:, hit] = self.uk[k][:, mp[hit]]
+            y.append(yk)
+        return self.project_c(y)
+
+    # ----- operators -----------------------------------------------------------------
+    def apply_h_minus_eps(self, x):
+        """(H_{k+Q} - eps_{vk}) x_{vk}, unprojected: kinetic, V_KS(r), KB projectors."""
+        n = self.n
+        out = []
+        for k, xk in enumerate(x):
+            mil = self.mkq[k]
+            psi = basis.to_grid(xk, mil, n)
+            t = basis.to_sphere(self.vloc[None] * psi, mil, n)
+            t += (self.kin[k][None, :] - self.eps[k][:, None]) * xk
+            b = self.beta[k]
+            if b.shape[0]:
+                c = b.conj() @ xk.T                        # <beta_p|x_v>   (nproj, nbnd)
+                t += ((b.T * self.dij) @ c).T
+            out.append(t)
+        return out
+
+    def apply_d(self, x):
+        return self.project_c(self.apply_h_minus_eps(x))
+
+    def response_density(self, x):
+        """n'(r) = 4 (1/N_k) sum_{vk} u*_{vk}(r) x_{vk}(r), u = psi/sqrt(Omega)."""
+        n = self.n
+        nr = np.zeros((n, n, n), dtype=np.complex128)
+        for k, xk in enumerate(x):
+            psi = basis.to_grid(xk, self.mkq[k], n)
+            nr += np.sum(self.ur[k].conj() * psi, axis=0)
+        return 4.0 * nr / (self.omega * self.nks)
+
+    def hxc_potential(self, nr):
+        """v'(r) = sum_G 4 pi n'(G)/|Q+G|^2 e^{iG.r} + f_xc(n0(r)) n'(r)."""
+        vh = np.fft.ifftn(self.whart * np.fft.fftn(nr))
+        return vh + self.fxc * nr
+
+    def apply_k(self, x):
+        if self.approx == "ipa":
+            return self.zeros()
+        v = self.hxc_potential(self.response_density(x))
+        out = []
+        for k in range(self.nks):
+            out.append(basis.to_sphere(v[None] * self.ur[k], self.mkq[k], self.n))
+        return self.project_c(out)
+
+    def apply_op(self, x, upper: bool):
+        """The operator the recursions apply to one half of a batch: D + K on the upper
+        (q) component, D on the lower (p) component (Eq. 18)."""
+        d = self.apply_d(x)
+        if not upper or self.approx == "ipa":
+            return d
+        kx = self.apply_k(x)
+        return [a + b for a, b in zip(d, kx)]
+
+    def apply_l(self, up, lo):
+        """L (q, p) = (D p, (D + K) q) on a full batch pair (either half may be None = 0)."""
+        new_up = self.apply_op(lo, upper=False) if lo is not None else None
+        new_lo = self.apply_op(up, upper=True) if up is not None else None
+        return new_up, new_lo
+
+
+def axpy(a, x, y):
+    """a x + y on batches."""
+    return [a * xk + yk for xk, yk in zip(x, y)]
+
+
+def scale(a, x):
+    return [a * xk for xk in x]

@@ -1,0 +1,163 @@
+"""Seeded synthetic systems: cells, k-meshes, momentum transfers and plane-wave spheres.
+
+This module is an input generator shared by the FP64 oracle and the CUDA path.  It
+holds none of the Liouville-Lanczos arithmetic (no response density, no Liouvillian,
+no Lanczos step, no spectrum): it only describes the crystal and enumerates the
+integer Miller indices of the plane-wave basis, i.e. what the ground-state program
+(pw.x in the paper, Sec. 3.1) hands to the linear-response code.
+
+Units are Hartree atomic units (Sec. 2.2); cut-offs are given in Rydberg as in the
+paper's input tables and used as |k+G|^2 <= ecut_Ry (bohr^-2).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+HA_EV = 27.211386245988          # CODATA 2018 Hartree in eV
+A_LAT = 10.26                    # bohr: the lattice parameter of every synthetic cell
+
+
+def fcc_primitive(a: float) -> np.ndarray:
+    """Rows are the primitive vectors of the face-centred cubic lattice (ibrav=2 axes)."""
+    return 0.5 * a * np.array([[-1.0, 0.0, 1.0], [0.0, 1.0, 1.0], [-1.0, 1.0, 0.0]])
+
+
+def reciprocal(lattice: np.ndarray) -> np.ndarray:
+    """Rows b_i with a_i . b_j = 2 pi delta_ij."""
+    return 2.0 * np.pi * np.linalg.inv(lattice).T
+
+
+def kmesh_frac(n: tuple[int, int, int]) -> np.ndarray:
+    """Gamma-centred mesh in fractions of the reciprocal vectors, each in [0, 1), C order."""
+    i, j, k = np.meshgrid(np.arange(n[0]), np.arange(n[1]), np.arange(n[2]), indexing="ij")
+    return np.stack([i.ravel() / n[0], j.ravel() / n[1], k.ravel() / n[2]], axis=1)
+
+
+@dataclass
+class SystemSpec:
+    """One synthetic crystal plus the response calculation run on it."""
+    name: str
+    lattice: np.ndarray            # (3,3) rows a_i, bohr
+    tau: np.ndarray                # (nat,3) Cartesian atomic positions, bohr
+    zval: float                    # ionic charge per atom of the local potential
+    rc: float                      # Gaussian smearing radius of the local potential, bohr
+    ecut_ry: float                 # wavefunction cut-off, Ry
+    nfft: int                      # FFT grid side N (cubic N^3 grid along a_i)
+    kmesh: tuple                   # response k-mesh (Gamma-centred)
+    nbnd: int                      # occupied bands
+    q_cart: np.ndarray             # momentum transfer Q, Cartesian bohr^-1
+    approx: str = "tddft"          # 'ipa' | 'rpa' | 'tddft'
+    kb: bool = False               # extra Kleinman-Bylander s+p channels on every atom
+    kb_b: float = 0.8              # radial width of beta(r) = exp(-r^2/b^2), bohr
+    kb_d_ry: tuple = (2.0, -1.0)   # (D_s, D_p) of the extra channels, Ry
+    s_core_ry: float = 40.0        # repulsive s channel of every atom's pseudopotential, Ry
+    scf_kmesh: tuple | None = None # mesh of the self-consistent density (None: kmesh)
+    steps: int = 300
+    flavour: str = "ph"            # 'ph' pseudo-Hermitian | 'nh' non-Hermitian
+    free_electron: bool = False    # V_ion = 0 and plane-wave occupations (Lindhard pins)
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def omega(self) -> float:
+        return float(abs(np.linalg.det(self.lattice)))
+
+    @property
+    def bvec(self) -> np.ndarray:
+        return reciprocal(self.lattice)
+
+    @property
+    def nks(self) -> int:
+        return int(np.prod(self.kmesh))
+
+    @property
+    def nelec(self) -> float:
+        return 2.0 * self.nbnd
+
+    @property
+    def nproj(self) -> int:
+        """Projectors per cell: s on every atom, plus p_x, p_y, p_z when kb is set."""
+        if len(self.tau) == 0 or (not self.kb and self.s_core_ry == 0.0):
+            return 0
+        return len(self.tau) * (4 if self.kb else 1)
+
+
+def _diamond(a: float) -> tuple[np.ndarray, np.ndarray]:
+    lat = fcc_primitive(a)
+    tau = np.array([[0.0, 0.0, 0.0], [0.25 * a, 0.25 * a, 0.25 * a]])
+    return lat, tau
+
+
+def config_small() -> SystemSpec:
+    """Two-atom diamond-structure cell, 10 Ry, 18^3 grid, 4x4x4 mesh, Q = 0.1 (2pi/a) x,
+    RPA+ALDA kernel, 300 pseudo-Hermitian steps, FP64."""
+    lat, tau = _diamond(A_LAT)
+    q = 0.1 * (2 * np.pi / A_LAT) * np.array([1.0, 0.0, 0.0])
+    return SystemSpec("fcc2_10ry_18", lat, tau, 4.0, 1.0, 10.0, 18, (4, 4, 4), 4, q,
+                      approx="tddft", steps=300, flavour="ph")
+
+
+def config_kb() -> SystemSpec:
+    """Same cell and Q as config_small plus KB s/p projectors, 25 Ry, 32^3 grid,
+    8x8x8 mesh, 1000 steps of either recursion."""
+    lat, tau = _diamond(A_LAT)
+    q = 0.1 * (2 * np.pi / A_LAT) * np.array([1.0, 0.0, 0.0])
+    return SystemSpec("fcc2kb_25ry_32", lat, tau, 4.0, 1.0, 25.0, 32, (8, 8, 8), 4, q,
+                      approx="tddft", kb=True, scf_kmesh=(4, 4, 4), steps=1000, flavour="ph")
+
+
+def config_tiny(kb: bool = False, approx: str = "tddft") -> SystemSpec:
+    """A cell small enough for brute-force Casida diagonalisation: 4 Ry, 12^3, 2x2x2 k."""
+    lat, tau = _diamond(A_LAT)
+    q = 0.1 * (2 * np.pi / A_LAT) * np.array([1.0, 0.0, 0.0])
+    return SystemSpec("fcc2_4ry_12" + ("kb" if kb else ""), lat, tau, 4.0, 1.0, 4.0, 12,
+                      (2, 2, 2), 4, q, approx=approx, kb=kb, steps=60, flavour="ph")
+
+
+def config_local_insulator() -> SystemSpec:
+    """Local-potential-only insulator for the f-sum rule (exact only for local potentials):
+    the tiny cell without projectors, its two deep s-like bands occupied."""
+    s = config_tiny()
+    s.name, s.s_core_ry, s.nbnd = "fcc2_4ry_12_local2", 0.0, 2
+    return s
+
+
+def config_free_electron(nk: int = 6, ecut: float = 3.0, nfft: int = 12,
+                         qfrac: float = 1.0 / 6.0) -> SystemSpec:
+    """Simple-cubic free-electron gas (V_ion = 0); Q = qfrac * b_1 commensurate with the mesh."""
+    a = A_LAT
+    lat = a * np.eye(3)
+    q = qfrac * (2 * np.pi / a) * np.array([1.0, 0.0, 0.0])
+    s = SystemSpec("feg", lat, np.zeros((0, 3)), 0.0, 1.0, ecut, nfft, (nk, nk, nk), 1, q,
+                   approx="rpa", steps=200, flavour="ph", free_electron=True, s_core_ry=0.0)
+    return s
+
+
+CONFIGS = {"small": config_small, "kb": config_kb, "tiny": config_tiny}
+
+
+def sphere(kcart: np.ndarray, bvec: np.ndarray, ecut_ry: float, guard: float = 1e-9) -> np.ndarray:
+    """Miller indices m (int32, shape (npw,3)) with |k + m.B|^2 <= ecut, lexicographic order.
+
+    Raises if a point sits within `guard` (relative) of the cut-off, so that the
+    membership decision cannot depend on rounding order."""
+    kmax = np.sqrt(ecut_ry) + np.linalg.norm(kcart)
+    lat = 2 * np.pi * np.linalg.inv(bvec).T          # rows a_i
+    mmax = [int(np.ceil(kmax * np.linalg.norm(lat[i]) / (2 * np.pi))) + 1 for i in range(3)]
+    r = [np.arange(-mm, mm + 1) for mm in mmax]
+    m1, m2, m3 = np.meshgrid(*r, indexing="ij")
+    m = np.stack([m1.ravel(), m2.ravel(), m3.ravel()], axis=1)
+    kg = kcart[None, :] + m @ bvec
+    g2 = np.einsum("ij,ij->i", kg, kg)
+    near = np.abs(g2 - ecut_ry) <= guard * ecut_ry
+    if np.any(near):
+        raise ValueError(f"plane wave within {guard} of the cut-off at k={kcart}")
+    sel = m[g2 <= ecut_ry]
+    order = np.lexsort((sel[:, 2], sel[:, 1], sel[:, 0]))
+    return np.ascontiguousarray(sel[order].astype(np.int32))
+
+
+def fft_miller(n: int) -> np.ndarray:
+    """Integer frequency of each grid index, numpy fftfreq order: 0..N/2-1, -N/2..-1."""
+    return np.fft.fftfreq(n, 1.0 / n).astype(np.int64)
