@@ -148,7 +148,8 @@ def test_hartree_kernel_and_fxc_tables(tiny):
         assert np.isclose(sys.whart[idx], 4 * np.pi / (qg @ qg), rtol=1e-14)
     assert np.allclose(sys.fxc, xc.fxc(tiny.rho_r), rtol=0, atol=0)
     assert np.all(System(tiny, "rpa").fxc == 0)
-    # the response density of y integrates to 4 (y, y)-weighted zero: int n' dr = 4 sum w <u|y> = 0
+    # Eq. 21 normalisation: int_cell n'[y] dr = 4 (1/N_k) sum <u_vk|y_vk> = 4 (y, y)
+    # because y = P_c u and P_c is a projector
     y = sys.starting_vector()
     nr = sys.response_density(y)
-    assert abs(nr.mean()) * sys.omega < 1e-12
+    assert abs(nr.mean() * sys.omega - 4.0 * sys.inner(y, y)) < 1e-12
