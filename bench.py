@@ -1,0 +1,319 @@
+#!/usr/bin/env python3
+"""Lanczos steps/s of the Liouville-Lanczos hot path on one GB300 (per rank).
+
+Workload (the configuration the metric is quoted on): the two-atom FCC cell with
+Kleinman-Bylander s/p projectors, 25 Ry, 32^3 FFT grid, 8x8x8 k-mesh, 4 bands (2048
+response orbitals), Q = 0.1 (2 pi/a) x, TDDFT (RPA + ALDA) kernel, pseudo-Hermitian
+recursion.  A step is one Lanczos step: the update of the Lanczos vectors and scalars plus
+one application of the Liouvillian (D + K or D) to the whole batch.  `value` is the FP32
+path (FP32 orbitals and FFTs, FP64 Lanczos scalars); the plain FP64 path is timed beside it
+on the same steps, and the spectrum error of the FP32 path against it is reported.
+
+Inputs: the seeded synthetic ground state of that cell (workloads/), built once and cached.
+Device inputs stay resident; the per-step working set (orbital grids, column buffers,
+vectors: ~0.6 GB in FP32) is larger than the 129 MB L2, so no flush is needed.
+
+Usage: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Under torchrun every rank runs an independent chain on its own GPU (replicas; chains of
+different momenta are independent problems) and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Lanczos steps/s (Liouvillian applies) FP32 vs FP64 @1e-3 err; p50/p99 latency"
+WORKLOAD = ("fcc2kb_25ry_32: 2-atom FCC a=10.26 + KB s/p, 25 Ry, 32^3 FFT, 8x8x8 k, 4 bands, "
+            "Q=0.1(2pi/a)x, RPA+ALDA, pseudo-Hermitian")
+SPEC_WINDOW = 100        # coefficients of the reproducible part of the recursion
+FP32_PEAK_PER_SM_CLK = 128 * 2   # FP32 lanes per SM x 2 flops per FMA
+
+
+def _bundle():
+    import workloads as w
+    return w.get_bundle(w.config_kb())
+
+
+def _chain(b, precision, max_steps, stream):
+    from paper_2111_06623_gb300 import ll
+    s = b.spec
+    return ll.Chain(lattice=s.lattice, nfft=s.nfft, kcart=b.kcart, miller_k=b.miller_k, miller_kq=b.miller_kq,
+                    u_k=b.u_k, u_kq=b.u_kq, eps_k=b.eps_k, vloc_r=b.vloc_r, rho_r=b.rho_r, beta_kq=b.beta_kq,
+                    dij=b.dij, q_cart=s.q_cart, approx="tddft", flavour="ph", precision=precision,
+                    max_steps=max_steps, stream=stream)
+
+
+def _bundle_bytes(b) -> int:
+    n = sum(a.nbytes for a in (b.kcart, b.eps_k, b.vloc_r, b.rho_r, b.dij))
+    n += sum(m.nbytes for m in b.miller_k) + sum(m.nbytes for m in b.miller_kq)
+    n += sum(u.nbytes for u in b.u_k) + sum(u.nbytes for u in b.u_kq) + sum(x.nbytes for x in b.beta_kq)
+    return int(n)
+
+
+class Clocks:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    def __init__(self, index: int):
+        self.index, self.rows, self.proc = index, [], None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[1]) for r in self.rows if len(r) > 8 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 8 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows if len(r) > 8 for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def _xy_flops_per_apply(b, with_k: bool) -> float:
+    """Algorithmic FP32 flops of the per-plane kernel for one operator application: for every
+    orbital and plane, (rows + N) inverse and (N + rows) forward line FFTs of 5 N log2 N flops,
+    the V(r) x(r) product (2 flops/point) and, with K, the density product (8 flops/point)."""
+    n = b.spec.nfft
+    line = 5.0 * n * np.log2(n)
+    tot = 0.0
+    for m in b.miller_kq:
+        rows = len(np.unique(m[:, 0]))
+        per_plane = (2 * rows + 2 * n) * line + (2 + (8 if with_k else 0)) * n * n
+        tot += b.spec.nbnd * n * per_plane
+    return tot
+
+
+def _time_chain(b, precision, steps, warmup, stream, profile=False):
+    import torch
+    ch = _chain(b, precision, warmup + steps, stream)
+    ch.lanczos(warmup)
+    torch.cuda.synchronize()
+    if profile:
+        ch.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    coefs = ch.lanczos(steps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    prof = ch.profile_read() if profile else None
+    return ch, coefs, ms, prof
+
+
+def _loss(coefs, b, m):
+    from paper_2111_06623_gb300 import ll
+    w = np.linspace(0.0, 40.0, 4001)
+    beta, gamma, z = (c[:m] for c in coefs)
+    _, ei, _ = ll.spectrum(beta, gamma, z, b.spec.omega, b.spec.q_cart, w, 0.1)
+    return -ei.imag
+
+
+def _oracle_sample(b, nk_sample: int, nsteps: int):
+    """Seconds per pseudo-Hermitian oracle step on the first nk_sample k-points."""
+    import copy
+
+    from oracle import lanczos
+    from oracle.liouvillian import System
+    sub = copy.copy(b)
+    for f in ("miller_k", "miller_kq", "u_k", "u_kq", "beta_kq"):
+        setattr(sub, f, getattr(b, f)[:nk_sample])
+    sub.kfrac, sub.kcart, sub.eps_k, sub.eps_kq = b.kfrac[:nk_sample], b.kcart[:nk_sample], b.eps_k[:nk_sample], \
+        b.eps_kq[:nk_sample]
+    sys_ = System(sub)
+    lanczos.pseudo_hermitian(sys_, 1)
+    t0 = time.perf_counter()
+    lanczos.pseudo_hermitian(sys_, nsteps)
+    return (time.perf_counter() - t0) / nsteps
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    b = _bundle()
+    nk = 4
+    t0 = time.perf_counter()
+    _oracle_sample(b, nk, max(1, args.warmup))
+    per_step = _oracle_sample(b, nk, args.steps)
+    frac = nk / b.nks
+    value = frac / per_step
+    sample = (f"one pseudo-Hermitian oracle step (NumPy FP64) on {nk} of the {b.nks} k-points per step; "
+              f"value scaled to the full workload")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_kpoints": nk},
+            "cpu_baseline": {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": time.perf_counter() - t0}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("at least 3 warm-up steps")
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    from paper_2111_06623_gb300.build import build_library
+    build_library()
+    from paper_2111_06623_gb300 import ll
+
+    b = _bundle()
+    stream = torch.cuda.current_stream().cuda_stream
+    K, W = args.steps, args.warmup
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    # FP32 path: the headline, with per-kernel-class device time
+    barrier()
+    with Clocks(local) as clk:
+        ch32, c32, ms32, prof = _time_chain(b, "fp32", K, W, stream, profile=True)
+    barrier()
+    clocks = clk.summary()
+    # FP64 path on the same number of steps
+    ch64, c64, ms64, _ = _time_chain(b, "fp64", K, W, stream)
+    m = min(SPEC_WINDOW, len(c32[0]), len(c64[0]))
+    l32, l64 = _loss(c32, b, m), _loss(c64, b, m)
+    spec_err = float(np.max(np.abs(l32 - l64)) / np.max(np.abs(l64)))
+    lf32, lf64 = _loss(c32, b, len(c32[0])), _loss(c64, b, len(c64[0]))
+    spec_err_full = float(np.max(np.abs(lf32 - lf64)) / np.max(np.abs(lf64)))
+    # per-step latency (single-step calls, host sync included)
+    lat = []
+    for _ in range(50):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if ch32.steps >= ch32.max_steps:
+            break
+        e0.record()
+        ch32.lanczos(1)
+        e1.record()
+        torch.cuda.synchronize()
+        lat.append(e0.elapsed_time(e1))
+    ch32.close()
+    ch64.close()
+
+    # end to end through the C ABI with host buffers: create (H2D of the ground state and
+    # set-up), K steps, spectrum, coefficients and spectrum back to the host
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    che = _chain(b, "fp32", K, stream)
+    ce = che.lanczos(K)
+    wgrid = np.linspace(0.0, 40.0, 4001)
+    chi, ei, eps = che.spectrum(wgrid, 0.1)
+    che.close()
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    e2e = {"value": K / t_e2e, "unit": "steps/s", "h2d_bytes_per_step": _bundle_bytes(b) / K,
+           "d2h_bytes_per_step": (sum(c.nbytes for c in ce) + chi.nbytes + ei.nbytes + eps.nbytes) / K}
+
+    # max over ranks of the timed region
+    tmax = ms32
+    if world > 1:
+        t = torch.tensor([ms32], dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tmax = float(t.item())
+    value = world * K / (tmax / 1e3)
+
+    ms_cls, launches, total = prof
+    dom = max(ms_cls, key=ms_cls.get)
+    n_dom = max(1, launches[dom])
+    # one pass-1 launch per operator application; half of the K applications carry K
+    flops = 0.5 * (_xy_flops_per_apply(b, True) + _xy_flops_per_apply(b, False))
+    sm_mhz = clocks.get("sm_max_mhz") or 2070.0
+    peak = 152 * FP32_PEAK_PER_SM_CLK * sm_mhz * 1e6 / 1e12
+    roofline = None
+    if dom == "xy1":
+        ach = flops / (ms_cls[dom] / n_dom / 1e3) / 1e12
+        roofline = {"bound": "alu", "kernel": "k_xy (pass 1: per-plane 2D FFTs, V x, density)", "achieved": ach,
+                    "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                    "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flops x max SM clock (derived)"}
+    else:
+        roofline = {"bound": "alu", "kernel": dom, "achieved": None, "peak": peak, "unit": "TFLOP/s",
+                    "frac": None, "traffic": None}
+
+    cpu = None
+    if rank == 0:
+        nk = 8
+        t1 = _oracle_sample(b, nk, 1)
+        n = max(1, int(args.cpu_seconds / max(t1, 1e-3)))
+        per = _oracle_sample(b, nk, n)
+        cpu = {"value": (nk / b.nks) / per, "unit": "steps/s", "cores": 1, "kind": "oracle",
+               "sample": f"{n} pseudo-Hermitian oracle steps (NumPy FP64, single-threaded FFTs) on {nk} of "
+                         f"{b.nks} k-points, scaled to the full workload"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": tmax / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic (seeded LDA ground state, workloads/)",
+            "config": {"workload": WORKLOAD, "orbitals": int(b.nks * b.spec.nbnd), "npw_avg": float(np.mean(b.npw_kq)),
+                       "l2": "per-step working set ~0.6 GB > 129 MB L2 (no flush)", "parallelism": "replicas"},
+            "fp64": {"value": world * K / (ms64 / 1e3), "ms_per_step": ms64 / K, "dtype": "f64"},
+            "speedup_fp32_vs_fp64": ms64 / ms32,
+            "spectrum_err_fp32_vs_fp64": spec_err, "spectrum_window_steps": m,
+            "spectrum_err_fp32_vs_fp64_all_steps": spec_err_full,
+            "step_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))} if lat else None,
+            "kernel_ms": ms_cls, "kernel_launches": launches,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(total), "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,152 @@
+/* C ABI of the GB300 Liouville-Lanczos library (libll.so).
+ *
+ * The library applies the Liouvillian of time-dependent density-functional perturbation
+ * theory, in the standard batch representation, to a batch of plane-wave response orbitals
+ * {x_{v,k+Q}} and runs the Lanczos recursions whose coefficients give the charge-density
+ * susceptibility chi(Q, omega) and the inverse dielectric function at finite momentum
+ * transfer Q (Timrov et al., turboEELS, Sec. 2; Eqs. 10, 23-33).
+ *
+ * Conventions
+ *   - Every function returns an ll_status; nothing throws across the ABI.  After a failure
+ *     ll_last_error() returns a message for the calling thread.
+ *   - Hartree atomic units throughout, except the frequency grid and broadening of the
+ *     spectrum calls (eV, as in the post-processing input of Sec. 3.3).
+ *   - Complex numbers are interleaved (re, im) doubles; arrays are C-contiguous.
+ *   - Host pointers unless a name ends in _dev.  Input arrays are copied by ll_create; the
+ *     caller may free them afterwards.  Output arrays are caller-owned.
+ *   - Streams are cudaStream_t passed as void* (NULL = the legacy default stream).
+ *   - One handle drives one chain on one device; calls on one handle must not overlap.
+ */
+#ifndef LL_H
+#define LL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LL_OK = 0,
+  LL_EINVAL = 1,        /* an argument or an input array is malformed                    */
+  LL_ENOMEM = 2,        /* device allocation failed                                      */
+  LL_EBREAKDOWN = 3,    /* Lanczos breakdown (|s| or beta^2 below tolerance)             */
+  LL_ENOTPD = 4,        /* pseudo-Hermitian metric not positive (D or D+K indefinite)     */
+  LL_ETIMEOUT = 5,      /* a bounded device wait gave up                                 */
+  LL_ECUDA = 6,         /* a CUDA runtime call failed                                    */
+  LL_PENDING = 7,
+  LL_ENOTFOUND = 8,
+  LL_EUNSUPPORTED = 9   /* valid input outside what this build implements                */
+} ll_status;
+
+enum { LL_APPROX_IPA = 0, LL_APPROX_RPA = 1, LL_APPROX_TDDFT = 2 };   /* Sec. 3.2 */
+enum { LL_FLAVOUR_PH = 0, LL_FLAVOUR_NH = 1 };                          /* Sec. 2.5 */
+enum { LL_PREC_FP64 = 0, LL_PREC_FP32 = 1 };
+
+typedef struct ll_handle ll_handle;
+
+/* Ground state and response set-up of one chain (the data pw.x hands to turbo_eels.x,
+ * Sec. 3.1, plus the turbo_eels.x input of Sec. 3.2). */
+typedef struct {
+  double lattice[3][3];     /* rows a_i, bohr                                              */
+  int nfft;                 /* FFT grid N (N^3 points along a_i); 12,16,18,24,32,36,48      */
+  int nks;                  /* k-points, weights 1/nks                                     */
+  int nbnd;                 /* occupied bands per k (<= 32)                                */
+  int nproj;                /* KB projectors per k (0 allowed)                             */
+  double q_cart[3];         /* momentum transfer Q (bohr^-1); Q + G != 0 on the grid       */
+  const double* kcart;      /* [nks][3]                                                    */
+  const int* npw_k;         /* [nks] sphere sizes of k                                     */
+  const int* miller_k;      /* [sum npw_k][3], each sphere lexicographic in (m1,m2,m3)     */
+  const int* npw_kq;        /* [nks] sphere sizes of k+Q                                   */
+  const int* miller_kq;     /* [sum npw_kq][3]                                             */
+  const double* u_k;        /* complex, per k [nbnd][npw_k[k]] concatenated: u_{vk}(G)    */
+  const double* u_kq;       /* complex, per k [nbnd][npw_kq[k]]: occupied states at k+Q   */
+  const double* eps_k;      /* [nks][nbnd] eigenvalues eps_{vk} (Ha)                       */
+  const double* vloc_r;     /* [N][N][N] (index j1,j2,j3) total Kohn-Sham local potential  */
+  const double* rho_r;      /* [N][N][N] ground-state density (bohr^-3)                    */
+  const double* beta_kq;    /* complex, per k [nproj][npw_kq[k]]: beta_p(k+Q+G)            */
+  const double* dij;        /* [nproj] KB strengths D_p (Ha)                               */
+  int approx;               /* LL_APPROX_*                                                 */
+  int flavour;              /* LL_FLAVOUR_*                                                */
+  int precision;            /* LL_PREC_*: FP64 everywhere, or FP32 orbitals/FFTs with FP64
+                               Lanczos scalars                                             */
+  int max_steps;            /* capacity of the device coefficient arrays                   */
+} ll_system_desc;
+
+/* Builds the device state of one chain (Sec. 2.4-2.5): index maps (sphere(k+Q) -> sphere(k)
+ * intersection, column/plane tables), u_{vk}(r) grids, f_xc(n0), the Hartree kernel
+ * 4 pi/|Q+G|^2, the starting vector y = P_c u (Eq. 28) and, for the pseudo-Hermitian
+ * flavour, its first operator application D y.  Work is queued on `stream`; the call
+ * returns once the set-up has finished.  LL_EINVAL on malformed input (unsorted spheres,
+ * Miller indices that do not fit the grid, Q on the reciprocal lattice ...).
+ * *out receives a handle to release with ll_destroy. */
+int ll_create(const ll_system_desc* desc, void* stream, ll_handle** out);
+int ll_destroy(ll_handle* h);
+
+/* Runs n_steps more Lanczos steps (Sec. 2.5), continuing from the resident state
+ * (restart semantics of Sec. 3.2).  On return the arrays hold every coefficient so far
+ * (`*steps_done` of them; capacity max_steps):
+ *   beta[i]  = b_1 (i = 0) or T_{i+1,i};   gamma[i] (complex) = b_1 or T_{i,i+1};
+ *   z[i] (complex) = z_{i+1} = ((y, 0), v_{i+1}) (Eq. 31).
+ * Any of beta, gamma, z may be NULL.  LL_ENOTPD / LL_EBREAKDOWN stop the chain; steps_done
+ * then counts the steps whose coefficients are valid. */
+int ll_lanczos(ll_handle* h, int n_steps, double* beta, double* gamma, double* z, int* steps_done);
+
+/* Spectrum of a handle's own coefficients on the device (Eqs. 32-33, 5):
+ * chi(Q, w) = (4/Omega) b_1 sum_j z_j x_j with ((w + i eta) - T_M) x = e_1, using the first
+ * m coefficients (m <= steps done; m <= 0: all).  eps_inv = 1 + 4 pi/|Q|^2 chi, eps = 1/eps_inv.
+ * omega_ev [n_omega] and eta_ev in eV; chi, eps_inv, eps complex [n_omega] (host). */
+int ll_lanczos_spectrum(ll_handle* h, int m, const double* omega_ev, int n_omega, double eta_ev,
+                        double* chi, double* eps_inv, double* eps);
+
+/* The same from caller-held coefficients (host arrays beta[m], gamma[m] complex, z[m]
+ * complex), for a cell of volume omega_cell (bohr^3) and momentum q_cart (bohr^-1). */
+int ll_spectrum(const double* beta, const double* gamma, const double* z, int m, double omega_cell,
+                const double* q_cart, const double* omega_ev, int n_omega, double eta_ev, double* chi,
+                double* eps_inv, double* eps, void* stream);
+
+/* One application of the SBR operator to a batch (Eqs. 24-28): out = (D + K) x when
+ * upper != 0 (K omitted for IPA), out = D x otherwise, with D = P_c (H_{k+Q} - eps_{vk})
+ * and the P_c of Eq. 16 on the output.  x and out are complex batches laid out per k as
+ * [nbnd][npw_kq[k]] concatenated over k (host). */
+int ll_apply(ll_handle* h, int upper, const double* x, double* out);
+
+/* Bit-exact index map: for each k, each Miller of sphere(k+Q) -> its position in sphere(k)
+ * or -1; int32 [sum npw_kq] concatenated (host). */
+int ll_get_map(ll_handle* h, int* map_out);
+
+/* The starting vector y = P_c u (Eq. 28) as a complex batch laid out like ll_apply's. */
+int ll_get_start(ll_handle* h, double* y_out);
+
+/* Kernel classes of the per-class device-time profile. */
+enum {
+  LL_PROF_ZINV = 0,     /* sphere -> columns, inverse FFT along axis 3                    */
+  LL_PROF_XY1 = 1,      /* per-plane 2D FFTs, V(r) x(r), response density                 */
+  LL_PROF_HXC = 2,      /* Hartree + XC response potential of the density                 */
+  LL_PROF_XY2 = 3,      /* per-plane forward 2D FFTs of v'(r) u(r)                         */
+  LL_PROF_ZFWD = 4,     /* forward FFT along axis 3, columns -> sphere                    */
+  LL_PROF_PROJ = 5,     /* kinetic - eps, KB projectors, P_c, norm partials               */
+  LL_PROF_UPDATE = 6,   /* Lanczos scalars and vector updates                             */
+  LL_NPROF = 7
+};
+
+/* Starts (enable != 0: counters cleared) or stops recording CUDA events around each
+ * kernel class on the handle's stream.  Launch counting is always on. */
+int ll_profile(ll_handle* h, int enable);
+
+/* Device milliseconds per class summed over the recorded spans (ms[LL_NPROF]), kernel
+ * launches per class (launches[LL_NPROF]) and in total since the last ll_profile(h, 1).
+ * Synchronises the stream.  Any output may be NULL. */
+int ll_profile_read(ll_handle* h, double* ms, long long* launches, long long* total);
+
+/* Device bytes a handle for this descriptor will hold (input arrays are not read). */
+int ll_footprint(const ll_system_desc* desc, size_t* bytes);
+
+const char* ll_last_error(void);
+const char* ll_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -10,9 +10,9 @@ it.  The product path never calls it.
 
 Modules
   basis       G-sphere <-> FFT-grid maps, the k -> k+Q intersection map    (Sec. 2.3)
-  xc          Slater + Perdew-Zunger 1981 LDA: e_xc, v_xc, f_xc           (Sec. 5, Eq. 9)
-  liouvillian D, K, P_c, response density, Hartree+XC response            (Eqs. 7-9, 18-22)
+  xc          Slater + Perdew-Zunger 1981 LDA: e_xc, v_xc, f_xc           (Sec. 5; Eq. 12)
+  liouvillian D, K, P_c, response density, Hartree+XC response            (Eqs. 12-13, 16, 24-28)
   lanczos     pseudo-Hermitian and non-Hermitian recursions               (Sec. 2.5)
-  spectrum    (omega - T) x = e_1, chi = (z, x), eps^-1, eps              (Eqs. 3, 24-27)
+  spectrum    (omega - T) x = e_1, chi = (z, x), eps^-1, eps              (Eqs. 5, 30-33)
   casida      brute-force diagonalisation of the full Liouvillian         (pin)
 """

@@ -6,9 +6,9 @@ sum_p beta_p(G) D_p beta_p(G')^*, with V(G - G') the cyclic convolution of the g
 potential.  In the orthonormal transition basis I = (v, c, k):
     D_IJ = (eps_{c,k+Q} - eps_{vk}) delta_IJ
     K_IJ = 4 / (Omega N_k N^3) sum_r conj(rho_I(r)) (kappa rho_J)(r),
-           rho_I(r) = conj(psi_{vk}(r)) psi_{c,k+Q}(r),  kappa = Hartree + f_xc (Eqs. 9-10)
+           rho_I(r) = conj(psi_{vk}(r)) psi_{c,k+Q}(r),  kappa = Hartree + f_xc (Eqs. 12-13)
     y_I  = <c_{k+Q} | u_{vk}> / sqrt(N_k)
-and the resolvent element of Eq. 6 in the SBR is
+and the resolvent element of Eq. 10 in the SBR is
     ((y, 0), (w - L)^-1 (0, y)) = y^H D^1/2 (w^2 - M)^-1 D^1/2 y,  M = D^1/2 (D + K) D^1/2
 (from w q = D p, w p = (D + K) q + y).  Diagonalising M gives the exact finite-basis
 spectrum the Lanczos recursions converge to.

@@ -1,15 +1,15 @@
 """The two Lanczos recursions of Sec. 2.5, FP64, one operator application at a time.
 
-Both start from the right-hand side of Eq. 17, (0, y), and produce a tridiagonal matrix
+Both start from the right-hand side of Eq. 23, (0, y), and produce a tridiagonal matrix
 T_M with zero diagonal (each Lanczos vector has only one non-zero SBR half, and L maps an
 upper-only vector to a lower-only one and back, so every alpha_j vanishes), plus
-z_j = ((y, 0), v_j) (Eq. 24), accumulated on the fly.
+z_j = ((y, 0), v_j) (Eq. 31), accumulated on the fly.
 
 Output convention (shared with the C ABI): after n steps
     beta[0]  = b_1 = the norm of the starting vector, beta[i] = T_{i+1,i}  (i >= 1)
     gamma[0] = b_1,                                    gamma[i] = T_{i,i+1}
     z[i] = z_{i+1}
-so that chi ~ b_1 sum_j z_j [(omega - T)^-1]_{j1} (Eqs. 23, 25-26).
+so that chi ~ b_1 sum_j z_j [(omega - T)^-1]_{j1} (Eqs. 30, 32-33).
 
 Non-Hermitian biorthogonal recursion (Sec. 2.5): right vectors v_j with L, left vectors
 w_j with L^dagger = [[0, D+K], [D, 0]]; with s = (w_hat, v_hat):

@@ -5,15 +5,15 @@ k-point k, expanded on the sphere of k+Q; here it is a list over k of (nbnd, npw
 complex arrays.  Scalar product of batches (the one the Lanczos recursions use):
     (a, b) = (1/N_k) sum_k sum_v sum_G conj(a_{vk}(G)) b_{vk}(G).
 
-Operators (Eqs. 18-22, Hartree units):
-    D x = { P_c^{k+Q} (H_{k+Q} - eps_{vk}) x_{vk} }                      (Eq. 19)
-    K x = { P_c^{k+Q} v'_HXC[n'](r) u_{vk}(r) }                          (Eq. 20)
-    n'(r) = 4 sum_{vk} w_k u*_{vk}(r) x_{vk}(r),  w_k = 1/N_k            (Eq. 21)
-    v'_H(G) = 4 pi n'(G) / |Q+G|^2  on every grid frequency               (Eq. 10)
+Operators (Eqs. 24-28, Hartree units):
+    D x = { P_c^{k+Q} (H_{k+Q} - eps_{vk}) x_{vk} }                      (Eq. 25)
+    K x = { P_c^{k+Q} v'_HXC[n'](r) u_{vk}(r) }                          (Eq. 26)
+    n'(r) = 4 sum_{vk} w_k u*_{vk}(r) x_{vk}(r),  w_k = 1/N_k            (Eq. 27)
+    v'_H(G) = 4 pi n'(G) / |Q+G|^2  on every grid frequency               (Eq. 13)
     v'_XC(r) = f_xc(n0(r)) n'(r)  (ALDA; RPA drops it; IPA drops K)      (Sec. 3.2)
-    y = { P_c^{k+Q} u_{vk} }  (perturbation e^{iQ.r} with Q kept unfolded)  (Eq. 22)
-    P_c^{k} = 1 - sum_v |u_{vk}><u_{vk}|                                  (Eq. 14)
-    L (q, p) = (D p, (D + K) q)                                           (Eq. 18)
+    y = { P_c^{k+Q} u_{vk} }  (perturbation e^{iQ.r} with Q kept unfolded)  (Eq. 28)
+    P_c^{k} = 1 - sum_v |u_{vk}><u_{vk}|                                  (Eq. 16)
+    L (q, p) = (D p, (D + K) q)                                           (Eq. 24)
 
 Readings: P_c is applied to the whole output of D and K (projecting H x as well keeps
 every Lanczos vector in the conduction manifold); H_{k+Q} = kinetic + V_KS(r) + KB
@@ -77,7 +77,7 @@ class System:
         return sum(np.vdot(ak, bk) for ak, bk in zip(a, b)) / self.nks
 
     def project_c(self, x):
-        """P_c^{k+Q} x = x - U (U^H x) with U the occupied states at k+Q (Eq. 14)."""
+        """P_c^{k+Q} x = x - U (U^H x) with U the occupied states at k+Q (Eq. 16)."""
         out = []
         for k, xk in enumerate(x):
             u = self.ukq[k]
@@ -140,7 +140,7 @@ class System:
 
     def apply_op(self, x, upper: bool):
         """The operator the recursions apply to one half of a batch: D + K on the upper
-        (q) component, D on the lower (p) component (Eq. 18)."""
+        (q) component, D on the lower (p) component (Eq. 24)."""
         d = self.apply_d(x)
         if not upper or self.approx == "ipa":
             return d

@@ -1,9 +1,9 @@
-"""Post-processing of the Lanczos coefficients (Sec. 3.3; Eqs. 3, 23, 25-26).
+"""Post-processing of the Lanczos coefficients (Sec. 3.3; Eqs. 5, 30-33).
 
 For each frequency, with omega -> omega + i eta (Lorentzian broadening, Sec. 3.3):
     ((omega + i eta) I - T_M) x = e_1          solved with LAPACK zgtsv
     chi(Q, omega) = (4 / Omega) b_1 sum_j z_j x_j
-    eps^-1(Q, omega) = 1 + (4 pi / |Q|^2) chi   (Eq. 3, diagonal element)
+    eps^-1(Q, omega) = 1 + (4 pi / |Q|^2) chi   (Eq. 5, diagonal element)
     eps(Q, omega) = 1 / eps^-1                 (a scalar inverse, Sec. 2.1)
 The factor 4/Omega turns ((y, 0), (omega - L)^-1 (0, y)), with the batch scalar product
 that carries the 1/N_k k-weights, into the susceptibility per unit volume of a

@@ -1,7 +1,7 @@
 """Slater exchange + Perdew-Zunger 1981 correlation, unpolarised, Hartree units.
 
 The paper uses the LDA with the Perdew-Zunger parametrisation (Sec. 5) and the adiabatic
-XC kernel (Eq. 9: kappa_XC independent of frequency).  In the ALDA the kernel is local,
+XC kernel (Eq. 12: kappa_XC independent of frequency).  In the ALDA the kernel is local,
 kappa_XC(r, r') = f_xc(n(r)) delta(r - r'), with f_xc = d v_xc / dn = d^2 (n e_xc) / dn^2.
 
 Readings: f_xc = 0 where n <= 1e-10 bohr^-3; at r_s = 1 exactly the r_s >= 1 branch.

@@ -1,0 +1,736 @@
+// Host side of one Lanczos chain: device state, the operator schedule and the recursions.
+// Included once per precision translation unit (double: plain FP64 path; float: FP32
+// orbitals and FFTs with FP64 Lanczos scalars).
+#pragma once
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "ll.h"
+#include "kernels.cuh"
+
+namespace ll {
+
+struct ChainBase {
+  virtual ~ChainBase() {}
+  virtual int create(const ll_system_desc* d, cudaStream_t st, std::string& err) = 0;
+  virtual int lanczos(int n, double* beta, double* gamma, double* z, int* done, std::string& err) = 0;
+  virtual int spectrum(int m, const double* w_ev, int nw, double eta_ev, double* chi, double* ei, double* e,
+                       std::string& err) = 0;
+  virtual int apply(int upper, const double* x, double* out, std::string& err) = 0;
+  virtual int get_map(int* out, std::string& err) = 0;
+  virtual int get_start(double* y, std::string& err) = 0;
+  virtual size_t bytes() const = 0;
+  virtual int profile(int enable, std::string& err) = 0;
+  virtual int profile_read(double* ms, long long* launches, long long* total, std::string& err) = 0;
+};
+
+// Per-kernel-class device time, bracketed by CUDA events on the chain's stream while
+// profiling is on; launch counts are kept always.
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  int used = 0;
+  std::vector<int> cls, ea, eb;
+  long long launches[LL_NPROF] = {0}, total = 0;
+  int mark(cudaStream_t st) {
+    if (!on) return -1;
+    if (used == (int)pool.size()) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return -1;
+      pool.push_back(e);
+    }
+    cudaEventRecord(pool[used], st);
+    return used++;
+  }
+  void span(int c, int a, int b) {
+    if (a < 0 || b < 0) return;
+    cls.push_back(c); ea.push_back(a); eb.push_back(b);
+  }
+  void count(int c, int n = 1) { launches[c] += n; total += n; }
+  void reset() {
+    used = 0; cls.clear(); ea.clear(); eb.clear();
+    for (auto& l : launches) l = 0;
+    total = 0;
+  }
+  ~Profiler() { for (auto e : pool) cudaEventDestroy(e); }
+};
+
+ChainBase* make_chain_f64();
+ChainBase* make_chain_f32();
+int footprint_bytes(const ll_system_desc* d, size_t* out, std::string& err);
+
+#define LL_CK(call)                                                                    \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess) {                                                           \
+      err = std::string(#call) + ": " + cudaGetErrorString(e_);                        \
+      return (e_ == cudaErrorMemoryAllocation) ? LL_ENOMEM : LL_ECUDA;                 \
+    }                                                                                  \
+  } while (0)
+
+// Column/row tables of one sphere family, built on the host from the Miller lists.
+struct HostSphere {
+  int nks = 0, npw_pad = 0, ncol_max = 0, nrow_max = 0;
+  std::vector<int> npw, off, ncol, nrow, colstart;
+  std::vector<int4> col, row;
+};
+
+static inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+static inline bool build_sphere(int nks, const int* npw, const int* mil, int n, HostSphere& h, std::string& err) {
+  h.nks = nks;
+  h.npw.assign(npw, npw + nks);
+  h.off.resize(nks + 1);
+  h.off[0] = 0;
+  int maxnpw = 1;
+  for (int k = 0; k < nks; ++k) {
+    if (npw[k] <= 0) { err = "empty plane-wave sphere"; return false; }
+    h.off[k + 1] = h.off[k] + npw[k];
+    maxnpw = std::max(maxnpw, npw[k]);
+  }
+  h.npw_pad = round_up(maxnpw, 4);
+  std::vector<std::vector<int4>> cols(nks), rows(nks);
+  std::vector<std::vector<int>> starts(nks);
+  for (int k = 0; k < nks; ++k) {
+    const int* m = mil + 3L * h.off[k];
+    int lo[3] = {m[0], m[1], m[2]}, hi[3] = {m[0], m[1], m[2]};
+    for (int i = 0; i < npw[k]; ++i) {
+      for (int a = 0; a < 3; ++a) { lo[a] = std::min(lo[a], m[3 * i + a]); hi[a] = std::max(hi[a], m[3 * i + a]); }
+      if (i > 0) {
+        const int* p = m + 3 * (i - 1);
+        const int* q = m + 3 * i;
+        const bool less = p[0] < q[0] || (p[0] == q[0] && (p[1] < q[1] || (p[1] == q[1] && p[2] < q[2])));
+        if (!less) { err = "Miller indices of a sphere are not strictly lexicographic"; return false; }
+      }
+    }
+    for (int a = 0; a < 3; ++a)
+      if (hi[a] - lo[a] >= n) { err = "a plane-wave sphere does not fit the FFT grid"; return false; }
+    int i = 0;
+    while (i < npw[k]) {
+      int j = i;
+      while (j < npw[k] && m[3 * j] == m[3 * i] && m[3 * j + 1] == m[3 * i + 1]) {
+        if (j > i && m[3 * j + 2] != m[3 * (j - 1) + 2] + 1) { err = "a sphere column is not a contiguous run"; return false; }
+        ++j;
+      }
+      cols[k].push_back(make_int4(m[3 * i], m[3 * i + 1], m[3 * i + 2], j - i));
+      starts[k].push_back(i);
+      i = j;
+    }
+    // rows: runs of columns with equal m1, consecutive m2; the m1 values consecutive
+    int c = 0;
+    const int nc = (int)cols[k].size();
+    while (c < nc) {
+      int d = c;
+      while (d < nc && cols[k][d].x == cols[k][c].x) {
+        if (d > c && cols[k][d].y != cols[k][d - 1].y + 1) { err = "a sphere row is not a contiguous run"; return false; }
+        ++d;
+      }
+      if (!rows[k].empty() && cols[k][c].x != rows[k].back().x + 1) { err = "sphere rows are not consecutive"; return false; }
+      rows[k].push_back(make_int4(cols[k][c].x, c, cols[k][c].y, d - c));
+      c = d;
+    }
+    h.ncol_max = std::max(h.ncol_max, nc);
+    h.nrow_max = std::max(h.nrow_max, (int)rows[k].size());
+  }
+  h.ncol.resize(nks);
+  h.nrow.resize(nks);
+  h.col.assign((size_t)nks * h.ncol_max, make_int4(0, 0, 0, 0));
+  h.colstart.assign((size_t)nks * h.ncol_max, 0);
+  h.row.assign((size_t)nks * h.nrow_max, make_int4(0, 0, 0, 0));
+  for (int k = 0; k < nks; ++k) {
+    h.ncol[k] = (int)cols[k].size();
+    h.nrow[k] = (int)rows[k].size();
+    for (int c = 0; c < h.ncol[k]; ++c) {
+      h.col[(size_t)k * h.ncol_max + c] = cols[k][c];
+      h.colstart[(size_t)k * h.ncol_max + c] = starts[k][c];
+    }
+    for (int r = 0; r < h.nrow[k]; ++r) h.row[(size_t)k * h.nrow_max + r] = rows[k][r];
+  }
+  return true;
+}
+
+static inline void recip(const double a[3][3], double b[3][3]) {
+  const double det = a[0][0] * (a[1][1] * a[2][2] - a[1][2] * a[2][1]) - a[0][1] * (a[1][0] * a[2][2] - a[1][2] * a[2][0]) +
+                     a[0][2] * (a[1][0] * a[2][1] - a[1][1] * a[2][0]);
+  const double f = 2.0 * 3.14159265358979323846 / det;
+  // b_i = 2 pi (a_j x a_k) / det
+  for (int i = 0; i < 3; ++i) {
+    const double* u = a[(i + 1) % 3];
+    const double* v = a[(i + 2) % 3];
+    b[i][0] = f * (u[1] * v[2] - u[2] * v[1]);
+    b[i][1] = f * (u[2] * v[0] - u[0] * v[2]);
+    b[i][2] = f * (u[0] * v[1] - u[1] * v[0]);
+  }
+}
+
+template <int N> struct BO { static constexpr int v = (128 / N) < 1 ? 1 : 128 / N; };
+
+template <typename T>
+class Chain : public ChainBase {
+ public:
+  ~Chain() override {
+    for (void* p : ptrs_) cudaFree(p);
+  }
+  size_t bytes() const override { return bytes_; }
+
+  int create(const ll_system_desc* d, cudaStream_t st, std::string& err) override {
+    st_ = st;
+    N_ = d->nfft;
+    nks_ = d->nks;
+    nbnd_ = d->nbnd;
+    nproj_ = d->nproj;
+    approx_ = d->approx;
+    flavour_ = d->flavour;
+    cap_ = d->max_steps;
+    const int n = N_;
+    bool ok_n = false;
+    for (int s : kGridSides) ok_n |= (s == n);
+    if (!ok_n) { err = "unsupported FFT grid side"; return LL_EUNSUPPORTED; }
+    if (nks_ < 1 || nbnd_ < 1 || nbnd_ > 32 || nproj_ < 0 || nproj_ > 64 || cap_ < 1) { err = "bad dimensions"; return LL_EINVAL; }
+    if (approx_ < 0 || approx_ > 2 || flavour_ < 0 || flavour_ > 1) { err = "bad approx/flavour"; return LL_EINVAL; }
+    if (!d->kcart || !d->npw_k || !d->miller_k || !d->npw_kq || !d->miller_kq || !d->u_k || !d->u_kq || !d->eps_k ||
+        !d->vloc_r || !d->rho_r || (nproj_ > 0 && (!d->beta_kq || !d->dij))) {
+      err = "missing input array";
+      return LL_EINVAL;
+    }
+    if (!build_sphere(nks_, d->npw_k, d->miller_k, n, hk_, err)) return LL_EINVAL;
+    if (!build_sphere(nks_, d->npw_kq, d->miller_kq, n, hq_, err)) return LL_EINVAL;
+    for (int k = 0; k < nks_; ++k)
+      if (d->npw_kq[k] < nbnd_ + 1) { err = "sphere smaller than the occupied manifold"; return LL_EINVAL; }
+    double b[3][3];
+    recip(d->lattice, b);
+    omega_ = fabs(d->lattice[0][0] * (d->lattice[1][1] * d->lattice[2][2] - d->lattice[1][2] * d->lattice[2][1]) -
+                  d->lattice[0][1] * (d->lattice[1][0] * d->lattice[2][2] - d->lattice[1][2] * d->lattice[2][0]) +
+                  d->lattice[0][2] * (d->lattice[1][0] * d->lattice[2][1] - d->lattice[1][1] * d->lattice[2][0]));
+    for (int a = 0; a < 3; ++a) q_[a] = d->q_cart[a];
+    const long n3 = (long)n * n * n;
+    const int pq = hq_.npw_pad, pk = hk_.npw_pad;
+    const long vq = (long)nks_ * nbnd_ * pq;  // one batch vector
+    nvec_ = (flavour_ == LL_FLAVOUR_NH) ? 2 : 1;
+
+    // Hartree kernel 4 pi / |Q + G|^2 / N^3 over the box, [m3][m2][m1]
+    std::vector<T> wh(n3);
+    for (int i3 = 0; i3 < n; ++i3)
+      for (int i2 = 0; i2 < n; ++i2)
+        for (int i1 = 0; i1 < n; ++i1) {
+          const int m1 = i1 < n / 2 ? i1 : i1 - n, m2 = i2 < n / 2 ? i2 : i2 - n, m3 = i3 < n / 2 ? i3 : i3 - n;
+          double g[3];
+          for (int a = 0; a < 3; ++a) g[a] = q_[a] + m1 * b[0][a] + m2 * b[1][a] + m3 * b[2][a];
+          const double g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+          if (!(g2 > 1e-20)) { err = "Q + G = 0 on the grid (Q is a reciprocal lattice vector)"; return LL_EINVAL; }
+          wh[((long)i3 * n + i2) * n + i1] = (T)(4.0 * 3.14159265358979323846 / g2 / (double)n3);
+        }
+    // kinetic 1/2 |k + Q + G|^2 on sphere(k+Q)
+    std::vector<T> kin((size_t)nks_ * pq, T(0));
+    for (int k = 0; k < nks_; ++k) {
+      const int* m = d->miller_kq + 3L * hq_.off[k];
+      for (int i = 0; i < hq_.npw[k]; ++i) {
+        double g[3];
+        for (int a = 0; a < 3; ++a)
+          g[a] = d->kcart[3 * k + a] + q_[a] + m[3 * i] * b[0][a] + m[3 * i + 1] * b[1][a] + m[3 * i + 2] * b[2][a];
+        kin[(size_t)k * pq + i] = (T)(0.5 * (g[0] * g[0] + g[1] * g[1] + g[2] * g[2]));
+      }
+    }
+    // padded orbital tables
+    std::vector<cplx<T>> uk = pad_batch(d->u_k, hk_, nbnd_);
+    std::vector<cplx<T>> ukq = pad_batch(d->u_kq, hq_, nbnd_);
+    std::vector<cplx<T>> bkq = nproj_ ? pad_batch(d->beta_kq, hq_, nproj_) : std::vector<cplx<T>>(1);
+    // grids transposed to [j3][j2][j1]
+    std::vector<T> vl(n3);
+    std::vector<double> rh(n3);
+    for (int j1 = 0; j1 < n; ++j1)
+      for (int j2 = 0; j2 < n; ++j2)
+        for (int j3 = 0; j3 < n; ++j3) {
+          const long src = ((long)j1 * n + j2) * n + j3, dst = ((long)j3 * n + j2) * n + j1;
+          vl[dst] = (T)d->vloc_r[src];
+          rh[dst] = d->rho_r[src];
+        }
+
+    int rc;
+    if ((rc = tw_tables_upload(st_)) != cudaSuccess) { err = "twiddle upload failed"; return LL_ECUDA; }
+    // device buffers
+    if ((rc = upload_sphere(hk_, dk_, err)) || (rc = upload_sphere(hq_, dq_, err))) return rc;
+    cb_ncol_ = std::max(hk_.ncol_max, hq_.ncol_max);
+    const int norb = nvec_ * nks_ * nbnd_;
+    ngroups_ = groups_for(norb);
+    if ((rc = alloc(&whart_, n3)) || (rc = alloc(&kin_, (long)nks_ * pq)) || (rc = alloc(&uk_, (long)nks_ * nbnd_ * pk)) ||
+        (rc = alloc(&ukq_, vq)) || (rc = alloc(&bkq_, (long)bkq.size())) || (rc = alloc(&eps_, (long)nks_ * nbnd_)) ||
+        (rc = alloc(&dij_, std::max(1, nproj_))) || (rc = alloc(&vloc_, n3)) || (rc = alloc(&rho_, n3)) ||
+        (rc = alloc(&fxc_, n3)) || (rc = alloc(&ur_, (long)nks_ * nbnd_ * n3)) ||
+        (rc = alloc(&cbuf_, (long)norb * n * cb_ncol_)) || (rc = alloc(&nprt_, (long)ngroups_ * n3)) ||
+        (rc = alloc(&nr_, n3)) || (rc = alloc(&ng_, n3)) || (rc = alloc(&vpr_, n3)) || (rc = alloc(&tbuf_, nvec_ * vq)) ||
+        (rc = alloc(&y_, vq)) || (rc = alloc(&map_, (long)nks_ * pq)) || (rc = alloc(&part_, 2L * nks_)) ||
+        (rc = alloc(&spart_, (long)nks_)) || (rc = alloc(&vecs_, 3L * nvec_ * vq)) ||
+        (rc = alloc(&beta_, cap_ + 2)) || (rc = alloc(&gamma_, cap_ + 2)) || (rc = alloc(&z_, cap_ + 1)) ||
+        (rc = alloc(&zpart_, (long)(cap_ + 1) * nks_)) || (rc = alloc(&err_, 2)))
+      return rc;
+    (void)err;
+    LL_CK(cudaMemcpyAsync(whart_, wh.data(), n3 * sizeof(T), cudaMemcpyHostToDevice, st_));
+    LL_CK(cudaMemcpyAsync(kin_, kin.data(), kin.size() * sizeof(T), cudaMemcpyHostToDevice, st_));
+    LL_CK(cudaMemcpyAsync(uk_, uk.data(), uk.size() * sizeof(cplx<T>), cudaMemcpyHostToDevice, st_));
+    LL_CK(cudaMemcpyAsync(ukq_, ukq.data(), ukq.size() * sizeof(cplx<T>), cudaMemcpyHostToDevice, st_));
+    LL_CK(cudaMemcpyAsync(bkq_, bkq.data(), bkq.size() * sizeof(cplx<T>), cudaMemcpyHostToDevice, st_));
+    LL_CK(cudaMemcpyAsync(eps_, d->eps_k, sizeof(double) * nks_ * nbnd_, cudaMemcpyHostToDevice, st_));
+    if (nproj_) LL_CK(cudaMemcpyAsync(dij_, d->dij, sizeof(double) * nproj_, cudaMemcpyHostToDevice, st_));
+    LL_CK(cudaMemcpyAsync(vloc_, vl.data(), n3 * sizeof(T), cudaMemcpyHostToDevice, st_));
+    LL_CK(cudaMemcpyAsync(rho_, rh.data(), n3 * sizeof(double), cudaMemcpyHostToDevice, st_));
+    LL_CK(cudaMemsetAsync(err_, 0, 2 * sizeof(int), st_));
+    LL_CK(cudaMemsetAsync(vecs_, 0, 3L * nvec_ * vq * sizeof(cplx<T>), st_));
+    LL_CK(cudaMemsetAsync(zpart_, 0, (long)(cap_ + 1) * nks_ * sizeof(cplx<double>), st_));
+    k_fxc<T><<<256, 256, 0, st_>>>(n3, rho_, fxc_, approx_ == LL_APPROX_TDDFT ? 1 : 0);
+    LL_CK(cudaGetLastError());
+
+    // index map sphere(k+Q) -> sphere(k) (on the device, from the Miller lists)
+    {
+      int *mk = nullptr, *mq = nullptr, *ok = nullptr, *oq = nullptr, *nk = nullptr, *nq = nullptr;
+      if ((rc = alloc(&mk, 3L * hk_.off[nks_])) || (rc = alloc(&mq, 3L * hq_.off[nks_])) || (rc = alloc(&ok, nks_ + 1)) ||
+          (rc = alloc(&oq, nks_ + 1)) || (rc = alloc(&nk, nks_)) || (rc = alloc(&nq, nks_)))
+        return rc;
+      LL_CK(cudaMemcpyAsync(mk, d->miller_k, 3L * hk_.off[nks_] * sizeof(int), cudaMemcpyHostToDevice, st_));
+      LL_CK(cudaMemcpyAsync(mq, d->miller_kq, 3L * hq_.off[nks_] * sizeof(int), cudaMemcpyHostToDevice, st_));
+      LL_CK(cudaMemcpyAsync(ok, hk_.off.data(), (nks_ + 1) * sizeof(int), cudaMemcpyHostToDevice, st_));
+      LL_CK(cudaMemcpyAsync(oq, hq_.off.data(), (nks_ + 1) * sizeof(int), cudaMemcpyHostToDevice, st_));
+      LL_CK(cudaMemcpyAsync(nk, d->npw_k, nks_ * sizeof(int), cudaMemcpyHostToDevice, st_));
+      LL_CK(cudaMemcpyAsync(nq, d->npw_kq, nks_ * sizeof(int), cudaMemcpyHostToDevice, st_));
+      k_intersection_map<<<nks_, 128, 0, st_>>>(nks_, ok, nk, mk, oq, nq, mq, pq, map_);
+      LL_CK(cudaGetLastError());
+      LL_CK(cudaStreamSynchronize(st_));
+      for (int* p : {mk, mq, ok, oq, nk, nq}) release(p);
+    }
+    // y = P_c (u_k on sphere(k+Q))   (Eq. 28)
+    k_gather_y<T><<<nks_, 128, 0, st_>>>(nks_, nbnd_, pq, pk, map_, uk_, y_);
+    k_project<T><<<dim3(nks_, 1), 128, 0, st_>>>(nks_, nbnd_, pq, dq_.npw, ukq_, y_);
+    LL_CK(cudaGetLastError());
+    // u_{vk}(r) grids: columns of sphere(k), then the planes
+    if ((rc = launch_zinv(dk_, uk_, 1)) || (rc = launch_xy(dk_, nks_ * nbnd_, 0, -1, 2, err))) return rc;
+    LL_CK(cudaGetLastError());
+
+    // start of the recursion
+    if (flavour_ == LL_FLAVOUR_PH) {
+      LL_CK(cudaMemcpyAsync(R(), y_, vq * sizeof(cplx<T>), cudaMemcpyDeviceToDevice, st_));
+      if ((rc = op(1, R(), X(), -1, err))) return rc;               // X_1 = D y
+      std::vector<double> hp(nks_);
+      LL_CK(cudaMemcpyAsync(hp.data(), part_, nks_ * sizeof(double), cudaMemcpyDeviceToHost, st_));
+      LL_CK(cudaStreamSynchronize(st_));
+      double s = 0;
+      for (double v : hp) s += v;
+      s /= nks_;
+      if (!(s > 0)) { err = "D is not positive on the starting vector"; return LL_ENOTPD; }
+      tol_ = 1e-28 * s;
+    } else {
+      k_dot_re<T><<<nks_, 128, 0, st_>>>(nks_, nbnd_, pq, y_, y_, part_);
+      std::vector<double> hp(nks_);
+      LL_CK(cudaMemcpyAsync(hp.data(), part_, nks_ * sizeof(double), cudaMemcpyDeviceToHost, st_));
+      LL_CK(cudaStreamSynchronize(st_));
+      double s = 0;
+      for (double v : hp) s += v;
+      s /= nks_;
+      if (!(s > 0)) { err = "the starting vector vanishes"; return LL_EINVAL; }
+      const double b1 = sqrt(s);
+      tol_ = 1e-28 * s;
+      k_scale<T><<<256, 256, 0, st_>>>(vq, y_, 1.0 / b1, Vc());
+      k_scale<T><<<256, 256, 0, st_>>>(vq, y_, 1.0 / b1, Wc());
+      cplx<double> g1 = mk(b1, 0.0);
+      LL_CK(cudaMemcpyAsync(beta_, &b1, sizeof(double), cudaMemcpyHostToDevice, st_));
+      LL_CK(cudaMemcpyAsync(gamma_, &g1, sizeof(g1), cudaMemcpyHostToDevice, st_));
+      LL_CK(cudaGetLastError());
+    }
+    LL_CK(cudaStreamSynchronize(st_));
+    steps_ = 0;
+    return LL_OK;
+  }
+
+  int lanczos(int n, double* beta, double* gamma, double* z, int* done, std::string& err) override {
+    if (n < 0 || steps_ + n > cap_) { err = "more steps than max_steps"; return LL_EINVAL; }
+    if (stopped_) {
+      if (done) *done = steps_;
+      err = "the chain stopped at a breakdown";
+      return LL_EBREAKDOWN;
+    }
+    int rc;
+    const int pq = hq_.npw_pad;
+    const size_t smem_upd = (size_t)nbnd_ * pq * sizeof(cplx<T>) + (size_t)(nbnd_ * nbnd_ + 1) * sizeof(cplx<double>);
+    const size_t smem_nh = 2 * (size_t)nbnd_ * pq * sizeof(cplx<T>) + 2 * (size_t)nbnd_ * nbnd_ * sizeof(cplx<double>);
+    Coef co{beta_, gamma_, zpart_, err_};
+    for (int s = 0; s < n; ++s) {
+      const int j = steps_ + s + 1;
+      if (flavour_ == LL_FLAVOUR_PH) {
+        if ((rc = set_smem(k_update_ph<T>, smem_upd, err))) return rc;
+        const int u0 = prof_.mark(st_);
+        k_update_ph<T><<<nks_, 128, smem_upd, st_>>>(j, (j % 2 == 0) ? 1 : 0, nks_, nbnd_, pq, dq_.npw, part_, R(), X(),
+                                                     Vp(), y_, ukq_, co, tol_);
+        prof_.count(LL_PROF_UPDATE);
+        prof_.span(LL_PROF_UPDATE, u0, prof_.mark(st_));
+        // r_{j+1} is upper when j is odd; the upper half gets D + K
+        const int dens = (j % 2 == 1 && approx_ != LL_APPROX_IPA) ? 0 : -1;
+        if ((rc = op(1, R(), X(), dens, err))) return rc;
+      } else {
+        const int upper = (j % 2 == 0) ? 1 : 0;
+        // L v_j: D + K on an upper v; L^dag w_j: D + K on a lower w
+        const int dens = (approx_ == LL_APPROX_IPA) ? -1 : (upper ? 0 : 1);
+        if ((rc = op(2, Vc(), XV(), dens, err))) return rc;
+        if ((rc = set_smem(k_nh_update<T>, smem_nh, err))) return rc;
+        const int u0 = prof_.mark(st_);
+        k_nh_update<T><<<nks_, 128, smem_nh, st_>>>(j, upper, nks_, nbnd_, pq, dq_.npw, XV(), XW(), VpNH(), Wp(), Vc(),
+                                                    y_, ukq_, co, spart_);
+        k_nh_normalize<T><<<nks_, 128, 0, st_>>>(j, nks_, nbnd_, pq, spart_, XV(), XW(), Vc(), VpNH(), Wc(), Wp(), co,
+                                                 tol_);
+        prof_.count(LL_PROF_UPDATE, 2);
+        prof_.span(LL_PROF_UPDATE, u0, prof_.mark(st_));
+      }
+      LL_CK(cudaGetLastError());
+    }
+    if (n > 0) {
+      k_reduce_z<<<(n + 127) / 128, 128, 0, st_>>>(zpart_, nks_, steps_, steps_ + n, z_);
+      LL_CK(cudaGetLastError());
+      prof_.count(LL_PROF_UPDATE);
+    }
+    int herr[2];
+    LL_CK(cudaMemcpyAsync(herr, err_, sizeof(herr), cudaMemcpyDeviceToHost, st_));
+    LL_CK(cudaStreamSynchronize(st_));
+    steps_ += n;
+    int status = LL_OK;
+    if (herr[0] != DEV_OK) {
+      steps_ = std::min(steps_, herr[1] - 1);
+      status = (herr[0] == DEV_NOTPD) ? LL_ENOTPD : LL_EBREAKDOWN;
+      err = (status == LL_ENOTPD) ? "pseudo-Hermitian metric not positive" : "Lanczos breakdown";
+      stopped_ = true;
+    }
+    if (done) *done = steps_;
+    if (steps_ > 0) {
+      if (beta) LL_CK(cudaMemcpyAsync(beta, beta_, steps_ * sizeof(double), cudaMemcpyDeviceToHost, st_));
+      if (gamma) LL_CK(cudaMemcpyAsync(gamma, gamma_, steps_ * sizeof(cplx<double>), cudaMemcpyDeviceToHost, st_));
+      if (z) LL_CK(cudaMemcpyAsync(z, z_, steps_ * sizeof(cplx<double>), cudaMemcpyDeviceToHost, st_));
+      LL_CK(cudaStreamSynchronize(st_));
+    }
+    return status;
+  }
+
+  int spectrum(int m, const double* w_ev, int nw, double eta_ev, double* chi, double* ei, double* e,
+               std::string& err) override {
+    if (m <= 0 || m > steps_) m = steps_;
+    if (m < 1 || nw < 1) { err = "no coefficients or no frequencies"; return LL_EINVAL; }
+    int rc;
+    if (nw > spec_cap_) {
+      release(spec_w_); release(spec_out_);
+      spec_w_ = nullptr; spec_out_ = nullptr;
+      if ((rc = alloc(&spec_w_, nw)) || (rc = alloc(&spec_out_, 3L * nw))) return rc;
+      spec_cap_ = nw;
+    }
+    const double ha = 27.211386245988;
+    std::vector<double> w(nw);
+    for (int i = 0; i < nw; ++i) w[i] = w_ev[i] / ha;
+    LL_CK(cudaMemcpyAsync(spec_w_, w.data(), nw * sizeof(double), cudaMemcpyHostToDevice, st_));
+    const double q2 = q_[0] * q_[0] + q_[1] * q_[1] + q_[2] * q_[2];
+    k_spectrum<<<(nw + 127) / 128, 128, 0, st_>>>(m, beta_, gamma_, z_, nw, spec_w_, eta_ev / ha, 4.0 / omega_,
+                                                  4.0 * 3.14159265358979323846 / q2, spec_out_, spec_out_ + nw,
+                                                  spec_out_ + 2L * nw);
+    LL_CK(cudaGetLastError());
+    if (chi) LL_CK(cudaMemcpyAsync(chi, spec_out_, nw * sizeof(cplx<double>), cudaMemcpyDeviceToHost, st_));
+    if (ei) LL_CK(cudaMemcpyAsync(ei, spec_out_ + nw, nw * sizeof(cplx<double>), cudaMemcpyDeviceToHost, st_));
+    if (e) LL_CK(cudaMemcpyAsync(e, spec_out_ + 2L * nw, nw * sizeof(cplx<double>), cudaMemcpyDeviceToHost, st_));
+    LL_CK(cudaStreamSynchronize(st_));
+    return LL_OK;
+  }
+
+  int apply(int upper, const double* x, double* out, std::string& err) override {
+    int rc;
+    const long vq = (long)nks_ * nbnd_ * hq_.npw_pad;
+    if (!scratch_ && (rc = alloc(&scratch_, 2 * vq))) return rc;
+    std::vector<cplx<T>> h = pad_batch(x, hq_, nbnd_);
+    LL_CK(cudaMemcpyAsync(scratch_, h.data(), vq * sizeof(cplx<T>), cudaMemcpyHostToDevice, st_));
+    // a one-vector application reuses the cbuf/tbuf sized for nvec_ >= 1
+    if ((rc = op(1, scratch_, scratch_ + vq, (upper && approx_ != LL_APPROX_IPA) ? 0 : -1, err))) return rc;
+    LL_CK(cudaMemcpyAsync(h.data(), scratch_ + vq, vq * sizeof(cplx<T>), cudaMemcpyDeviceToHost, st_));
+    LL_CK(cudaStreamSynchronize(st_));
+    unpad_batch(h, hq_, nbnd_, out);
+    return LL_OK;
+  }
+
+  int get_map(int* out, std::string& err) override {
+    std::vector<int> h((size_t)nks_ * hq_.npw_pad);
+    LL_CK(cudaMemcpyAsync(h.data(), map_, h.size() * sizeof(int), cudaMemcpyDeviceToHost, st_));
+    LL_CK(cudaStreamSynchronize(st_));
+    for (int k = 0; k < nks_; ++k)
+      memcpy(out + hq_.off[k], h.data() + (size_t)k * hq_.npw_pad, hq_.npw[k] * sizeof(int));
+    return LL_OK;
+  }
+
+  int get_start(double* y, std::string& err) override {
+    std::vector<cplx<T>> h((size_t)nks_ * nbnd_ * hq_.npw_pad);
+    LL_CK(cudaMemcpyAsync(h.data(), y_, h.size() * sizeof(cplx<T>), cudaMemcpyDeviceToHost, st_));
+    LL_CK(cudaStreamSynchronize(st_));
+    unpad_batch(h, hq_, nbnd_, y);
+    return LL_OK;
+  }
+
+  int profile(int enable, std::string& err) override {
+    LL_CK(cudaStreamSynchronize(st_));
+    if (enable) prof_.reset();
+    prof_.on = enable != 0;
+    return LL_OK;
+  }
+
+  int profile_read(double* ms, long long* launches, long long* total, std::string& err) override {
+    LL_CK(cudaStreamSynchronize(st_));
+    for (int c = 0; c < LL_NPROF; ++c) {
+      if (ms) ms[c] = 0.0;
+      if (launches) launches[c] = prof_.launches[c];
+    }
+    if (total) *total = prof_.total;
+    if (ms)
+      for (size_t i = 0; i < prof_.cls.size(); ++i) {
+        float t = 0.f;
+        LL_CK(cudaEventElapsedTime(&t, prof_.pool[prof_.ea[i]], prof_.pool[prof_.eb[i]]));
+        ms[prof_.cls[i]] += t;
+      }
+    return LL_OK;
+  }
+
+ private:
+  // one batch operator application on nvec contiguous vectors (Eqs. 24-28)
+  int op(int nvec, const cplx<T>* in, cplx<T>* out, int dens_vec, std::string& err) {
+    int rc;
+    const int e0 = prof_.mark(st_);
+    if ((rc = launch_zinv(dq_, in, nvec))) { err = "zinv launch"; return rc; }
+    prof_.count(LL_PROF_ZINV);
+    const int e1 = prof_.mark(st_);
+    prof_.span(LL_PROF_ZINV, e0, e1);
+    if ((rc = launch_xy(dq_, nvec * nks_ * nbnd_, 0, dens_vec, 0, err))) return rc;
+    prof_.count(LL_PROF_XY1);
+    int e2 = prof_.mark(st_);
+    prof_.span(LL_PROF_XY1, e1, e2);
+    if (dens_vec >= 0) {
+      if ((rc = launch_hxc(err))) return rc;
+      prof_.count(LL_PROF_HXC, 3);
+      const int e3 = prof_.mark(st_);
+      prof_.span(LL_PROF_HXC, e2, e3);
+      if ((rc = launch_xy(dq_, nks_ * nbnd_, dens_vec * nks_ * nbnd_, dens_vec, 1, err))) return rc;
+      prof_.count(LL_PROF_XY2);
+      e2 = prof_.mark(st_);
+      prof_.span(LL_PROF_XY2, e3, e2);
+    }
+    if ((rc = launch_zfwd(nvec))) { err = "zfwd launch"; return rc; }
+    prof_.count(LL_PROF_ZFWD);
+    const int e4 = prof_.mark(st_);
+    prof_.span(LL_PROF_ZFWD, e2, e4);
+    const size_t smem = 2 * (size_t)nbnd_ * hq_.npw_pad * sizeof(cplx<T>) +
+                        (size_t)std::max(nproj_, nbnd_) * nbnd_ * sizeof(cplx<double>);
+    if ((rc = set_smem(k_proj<T>, smem, err))) return rc;
+    k_proj<T><<<dim3(nks_, nvec), 128, smem, st_>>>(nks_, nbnd_, hq_.npw_pad, dq_.npw, in, tbuf_, kin_, eps_, ukq_, bkq_,
+                                                   dij_, nproj_, out, part_);
+    LL_CK(cudaGetLastError());
+    prof_.count(LL_PROF_PROJ);
+    prof_.span(LL_PROF_PROJ, e4, prof_.mark(st_));
+    return LL_OK;
+  }
+
+  template <int N>
+  int zinv_n(const SphereDev& s, const cplx<T>* in, int nvec) {
+    k_zinv<T, N><<<dim3(nks_, nvec), 128, 0, st_>>>(s, in, nbnd_, cbuf_, cb_ncol_);
+    return cudaGetLastError() == cudaSuccess ? LL_OK : LL_ECUDA;
+  }
+  int launch_zinv(const SphereDev& s, const cplx<T>* in, int nvec) {
+    switch (N_) {
+      case 12: return zinv_n<12>(s, in, nvec);
+      case 16: return zinv_n<16>(s, in, nvec);
+      case 18: return zinv_n<18>(s, in, nvec);
+      case 24: return zinv_n<24>(s, in, nvec);
+      case 32: return zinv_n<32>(s, in, nvec);
+      case 36: return zinv_n<36>(s, in, nvec);
+      case 48: return zinv_n<48>(s, in, nvec);
+    }
+    return LL_EUNSUPPORTED;
+  }
+  template <int N>
+  int zfwd_n(int nvec) {
+    k_zfwd<T, N><<<dim3(nks_, nvec), 128, 0, st_>>>(dq_, cbuf_, cb_ncol_, nbnd_, tbuf_);
+    return cudaGetLastError() == cudaSuccess ? LL_OK : LL_ECUDA;
+  }
+  int launch_zfwd(int nvec) {
+    switch (N_) {
+      case 12: return zfwd_n<12>(nvec);
+      case 16: return zfwd_n<16>(nvec);
+      case 18: return zfwd_n<18>(nvec);
+      case 24: return zfwd_n<24>(nvec);
+      case 32: return zfwd_n<32>(nvec);
+      case 36: return zfwd_n<36>(nvec);
+      case 48: return zfwd_n<48>(nvec);
+    }
+    return LL_EUNSUPPORTED;
+  }
+  int groups_for(int norb) const {
+    const int target = 4 * 152;
+    int g = std::max(1, (target + N_ - 1) / N_);
+    return std::min(g, norb);
+  }
+  template <int N>
+  int xy_n(const SphereDev& s, int norb, int o_off, int dens_vec, int mode, std::string& err) {
+    constexpr int B = BO<N>::v;
+    const int ng = std::min(ngroups_, norb);
+    XYArgs a;
+    a.s = s;
+    a.nbnd = nbnd_;
+    a.norb = norb;
+    a.cb_ncol = cb_ncol_;
+    a.per_group = (norb + ng - 1) / ng;
+    a.o_off = o_off;
+    a.dens_vec = (mode == 0) ? dens_vec : -1;
+    a.mode = mode;
+    const int NP = N + 1;
+    size_t smem = (size_t)B * cb_ncol_ + (size_t)B * s.nrow_max * NP;
+    if (mode == 0 && a.dens_vec >= 0) smem += (size_t)B * N * NP;
+    smem += (size_t)N * NP;
+    smem *= sizeof(cplx<T>);
+    int rc;
+    if ((rc = set_smem(k_xy<T, N, B>, smem, err))) return rc;
+    k_xy<T, N, B><<<dim3(N, ng), 128, smem, st_>>>(a, cbuf_, vloc_, vpr_, ur_, nprt_, ur_);
+    if (mode == 0) last_ng_ = ng;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { err = std::string("k_xy: ") + cudaGetErrorString(e); return LL_ECUDA; }
+    return LL_OK;
+  }
+  int launch_xy(const SphereDev& s, int norb, int o_off, int dens_vec, int mode, std::string& err) {
+    switch (N_) {
+      case 12: return xy_n<12>(s, norb, o_off, dens_vec, mode, err);
+      case 16: return xy_n<16>(s, norb, o_off, dens_vec, mode, err);
+      case 18: return xy_n<18>(s, norb, o_off, dens_vec, mode, err);
+      case 24: return xy_n<24>(s, norb, o_off, dens_vec, mode, err);
+      case 32: return xy_n<32>(s, norb, o_off, dens_vec, mode, err);
+      case 36: return xy_n<36>(s, norb, o_off, dens_vec, mode, err);
+      case 48: return xy_n<48>(s, norb, o_off, dens_vec, mode, err);
+    }
+    return LL_EUNSUPPORTED;
+  }
+  template <int N>
+  int hxc_n(std::string& err) {
+    const T scale = (T)(4.0 / (omega_ * nks_));
+    k_hxc_fwd<T, N><<<N, 64, 0, st_>>>(nprt_, last_ng_, scale, nr_, ng_);
+    k_hxc_z<T, N><<<(N * N + 63) / 64, 64, 0, st_>>>(ng_, whart_);
+    k_hxc_inv<T, N><<<N, 64, 0, st_>>>(ng_, nr_, fxc_, vpr_);
+    LL_CK(cudaGetLastError());
+    return LL_OK;
+  }
+  int launch_hxc(std::string& err) {
+    switch (N_) {
+      case 12: return hxc_n<12>(err);
+      case 16: return hxc_n<16>(err);
+      case 18: return hxc_n<18>(err);
+      case 24: return hxc_n<24>(err);
+      case 32: return hxc_n<32>(err);
+      case 36: return hxc_n<36>(err);
+      case 48: return hxc_n<48>(err);
+    }
+    return LL_EUNSUPPORTED;
+  }
+
+  template <typename F>
+  int set_smem(F* fn, size_t bytes, std::string& err) {
+    if (bytes > 48 * 1024) {
+      if (bytes > 227 * 1024) { err = "shared-memory tile exceeds 227 KB for this system"; return LL_EUNSUPPORTED; }
+      LL_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    }
+    return LL_OK;
+  }
+
+  static std::vector<cplx<T>> pad_batch(const double* src, const HostSphere& h, int nb) {
+    std::vector<cplx<T>> out((size_t)h.nks * nb * h.npw_pad, czero<T>());
+    size_t pos = 0;
+    for (int k = 0; k < h.nks; ++k)
+      for (int v = 0; v < nb; ++v)
+        for (int i = 0; i < h.npw[k]; ++i, ++pos)
+          out[((size_t)k * nb + v) * h.npw_pad + i] = mk((T)src[2 * pos], (T)src[2 * pos + 1]);
+    return out;
+  }
+  static void unpad_batch(const std::vector<cplx<T>>& in, const HostSphere& h, int nb, double* dst) {
+    size_t pos = 0;
+    for (int k = 0; k < h.nks; ++k)
+      for (int v = 0; v < nb; ++v)
+        for (int i = 0; i < h.npw[k]; ++i, ++pos) {
+          const cplx<T> c = in[((size_t)k * nb + v) * h.npw_pad + i];
+          dst[2 * pos] = (double)c.x;
+          dst[2 * pos + 1] = (double)c.y;
+        }
+  }
+
+  template <typename U>
+  int alloc(U** p, long count) {
+    void* q = nullptr;
+    const size_t nbytes = sizeof(U) * (size_t)std::max(1L, count);
+    if (cudaMalloc(&q, nbytes) != cudaSuccess) { cudaGetLastError(); return LL_ENOMEM; }
+    ptrs_.push_back(q);
+    bytes_ += nbytes;
+    *p = static_cast<U*>(q);
+    return LL_OK;
+  }
+  template <typename U>
+  void release(U* p) {
+    if (!p) return;
+    auto it = std::find(ptrs_.begin(), ptrs_.end(), (void*)p);
+    if (it != ptrs_.end()) { cudaFree(p); ptrs_.erase(it); }
+  }
+  int upload_sphere(const HostSphere& h, SphereDev& dsph, std::string& err) {
+    int *npw, *ncol, *nrow, *cs;
+    int4 *col, *row;
+    int rc;
+    if ((rc = alloc(&npw, h.nks)) || (rc = alloc(&ncol, h.nks)) || (rc = alloc(&nrow, h.nks)) ||
+        (rc = alloc(&cs, (long)h.colstart.size())) || (rc = alloc(&col, (long)h.col.size())) ||
+        (rc = alloc(&row, (long)h.row.size())))
+      return rc;
+    LL_CK(cudaMemcpyAsync(npw, h.npw.data(), h.nks * sizeof(int), cudaMemcpyHostToDevice, st_));
+    LL_CK(cudaMemcpyAsync(ncol, h.ncol.data(), h.nks * sizeof(int), cudaMemcpyHostToDevice, st_));
+    LL_CK(cudaMemcpyAsync(nrow, h.nrow.data(), h.nks * sizeof(int), cudaMemcpyHostToDevice, st_));
+    LL_CK(cudaMemcpyAsync(cs, h.colstart.data(), h.colstart.size() * sizeof(int), cudaMemcpyHostToDevice, st_));
+    LL_CK(cudaMemcpyAsync(col, h.col.data(), h.col.size() * sizeof(int4), cudaMemcpyHostToDevice, st_));
+    LL_CK(cudaMemcpyAsync(row, h.row.data(), h.row.size() * sizeof(int4), cudaMemcpyHostToDevice, st_));
+    LL_CK(cudaStreamSynchronize(st_));
+    dsph.nks = h.nks;
+    dsph.npw_pad = h.npw_pad;
+    dsph.ncol_max = h.ncol_max;
+    dsph.nrow_max = h.nrow_max;
+    dsph.npw = npw;
+    dsph.ncol = ncol;
+    dsph.nrow = nrow;
+    dsph.col = col;
+    dsph.colstart = cs;
+    dsph.row = row;
+    return LL_OK;
+  }
+
+  // batch vectors: PH uses [R | X | v_{j-1}], NH uses [v_j w_j | XV XW | v_{j-1} w_{j-1}]
+  long vq() const { return (long)nks_ * nbnd_ * hq_.npw_pad; }
+  cplx<T>* R() { return vecs_; }
+  cplx<T>* X() { return vecs_ + vq(); }
+  cplx<T>* Vp() { return vecs_ + 2 * vq(); }
+  cplx<T>* Vc() { return vecs_; }
+  cplx<T>* Wc() { return vecs_ + vq(); }
+  cplx<T>* XV() { return vecs_ + 2 * vq(); }
+  cplx<T>* XW() { return vecs_ + 3 * vq(); }
+  cplx<T>* VpNH() { return vecs_ + 4 * vq(); }
+  cplx<T>* Wp() { return vecs_ + 5 * vq(); }
+
+  cudaStream_t st_ = nullptr;
+  int N_ = 0, nks_ = 0, nbnd_ = 0, nproj_ = 0, approx_ = 0, flavour_ = 0, cap_ = 0, nvec_ = 1, ngroups_ = 1;
+  int cb_ncol_ = 0, steps_ = 0, spec_cap_ = 0, last_ng_ = 1;
+  bool stopped_ = false;
+  Profiler prof_;
+  double omega_ = 0, q_[3] = {0, 0, 0}, tol_ = 0;
+  HostSphere hk_, hq_;
+  SphereDev dk_{}, dq_{};
+  std::vector<void*> ptrs_;
+  size_t bytes_ = 0;
+  T *whart_ = nullptr, *kin_ = nullptr, *vloc_ = nullptr, *fxc_ = nullptr;
+  double *rho_ = nullptr, *eps_ = nullptr, *dij_ = nullptr, *part_ = nullptr, *beta_ = nullptr;
+  cplx<T> *uk_ = nullptr, *ukq_ = nullptr, *bkq_ = nullptr, *ur_ = nullptr, *cbuf_ = nullptr, *nprt_ = nullptr;
+  cplx<T> *nr_ = nullptr, *ng_ = nullptr, *vpr_ = nullptr, *tbuf_ = nullptr, *y_ = nullptr, *vecs_ = nullptr;
+  cplx<T>* scratch_ = nullptr;
+  cplx<double> *spart_ = nullptr, *gamma_ = nullptr, *z_ = nullptr, *zpart_ = nullptr, *spec_out_ = nullptr;
+  double* spec_w_ = nullptr;
+  int *map_ = nullptr, *err_ = nullptr;
+};
+
+}  // namespace ll

@@ -1,0 +1,40 @@
+// Shared device types for the Liouville-Lanczos kernels (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ll {
+
+template <typename T> struct cplx { T x, y; };
+
+template <typename T> __host__ __device__ __forceinline__ cplx<T> mk(T a, T b) { cplx<T> r; r.x = a; r.y = b; return r; }
+template <typename T> __host__ __device__ __forceinline__ cplx<T> operator+(cplx<T> a, cplx<T> b) { return mk(a.x + b.x, a.y + b.y); }
+template <typename T> __host__ __device__ __forceinline__ cplx<T> operator-(cplx<T> a, cplx<T> b) { return mk(a.x - b.x, a.y - b.y); }
+template <typename T> __host__ __device__ __forceinline__ cplx<T> operator*(cplx<T> a, T s) { return mk(a.x * s, a.y * s); }
+template <typename T> __host__ __device__ __forceinline__ cplx<T> cmul(cplx<T> a, cplx<T> b) {
+  return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// conj(a) * b
+template <typename T> __host__ __device__ __forceinline__ cplx<T> cjmul(cplx<T> a, cplx<T> b) {
+  return mk(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+template <typename T> __host__ __device__ __forceinline__ cplx<T> czero() { return mk(T(0), T(0)); }
+
+// Offsets of the twiddle table of each supported grid side N in the per-precision table of
+// W_N^e = exp(-2 pi i e / N), e = 0..N-1, laid out back to back.
+template <int N> struct TwOff;
+template <> struct TwOff<12> { static constexpr int v = 0; };
+template <> struct TwOff<16> { static constexpr int v = 12; };
+template <> struct TwOff<18> { static constexpr int v = 28; };
+template <> struct TwOff<24> { static constexpr int v = 46; };
+template <> struct TwOff<32> { static constexpr int v = 70; };
+template <> struct TwOff<36> { static constexpr int v = 102; };
+template <> struct TwOff<48> { static constexpr int v = 138; };
+constexpr int kTwTotal = 186;
+constexpr int kGridSides[] = {12, 16, 18, 24, 32, 36, 48};
+
+// Device status word: the kernels never trap; a detected fault sets a code here and the
+// host turns it into an ll_status after the call.
+enum DevErr : int { DEV_OK = 0, DEV_NOTPD = 1, DEV_BREAKDOWN = 2, DEV_BOUNDS = 3 };
+
+}  // namespace ll

@@ -1,0 +1,172 @@
+// C ABI of libll.so: argument checks, error strings, dispatch to the precision-specific
+// chain (FP64 or FP32).  See include/ll.h for the contract of every entry point.
+#include <string.h>
+
+#include <new>
+#include <string>
+#include <vector>
+
+#include "chain.cuh"
+
+struct ll_handle {
+  ll::ChainBase* chain = nullptr;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+};
+
+namespace {
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+}  // namespace
+
+extern "C" {
+
+const char* ll_last_error(void) { return g_err.c_str(); }
+const char* ll_version(void) { return "ll-gb300 1.0 (sm_103a)"; }
+
+int ll_create(const ll_system_desc* desc, void* stream, ll_handle** out) {
+  if (!desc || !out) return fail(LL_EINVAL, "null descriptor or output");
+  *out = nullptr;
+  if (desc->precision != LL_PREC_FP64 && desc->precision != LL_PREC_FP32) return fail(LL_EINVAL, "bad precision");
+  ll_handle* h = new (std::nothrow) ll_handle();
+  if (!h) return fail(LL_ENOMEM, "host allocation");
+  h->stream = static_cast<cudaStream_t>(stream);
+  cudaGetDevice(&h->device);
+  h->chain = (desc->precision == LL_PREC_FP64) ? ll::make_chain_f64() : ll::make_chain_f32();
+  std::string err;
+  int rc = h->chain->create(desc, h->stream, err);
+  if (rc != LL_OK) {
+    delete h->chain;
+    delete h;
+    return fail(rc, "ll_create: " + err);
+  }
+  *out = h;
+  return LL_OK;
+}
+
+int ll_destroy(ll_handle* h) {
+  if (!h) return LL_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  delete h->chain;
+  delete h;
+  return LL_OK;
+}
+
+int ll_lanczos(ll_handle* h, int n_steps, double* beta, double* gamma, double* z, int* steps_done) {
+  if (!h) return fail(LL_EINVAL, "null handle");
+  std::string err;
+  int rc = h->chain->lanczos(n_steps, beta, gamma, z, steps_done, err);
+  return rc == LL_OK ? LL_OK : fail(rc, "ll_lanczos: " + err);
+}
+
+int ll_lanczos_spectrum(ll_handle* h, int m, const double* omega_ev, int n_omega, double eta_ev, double* chi,
+                        double* eps_inv, double* eps) {
+  if (!h || !omega_ev || n_omega < 1) return fail(LL_EINVAL, "bad spectrum arguments");
+  std::string err;
+  int rc = h->chain->spectrum(m, omega_ev, n_omega, eta_ev, chi, eps_inv, eps, err);
+  return rc == LL_OK ? LL_OK : fail(rc, "ll_lanczos_spectrum: " + err);
+}
+
+int ll_spectrum(const double* beta, const double* gamma, const double* z, int m, double omega_cell, const double* q_cart,
+                const double* omega_ev, int n_omega, double eta_ev, double* chi, double* eps_inv, double* eps,
+                void* stream) {
+  if (!beta || !gamma || !z || m < 1 || !q_cart || !omega_ev || n_omega < 1 || !(omega_cell > 0))
+    return fail(LL_EINVAL, "bad spectrum arguments");
+  const double q2 = q_cart[0] * q_cart[0] + q_cart[1] * q_cart[1] + q_cart[2] * q_cart[2];
+  if (!(q2 > 0)) return fail(LL_EINVAL, "Q = 0");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const double ha = 27.211386245988;
+  std::vector<double> w(n_omega);
+  for (int i = 0; i < n_omega; ++i) w[i] = omega_ev[i] / ha;
+  double *db = nullptr, *dw = nullptr;
+  ll::cplx<double> *dg = nullptr, *dz = nullptr, *dout = nullptr;
+  auto cleanup = [&]() { cudaFree(db); cudaFree(dw); cudaFree(dg); cudaFree(dz); cudaFree(dout); };
+  if (cudaMalloc(&db, m * sizeof(double)) != cudaSuccess || cudaMalloc(&dg, m * sizeof(ll::cplx<double>)) != cudaSuccess ||
+      cudaMalloc(&dz, m * sizeof(ll::cplx<double>)) != cudaSuccess || cudaMalloc(&dw, n_omega * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&dout, 3L * n_omega * sizeof(ll::cplx<double>)) != cudaSuccess) {
+    cleanup();
+    return fail(LL_ENOMEM, "ll_spectrum: device allocation");
+  }
+  cudaMemcpyAsync(db, beta, m * sizeof(double), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(dg, gamma, m * sizeof(ll::cplx<double>), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(dz, z, m * sizeof(ll::cplx<double>), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(dw, w.data(), n_omega * sizeof(double), cudaMemcpyHostToDevice, st);
+  ll::k_spectrum<<<(n_omega + 127) / 128, 128, 0, st>>>(m, db, dg, dz, n_omega, dw, eta_ev / ha, 4.0 / omega_cell,
+                                                         4.0 * 3.14159265358979323846 / q2, dout, dout + n_omega,
+                                                         dout + 2L * n_omega);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) {
+    if (chi) cudaMemcpyAsync(chi, dout, n_omega * sizeof(ll::cplx<double>), cudaMemcpyDeviceToHost, st);
+    if (eps_inv) cudaMemcpyAsync(eps_inv, dout + n_omega, n_omega * sizeof(ll::cplx<double>), cudaMemcpyDeviceToHost, st);
+    if (eps) cudaMemcpyAsync(eps, dout + 2L * n_omega, n_omega * sizeof(ll::cplx<double>), cudaMemcpyDeviceToHost, st);
+    e = cudaStreamSynchronize(st);
+  }
+  cleanup();
+  if (e != cudaSuccess) return fail(LL_ECUDA, std::string("ll_spectrum: ") + cudaGetErrorString(e));
+  return LL_OK;
+}
+
+int ll_apply(ll_handle* h, int upper, const double* x, double* out) {
+  if (!h || !x || !out) return fail(LL_EINVAL, "bad apply arguments");
+  std::string err;
+  int rc = h->chain->apply(upper, x, out, err);
+  return rc == LL_OK ? LL_OK : fail(rc, "ll_apply: " + err);
+}
+
+int ll_get_map(ll_handle* h, int* map_out) {
+  if (!h || !map_out) return fail(LL_EINVAL, "bad arguments");
+  std::string err;
+  int rc = h->chain->get_map(map_out, err);
+  return rc == LL_OK ? LL_OK : fail(rc, "ll_get_map: " + err);
+}
+
+int ll_get_start(ll_handle* h, double* y_out) {
+  if (!h || !y_out) return fail(LL_EINVAL, "bad arguments");
+  std::string err;
+  int rc = h->chain->get_start(y_out, err);
+  return rc == LL_OK ? LL_OK : fail(rc, "ll_get_start: " + err);
+}
+
+int ll_profile(ll_handle* h, int enable) {
+  if (!h) return fail(LL_EINVAL, "null handle");
+  std::string err;
+  int rc = h->chain->profile(enable, err);
+  return rc == LL_OK ? LL_OK : fail(rc, "ll_profile: " + err);
+}
+
+int ll_profile_read(ll_handle* h, double* ms, long long* launches, long long* total) {
+  if (!h) return fail(LL_EINVAL, "null handle");
+  std::string err;
+  int rc = h->chain->profile_read(ms, launches, total, err);
+  return rc == LL_OK ? LL_OK : fail(rc, "ll_profile_read: " + err);
+}
+
+int ll_footprint(const ll_system_desc* d, size_t* bytes) {
+  if (!d || !bytes || !d->npw_k || !d->npw_kq || d->nks < 1 || d->nbnd < 1 || d->nfft < 1)
+    return fail(LL_EINVAL, "bad footprint arguments");
+  const size_t elem = (d->precision == LL_PREC_FP64) ? 16 : 8;
+  int mk = 1, mq = 1;
+  for (int k = 0; k < d->nks; ++k) {
+    mk = d->npw_k[k] > mk ? d->npw_k[k] : mk;
+    mq = d->npw_kq[k] > mq ? d->npw_kq[k] : mq;
+  }
+  const size_t pk = (mk + 3) / 4 * 4, pq = (mq + 3) / 4 * 4;
+  const size_t n3 = (size_t)d->nfft * d->nfft * d->nfft;
+  const size_t nvec = (d->flavour == LL_FLAVOUR_NH) ? 2 : 1;
+  const size_t vq = (size_t)d->nks * d->nbnd * pq;
+  const size_t orb = (size_t)d->nks * d->nbnd;
+  // columns per sphere are at most the sphere size; bounded by pq for the estimate
+  const size_t cb = nvec * orb * d->nfft * pq;
+  const size_t ngroups = (4 * 152 + d->nfft - 1) / d->nfft;
+  size_t b = elem * (vq * (3 * nvec + nvec + 2) + orb * pk + orb * n3 + cb + ngroups * n3 + 3 * n3 +
+                     (size_t)d->nks * d->nproj * pq);
+  b += (elem / 2) * (2 * n3 + (size_t)d->nks * pq) + 8 * n3 + 40 * (size_t)(d->max_steps + 2) * (d->nks + 2);
+  *bytes = b;
+  return LL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,234 @@
+"""Python binding of libll.so (ctypes): argument marshalling only.
+
+Every step of the Liouvillian application, the Lanczos recursions and the spectrum runs in
+the library's CUDA kernels; this module converts NumPy arrays to the C ABI of
+include/ll.h and back.  Importing it without the built library raises ImportError: there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libll.so")
+
+LL_OK, LL_EINVAL, LL_ENOMEM, LL_EBREAKDOWN, LL_ENOTPD, LL_ETIMEOUT, LL_ECUDA = 0, 1, 2, 3, 4, 5, 6
+LL_PENDING, LL_ENOTFOUND, LL_EUNSUPPORTED = 7, 8, 9
+APPROX = {"ipa": 0, "rpa": 1, "tddft": 2}
+FLAVOUR = {"ph": 0, "nh": 1}
+PRECISION = {"fp64": 0, "fp32": 1}
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int)
+
+
+class LLError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class SystemDesc(C.Structure):
+    _fields_ = [
+        ("lattice", (C.c_double * 3) * 3), ("nfft", C.c_int), ("nks", C.c_int), ("nbnd", C.c_int),
+        ("nproj", C.c_int), ("q_cart", C.c_double * 3), ("kcart", _dp), ("npw_k", _ip), ("miller_k", _ip),
+        ("npw_kq", _ip), ("miller_kq", _ip), ("u_k", _dp), ("u_kq", _dp), ("eps_k", _dp), ("vloc_r", _dp),
+        ("rho_r", _dp), ("beta_kq", _dp), ("dij", _dp), ("approx", C.c_int), ("flavour", C.c_int),
+        ("precision", C.c_int), ("max_steps", C.c_int),
+    ]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libll.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+    lib = C.CDLL(LIB_PATH)
+    vp = C.c_void_p
+    sig = {
+        "ll_create": (C.c_int, [C.POINTER(SystemDesc), vp, C.POINTER(vp)]),
+        "ll_destroy": (C.c_int, [vp]),
+        "ll_lanczos": (C.c_int, [vp, C.c_int, _dp, _dp, _dp, _ip]),
+        "ll_lanczos_spectrum": (C.c_int, [vp, C.c_int, _dp, C.c_int, C.c_double, _dp, _dp, _dp]),
+        "ll_spectrum": (C.c_int, [_dp, _dp, _dp, C.c_int, C.c_double, _dp, _dp, C.c_int, C.c_double, _dp, _dp, _dp, vp]),
+        "ll_apply": (C.c_int, [vp, C.c_int, _dp, _dp]),
+        "ll_get_map": (C.c_int, [vp, _ip]),
+        "ll_get_start": (C.c_int, [vp, _dp]),
+        "ll_footprint": (C.c_int, [C.POINTER(SystemDesc), C.POINTER(C.c_size_t)]),
+        "ll_profile": (C.c_int, [vp, C.c_int]),
+        "ll_profile_read": (C.c_int, [vp, _dp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
+        "ll_last_error": (C.c_char_p, []),
+        "ll_version": (C.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype, f.argtypes = res, args
+    return lib
+
+
+_lib = _load()
+EXPORTS = ("ll_create", "ll_destroy", "ll_lanczos", "ll_lanczos_spectrum", "ll_spectrum", "ll_apply",
+           "ll_get_map", "ll_get_start", "ll_footprint", "ll_profile", "ll_profile_read", "ll_last_error",
+           "ll_version")
+PROF_CLASSES = ("zinv", "xy1", "hxc", "xy2", "zfwd", "proj", "update")
+
+
+def version() -> str:
+    return _lib.ll_version().decode()
+
+
+def _check(rc: int):
+    if rc != LL_OK:
+        raise LLError(rc, _lib.ll_last_error().decode())
+
+
+def _d(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _i(a):
+    return a.ctypes.data_as(_ip)
+
+
+def _cat_complex(blocks) -> np.ndarray:
+    return np.ascontiguousarray(np.concatenate([np.ascontiguousarray(b, dtype=np.complex128).ravel() for b in blocks]))
+
+
+class Chain:
+    """One Lanczos chain resident on the device (ll_create ... ll_destroy)."""
+
+    def __init__(self, *, lattice, nfft, kcart, miller_k, miller_kq, u_k, u_kq, eps_k, vloc_r, rho_r,
+                 beta_kq=None, dij=None, q_cart, approx="tddft", flavour="ph", precision="fp64",
+                 max_steps=1000, stream=None):
+        nks = len(miller_k)
+        nbnd = int(u_k[0].shape[0])
+        nproj = int(beta_kq[0].shape[0]) if beta_kq is not None and len(beta_kq) and beta_kq[0].shape[0] else 0
+        self._keep = dict(
+            kcart=np.ascontiguousarray(kcart, dtype=np.float64),
+            npw_k=np.array([len(m) for m in miller_k], dtype=np.int32),
+            miller_k=np.ascontiguousarray(np.concatenate(miller_k), dtype=np.int32),
+            npw_kq=np.array([len(m) for m in miller_kq], dtype=np.int32),
+            miller_kq=np.ascontiguousarray(np.concatenate(miller_kq), dtype=np.int32),
+            u_k=_cat_complex(u_k), u_kq=_cat_complex(u_kq),
+            eps_k=np.ascontiguousarray(eps_k, dtype=np.float64),
+            vloc_r=np.ascontiguousarray(vloc_r, dtype=np.float64),
+            rho_r=np.ascontiguousarray(rho_r, dtype=np.float64),
+            beta_kq=_cat_complex(beta_kq) if nproj else np.zeros(2),
+            dij=np.ascontiguousarray(dij if nproj else np.zeros(1), dtype=np.float64),
+        )
+        k = self._keep
+        d = SystemDesc()
+        for i in range(3):
+            for j in range(3):
+                d.lattice[i][j] = float(lattice[i][j])
+            d.q_cart[i] = float(q_cart[i])
+        d.nfft, d.nks, d.nbnd, d.nproj = int(nfft), nks, nbnd, nproj
+        d.kcart, d.npw_k, d.miller_k = _d(k["kcart"]), _i(k["npw_k"]), _i(k["miller_k"])
+        d.npw_kq, d.miller_kq = _i(k["npw_kq"]), _i(k["miller_kq"])
+        d.u_k, d.u_kq, d.eps_k = _d(k["u_k"].view(np.float64)), _d(k["u_kq"].view(np.float64)), _d(k["eps_k"])
+        d.vloc_r, d.rho_r = _d(k["vloc_r"]), _d(k["rho_r"])
+        d.beta_kq = _d(k["beta_kq"].view(np.float64)) if nproj else None
+        d.dij = _d(k["dij"])
+        d.approx, d.flavour, d.precision = APPROX[approx], FLAVOUR[flavour], PRECISION[precision]
+        d.max_steps = int(max_steps)
+        self.desc = d
+        self.nks, self.nbnd, self.max_steps = nks, nbnd, int(max_steps)
+        self.npw_kq = k["npw_kq"].copy()
+        self.lattice = np.asarray(lattice, dtype=np.float64)
+        self.q_cart = np.asarray(q_cart, dtype=np.float64)
+        h = C.c_void_p()
+        _check(_lib.ll_create(C.byref(d), C.c_void_p(stream) if stream else None, C.byref(h)))
+        self._h = h
+        self.steps = 0
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.ll_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def lanczos(self, n_steps: int):
+        """Runs n_steps more steps; returns (beta, gamma, z) of every step so far."""
+        cap = self.max_steps
+        beta = np.zeros(cap)
+        gamma = np.zeros(cap, dtype=np.complex128)
+        z = np.zeros(cap, dtype=np.complex128)
+        done = C.c_int(0)
+        rc = _lib.ll_lanczos(self._h, int(n_steps), _d(beta), _d(gamma.view(np.float64)), _d(z.view(np.float64)),
+                             C.byref(done))
+        self.steps = done.value
+        if rc != LL_OK:
+            err = LLError(rc, _lib.ll_last_error().decode())
+            err.partial = (beta[: done.value], gamma[: done.value], z[: done.value])
+            raise err
+        return beta[: done.value].copy(), gamma[: done.value].copy(), z[: done.value].copy()
+
+    def spectrum(self, omega_ev, eta_ev: float, m: int = 0):
+        w = np.ascontiguousarray(omega_ev, dtype=np.float64)
+        out = [np.zeros(len(w), dtype=np.complex128) for _ in range(3)]
+        _check(_lib.ll_lanczos_spectrum(self._h, int(m), _d(w), len(w), float(eta_ev),
+                                        *[_d(o.view(np.float64)) for o in out]))
+        return tuple(out)
+
+    def _split(self, flat):
+        out, pos = [], 0
+        for n in self.npw_kq:
+            out.append(flat[pos:pos + self.nbnd * n].reshape(self.nbnd, n))
+            pos += self.nbnd * n
+        return out
+
+    def apply(self, x, upper: bool):
+        xin = _cat_complex(x)
+        out = np.zeros_like(xin)
+        _check(_lib.ll_apply(self._h, int(bool(upper)), _d(xin.view(np.float64)), _d(out.view(np.float64))))
+        return self._split(out)
+
+    def index_map(self):
+        m = np.zeros(int(self.npw_kq.sum()), dtype=np.int32)
+        _check(_lib.ll_get_map(self._h, _i(m)))
+        out, pos = [], 0
+        for n in self.npw_kq:
+            out.append(m[pos:pos + n].copy())
+            pos += n
+        return out
+
+    def start_vector(self):
+        y = np.zeros(self.nbnd * int(self.npw_kq.sum()), dtype=np.complex128)
+        _check(_lib.ll_get_start(self._h, _d(y.view(np.float64))))
+        return self._split(y)
+
+    def profile(self, enable: bool):
+        _check(_lib.ll_profile(self._h, int(bool(enable))))
+
+    def profile_read(self):
+        """({class: device ms}, {class: launches}, total launches) since profile(True)."""
+        ms = np.zeros(len(PROF_CLASSES))
+        n = (C.c_longlong * len(PROF_CLASSES))()
+        tot = C.c_longlong(0)
+        _check(_lib.ll_profile_read(self._h, _d(ms), n, C.byref(tot)))
+        return dict(zip(PROF_CLASSES, ms.tolist())), dict(zip(PROF_CLASSES, list(n))), int(tot.value)
+
+    def footprint(self) -> int:
+        b = C.c_size_t(0)
+        _check(_lib.ll_footprint(C.byref(self.desc), C.byref(b)))
+        return int(b.value)
+
+
+def spectrum(beta, gamma, z, omega_cell, q_cart, omega_ev, eta_ev, stream=None):
+    """chi, eps^-1, eps from caller-held coefficients (ll_spectrum)."""
+    b = np.ascontiguousarray(beta, dtype=np.float64)
+    g = np.ascontiguousarray(gamma, dtype=np.complex128)
+    zz = np.ascontiguousarray(z, dtype=np.complex128)
+    q = np.ascontiguousarray(q_cart, dtype=np.float64)
+    w = np.ascontiguousarray(omega_ev, dtype=np.float64)
+    out = [np.zeros(len(w), dtype=np.complex128) for _ in range(3)]
+    _check(_lib.ll_spectrum(_d(b), _d(g.view(np.float64)), _d(zz.view(np.float64)), len(b), float(omega_cell),
+                            _d(q), _d(w), len(w), float(eta_ev), *[_d(o.view(np.float64)) for o in out],
+                            C.c_void_p(stream) if stream else None))
+    return tuple(out)

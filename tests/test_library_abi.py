@@ -1,0 +1,78 @@
+"""The C-ABI library builds, loads without a GPU and exports every declared entry point;
+host-side input validation (no kernel runs) rejects malformed systems."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as w
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def ll():
+    from paper_2111_06623_gb300.build import build_library
+    build_library()
+    from paper_2111_06623_gb300 import ll as mod
+    return mod
+
+
+def test_exports_match_header(ll):
+    hdr = open(os.path.join(ROOT, "include", "ll.h")).read()
+    declared = set(re.findall(r"^\s*(?:int|const char\*)\s+(ll_\w+)\s*\(", hdr, flags=re.M))
+    assert declared, "no declarations parsed"
+    lib = ctypes.CDLL(ll.LIB_PATH)
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert declared == set(ll.EXPORTS)
+    assert "sm_103a" in ll.version()
+
+
+def _desc_args(b):
+    s = b.spec
+    return dict(lattice=s.lattice, nfft=s.nfft, kcart=b.kcart, miller_k=list(b.miller_k),
+                miller_kq=list(b.miller_kq), u_k=b.u_k, u_kq=b.u_kq, eps_k=b.eps_k, vloc_r=b.vloc_r,
+                rho_r=b.rho_r, beta_kq=b.beta_kq, dij=b.dij, q_cart=s.q_cart, max_steps=10)
+
+
+def test_rejects_unsorted_sphere(ll):
+    b = w.get_bundle(w.config_tiny())
+    args = _desc_args(b)
+    m = args["miller_kq"][0].copy()
+    m[[0, 1]] = m[[1, 0]]
+    args["miller_kq"][0] = m
+    with pytest.raises(ll.LLError) as e:
+        ll.Chain(**args)
+    assert e.value.code == ll.LL_EINVAL and "lexicographic" in str(e.value)
+
+
+def test_rejects_q_on_reciprocal_lattice(ll):
+    b = w.get_bundle(w.config_tiny())
+    args = _desc_args(b)
+    args["q_cart"] = b.spec.bvec[0].copy()
+    with pytest.raises(ll.LLError) as e:
+        ll.Chain(**args)
+    assert e.value.code == ll.LL_EINVAL and "reciprocal" in str(e.value)
+
+
+def test_rejects_unsupported_grid(ll):
+    b = w.get_bundle(w.config_tiny())
+    args = _desc_args(b)
+    args["nfft"] = 20
+    with pytest.raises(ll.LLError) as e:
+        ll.Chain(**args)
+    assert e.value.code == ll.LL_EUNSUPPORTED
+
+
+def test_rejects_sphere_too_large_for_grid(ll):
+    b = w.get_bundle(w.config_tiny())
+    args = _desc_args(b)
+    m = args["miller_k"][0].copy()
+    m[-1, 2] = m[-1, 2] + 40
+    args["miller_k"][0] = m
+    with pytest.raises(ll.LLError) as e:
+        ll.Chain(**args)
+    assert e.value.code == ll.LL_EINVAL

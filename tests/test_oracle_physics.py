@@ -109,7 +109,7 @@ def test_single_transition_spectrum():
 
 def test_fsum_exact_moment_local_potential():
     """With a local potential and Q on the k-mesh, the first frequency moment of chi is
-    n |Q|^2 (Eq. 4 / Thomas-Reiche-Kuhn): (4/Omega)(y, D y) = n Q^2, up to the plane-wave
+    n |Q|^2 (Eq. 6, Thomas-Reiche-Kuhn): (4/Omega)(y, D y) = n Q^2, up to the plane-wave
     truncation of e^{iQr} u (1e-7 of the norm at 30 Ry)."""
     spec = w.config_local_insulator()
     spec.ecut_ry, spec.nfft = 30.0, 20
@@ -138,7 +138,7 @@ def test_nh_and_ph_spectra_converge_together(tiny):
 
 
 def test_hartree_kernel_and_fxc_tables(tiny):
-    """The response kernel's ingredients against their definitions (Eq. 10, ALDA)."""
+    """The response kernel's ingredients against their definitions (Eq. 13, ALDA)."""
     from oracle import xc
     sys = System(tiny, "tddft")
     n = sys.n
@@ -148,7 +148,7 @@ def test_hartree_kernel_and_fxc_tables(tiny):
         assert np.isclose(sys.whart[idx], 4 * np.pi / (qg @ qg), rtol=1e-14)
     assert np.allclose(sys.fxc, xc.fxc(tiny.rho_r), rtol=0, atol=0)
     assert np.all(System(tiny, "rpa").fxc == 0)
-    # Eq. 21 normalisation: int_cell n'[y] dr = 4 (1/N_k) sum <u_vk|y_vk> = 4 (y, y)
+    # Eq. 27 normalisation: int_cell n'[y] dr = 4 (1/N_k) sum <u_vk|y_vk> = 4 (y, y)
     # because y = P_c u and P_c is a projector
     y = sys.starting_vector()
     nr = sys.response_density(y)

@@ -217,7 +217,7 @@ class _Runner:
     def __init__(self, work: float):
         self.pool = None
         ncpu = os.cpu_count() or 1
-        if work > 2e9 and ncpu > 1:
+        if work > 1e11 and ncpu > 1:
             import multiprocessing as mp
             keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
             saved = {k: os.environ.get(k) for k in keys}
