@@ -122,7 +122,7 @@ def _xy_flops_per_apply(b, with_k: bool) -> float:
 
 def _time_chain(b, precision, steps, warmup, stream, profile=False):
     import torch
-    ch = _chain(b, precision, warmup + steps, stream)
+    ch = _chain(b, precision, warmup + steps + 64, stream)
     ch.lanczos(warmup)
     torch.cuda.synchronize()
     if profile:

