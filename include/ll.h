@@ -106,6 +106,26 @@ int ll_spectrum(const double* beta, const double* gamma, const double* z, int m,
                 const double* q_cart, const double* omega_ev, int n_omega, double eta_ev, double* chi,
                 double* eps_inv, double* eps, void* stream);
 
+/* Allocation-free variant of ll_spectrum, for callers that cannot allocate device memory
+ * while they run: services whose memory pool has already reserved the GPU's memory, and
+ * latency-critical loops where a cudaMalloc/cudaFree (which may synchronise the device and
+ * stall work on other streams) is not acceptable.  The paper has no counterpart; it is an
+ * engineering addition.  Same arguments and results as ll_spectrum; the device staging of
+ * the coefficients, the frequency grid and the three output arrays uses one static device
+ * array compiled into the library (about 1.6 MB, held by every GPU that loads the library
+ * until the process exits), so it accepts at most LL_SPECTRUM_STATIC_MAX_COEF coefficients
+ * and LL_SPECTRUM_STATIC_MAX_OMEGA frequencies and returns LL_EINVAL with a message beyond
+ * that.  It calls no device allocator.  The first call on a device looks up that device's
+ * address of the array (make that first call before any stream capture).  Every call on a
+ * device shares the one array and leaves its contents behind: calls whose work may overlap on
+ * the GPU (other host threads, other streams) race and must be serialised by the caller.
+ * Returns after the results are on the host. */
+#define LL_SPECTRUM_STATIC_MAX_COEF 16384
+#define LL_SPECTRUM_STATIC_MAX_OMEGA 16384
+int ll_spectrum_static(const double* beta, const double* gamma, const double* z, int m, double omega_cell,
+                       const double* q_cart, const double* omega_ev, int n_omega, double eta_ev, double* chi,
+                       double* eps_inv, double* eps, void* stream);
+
 /* One application of the SBR operator to a batch (Eqs. 24-28): out = (D + K) x when
  * upper != 0 (K omitted for IPA), out = D x otherwise, with D = P_c (H_{k+Q} - eps_{vk})
  * and the P_c of Eq. 16 on the output.  x and out are complex batches laid out per k as

@@ -2,6 +2,7 @@
 // chain (FP64 or FP32).  See include/ll.h for the contract of every entry point.
 #include <string.h>
 
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -107,6 +108,98 @@ int ll_spectrum(const double* beta, const double* gamma, const double* z, int m,
   }
   cleanup();
   if (e != cudaSuccess) return fail(LL_ECUDA, std::string("ll_spectrum: ") + cudaGetErrorString(e));
+  return LL_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Allocation-free spectrum.  The device staging area lives in one file-scope array that
+// every GPU loading the library holds until exit; host code reaches it only through the
+// address cudaGetSymbolAddress returns for the current device (the symbol itself is a
+// host-side stand-in).  Layout: beta[MAX_COEF] | gamma[MAX_COEF] | z[MAX_COEF] |
+// omega[MAX_OMEGA] | chi, eps_inv, eps [MAX_OMEGA each].
+namespace {
+constexpr int kStaticMaxCoef = LL_SPECTRUM_STATIC_MAX_COEF;
+constexpr int kStaticMaxOmega = LL_SPECTRUM_STATIC_MAX_OMEGA;
+constexpr size_t kOffGamma = sizeof(double) * kStaticMaxCoef;
+constexpr size_t kOffZ = kOffGamma + sizeof(ll::cplx<double>) * kStaticMaxCoef;
+constexpr size_t kOffW = kOffZ + sizeof(ll::cplx<double>) * kStaticMaxCoef;
+constexpr size_t kOffOut = kOffW + sizeof(double) * kStaticMaxOmega;
+constexpr size_t kStaticBytes = kOffOut + 3 * sizeof(ll::cplx<double>) * kStaticMaxOmega;
+
+static __device__ __align__(256) unsigned char g_spectrum_scratch[kStaticBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+unsigned char* g_static_addr[kMaxDevices] = {nullptr};
+
+// Device address of the staging array on the current device, looked up once per device.
+int static_scratch(unsigned char** out, std::string& err) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) { err = std::string("cudaGetDevice: ") + cudaGetErrorString(e); return LL_ECUDA; }
+  if (dev < 0 || dev >= kMaxDevices) { err = "device ordinal out of range"; return LL_EUNSUPPORTED; }
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_spectrum_scratch);
+    if (e != cudaSuccess || !p) {
+      err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+      return LL_ECUDA;
+    }
+    g_static_addr[dev] = static_cast<unsigned char*>(p);
+  }
+  *out = g_static_addr[dev];
+  return LL_OK;
+}
+
+__global__ void k_ev_to_ha(int n, double* w) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) w[i] = w[i] / 27.211386245988;
+}
+}  // namespace
+
+int ll_spectrum_static(const double* beta, const double* gamma, const double* z, int m, double omega_cell,
+                       const double* q_cart, const double* omega_ev, int n_omega, double eta_ev, double* chi,
+                       double* eps_inv, double* eps, void* stream) {
+  if (!beta || !gamma || !z || m < 1 || !q_cart || !omega_ev || n_omega < 1 || !(omega_cell > 0))
+    return fail(LL_EINVAL, "bad spectrum arguments");
+  if (m > kStaticMaxCoef)
+    return fail(LL_EINVAL, "ll_spectrum_static: " + std::to_string(m) + " coefficients exceed the static limit of " +
+                               std::to_string(kStaticMaxCoef));
+  if (n_omega > kStaticMaxOmega)
+    return fail(LL_EINVAL, "ll_spectrum_static: " + std::to_string(n_omega) +
+                               " frequencies exceed the static limit of " + std::to_string(kStaticMaxOmega));
+  const double q2 = q_cart[0] * q_cart[0] + q_cart[1] * q_cart[1] + q_cart[2] * q_cart[2];
+  if (!(q2 > 0)) return fail(LL_EINVAL, "Q = 0");
+  std::string err;
+  unsigned char* base = nullptr;
+  int rc = static_scratch(&base, err);
+  if (rc != LL_OK) return fail(rc, "ll_spectrum_static: " + err);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  double* db = reinterpret_cast<double*>(base);
+  ll::cplx<double>* dg = reinterpret_cast<ll::cplx<double>*>(base + kOffGamma);
+  ll::cplx<double>* dz = reinterpret_cast<ll::cplx<double>*>(base + kOffZ);
+  double* dw = reinterpret_cast<double*>(base + kOffW);
+  ll::cplx<double>* dout = reinterpret_cast<ll::cplx<double>*>(base + kOffOut);
+  cudaError_t e = cudaMemcpyAsync(db, beta, m * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dg, gamma, m * sizeof(ll::cplx<double>), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dz, z, m * sizeof(ll::cplx<double>), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dw, omega_ev, n_omega * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    k_ev_to_ha<<<(n_omega + 127) / 128, 128, 0, st>>>(n_omega, dw);
+    ll::k_spectrum<<<(n_omega + 127) / 128, 128, 0, st>>>(m, db, dg, dz, n_omega, dw, eta_ev / 27.211386245988,
+                                                           4.0 / omega_cell, 4.0 * 3.14159265358979323846 / q2, dout,
+                                                           dout + kStaticMaxOmega, dout + 2L * kStaticMaxOmega);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && chi)
+    e = cudaMemcpyAsync(chi, dout, n_omega * sizeof(ll::cplx<double>), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && eps_inv)
+    e = cudaMemcpyAsync(eps_inv, dout + kStaticMaxOmega, n_omega * sizeof(ll::cplx<double>), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && eps)
+    e = cudaMemcpyAsync(eps, dout + 2L * kStaticMaxOmega, n_omega * sizeof(ll::cplx<double>), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(LL_ECUDA, std::string("ll_spectrum_static: ") + cudaGetErrorString(e));
   return LL_OK;
 }
 

@@ -52,6 +52,8 @@ def _load():
         "ll_lanczos": (C.c_int, [vp, C.c_int, _dp, _dp, _dp, _ip]),
         "ll_lanczos_spectrum": (C.c_int, [vp, C.c_int, _dp, C.c_int, C.c_double, _dp, _dp, _dp]),
         "ll_spectrum": (C.c_int, [_dp, _dp, _dp, C.c_int, C.c_double, _dp, _dp, C.c_int, C.c_double, _dp, _dp, _dp, vp]),
+        "ll_spectrum_static": (C.c_int, [_dp, _dp, _dp, C.c_int, C.c_double, _dp, _dp, C.c_int, C.c_double, _dp,
+                                         _dp, _dp, vp]),
         "ll_apply": (C.c_int, [vp, C.c_int, _dp, _dp]),
         "ll_get_map": (C.c_int, [vp, _ip]),
         "ll_get_start": (C.c_int, [vp, _dp]),
@@ -68,8 +70,8 @@ def _load():
 
 
 _lib = _load()
-EXPORTS = ("ll_create", "ll_destroy", "ll_lanczos", "ll_lanczos_spectrum", "ll_spectrum", "ll_apply",
-           "ll_get_map", "ll_get_start", "ll_footprint", "ll_profile", "ll_profile_read", "ll_last_error",
+EXPORTS = ("ll_create", "ll_destroy", "ll_lanczos", "ll_lanczos_spectrum", "ll_spectrum", "ll_spectrum_static",
+           "ll_apply", "ll_get_map", "ll_get_start", "ll_footprint", "ll_profile", "ll_profile_read", "ll_last_error",
            "ll_version")
 PROF_CLASSES = ("zinv", "xy1", "hxc", "xy2", "zfwd", "proj", "update")
 
@@ -231,4 +233,23 @@ def spectrum(beta, gamma, z, omega_cell, q_cart, omega_ev, eta_ev, stream=None):
     _check(_lib.ll_spectrum(_d(b), _d(g.view(np.float64)), _d(zz.view(np.float64)), len(b), float(omega_cell),
                             _d(q), _d(w), len(w), float(eta_ev), *[_d(o.view(np.float64)) for o in out],
                             C.c_void_p(stream) if stream else None))
+    return tuple(out)
+
+
+SPECTRUM_STATIC_MAX_COEF = 16384
+SPECTRUM_STATIC_MAX_OMEGA = 16384
+
+
+def spectrum_static(beta, gamma, z, omega_cell, q_cart, omega_ev, eta_ev, stream=None):
+    """ll_spectrum_static: the same results as spectrum() without any device allocation,
+    staged through the library's static device array (limits SPECTRUM_STATIC_MAX_*)."""
+    b = np.ascontiguousarray(beta, dtype=np.float64)
+    g = np.ascontiguousarray(gamma, dtype=np.complex128)
+    zz = np.ascontiguousarray(z, dtype=np.complex128)
+    q = np.ascontiguousarray(q_cart, dtype=np.float64)
+    w = np.ascontiguousarray(omega_ev, dtype=np.float64)
+    out = [np.zeros(len(w), dtype=np.complex128) for _ in range(3)]
+    _check(_lib.ll_spectrum_static(_d(b), _d(g.view(np.float64)), _d(zz.view(np.float64)), len(b),
+                                   float(omega_cell), _d(q), _d(w), len(w), float(eta_ev),
+                                   *[_d(o.view(np.float64)) for o in out], C.c_void_p(stream) if stream else None))
     return tuple(out)
