@@ -163,6 +163,57 @@ def _oracle_sample(b, nk_sample: int, nsteps: int):
     return (time.perf_counter() - t0) / nsteps
 
 
+def _serving(b_kb, n_jobs: int, seed: int = 7):
+    """A Poisson stream (mean 20 jobs/s) of Lanczos jobs through the request loop: the small
+    two-atom workload at four momentum transfers and the KB workload, 500-1500 pseudo-Hermitian
+    FP32 steps each, admission under a 150 GB HBM budget.  Returns throughput and the p50/p99
+    time from submission to the finished spectrum."""
+    import workloads as w
+    from paper_2111_06623_gb300 import ll
+    rng = np.random.default_rng(seed)
+    pool = []
+    qr = np.random.default_rng(5)
+    for _ in range(4):
+        spec = w.config_small()
+        d = qr.normal(size=3)
+        spec.q_cart = qr.uniform(0.05, 0.3) * (2 * np.pi / w.A_LAT) * d / np.linalg.norm(d)
+        spec.name = "fcc2_10ry_18_q%03d" % int(1000 * np.linalg.norm(spec.q_cart))
+        pool.append(w.get_bundle(spec))
+    pool.append(b_kb)
+    wgrid = np.linspace(0.0, 40.0, 4001)
+    srv = ll.Server(hbm_budget_bytes=150 << 30, max_slots=16, chunk=32)
+    t_arr = np.cumsum(rng.exponential(1.0 / 20.0, size=n_jobs))
+    picks = rng.integers(0, len(pool), size=n_jobs)
+    steps = rng.integers(500, 1501, size=n_jobs)
+    ids, t0 = [], time.perf_counter()
+    for ta, pk, ns in zip(t_arr, picks, steps):
+        while time.perf_counter() - t0 < ta:
+            time.sleep(0.001)
+        bb = pool[pk]
+        s = bb.spec
+        ids.append(srv.submit(int(ns), wgrid, 0.1, lattice=s.lattice, nfft=s.nfft, kcart=bb.kcart,
+                              miller_k=bb.miller_k, miller_kq=bb.miller_kq, u_k=bb.u_k, u_kq=bb.u_kq, eps_k=bb.eps_k,
+                              vloc_r=bb.vloc_r, rho_r=bb.rho_r, beta_kq=bb.beta_kq, dij=bb.dij, q_cart=s.q_cart,
+                              approx="tddft", flavour="ph", precision="fp32", max_steps=int(ns)))
+    lat, done = {}, 0
+    while len(lat) < len(ids):
+        for i in ids:
+            if i not in lat:
+                st, r = srv.poll(i)
+                if st in (ll.JOB_DONE, ll.JOB_FAILED):
+                    lat[i] = r["queue_s"] + r["run_s"]
+                    done += r["steps_done"] if st == ll.JOB_DONE else 0
+        time.sleep(0.002)
+    wall = time.perf_counter() - t0
+    peak = srv.stats()["peak"]
+    srv.close()
+    v = np.array(list(lat.values()))
+    return {"jobs": n_jobs, "steps_per_s": done / wall, "p50_s": float(np.percentile(v, 50)),
+            "p99_s": float(np.percentile(v, 99)), "wall_s": wall, "peak_hbm_gb": peak / 2 ** 30,
+            "budget_gb": 150, "slots": 16,
+            "stream": "Poisson 20 jobs/s (seed 7), small cell at 4 Q + KB workload, 500-1500 FP32 PH steps"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -193,6 +244,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--serving-jobs", type=int, default=16)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")
@@ -285,6 +337,8 @@ def main():
         roofline = {"bound": "alu", "kernel": dom, "achieved": None, "peak": peak, "unit": "TFLOP/s",
                     "frac": None, "traffic": None}
 
+    serving = _serving(b, args.serving_jobs) if args.serving_jobs > 0 else None
+
     cpu = None
     if rank == 0:
         nk = 8
@@ -308,7 +362,7 @@ def main():
             "spectrum_err_fp32_vs_fp64_all_steps": spec_err_full,
             "step_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))} if lat else None,
             "kernel_ms": ms_cls, "kernel_launches": launches,
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(total), "clocks": clocks,
+            "roofline": roofline, "serving": serving, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(total), "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

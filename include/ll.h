@@ -141,14 +141,15 @@ int ll_get_start(ll_handle* h, double* y_out);
 
 /* Kernel classes of the per-class device-time profile. */
 enum {
-  LL_PROF_ZINV = 0,     /* sphere -> columns, inverse FFT along axis 3                    */
+  LL_PROF_ZINV = 0,     /* sphere -> columns, inverse FFT along axis 3 (the pseudo-Hermitian
+                           vector update fused in front)                                 */
   LL_PROF_XY1 = 1,      /* per-plane 2D FFTs, V(r) x(r), response density                 */
   LL_PROF_HXC = 2,      /* Hartree + XC response potential of the density                 */
   LL_PROF_XY2 = 3,      /* per-plane forward 2D FFTs of v'(r) u(r)                         */
-  LL_PROF_ZFWD = 4,     /* forward FFT along axis 3, columns -> sphere                    */
-  LL_PROF_PROJ = 5,     /* kinetic - eps, KB projectors, P_c, norm partials               */
-  LL_PROF_UPDATE = 6,   /* Lanczos scalars and vector updates                             */
-  LL_NPROF = 7
+  LL_PROF_ZFWD = 4,     /* forward FFT along axis 3, columns -> sphere, fused with the
+                           kinetic - eps, KB projector and P_c terms and the norm partials */
+  LL_PROF_UPDATE = 5,   /* separate Lanczos update kernels (non-Hermitian), z reduction   */
+  LL_NPROF = 6
 };
 
 /* Starts (enable != 0: counters cleared) or stops recording CUDA events around each
@@ -165,6 +166,53 @@ int ll_footprint(const ll_system_desc* desc, size_t* bytes);
 
 const char* ll_last_error(void);
 const char* ll_version(void);
+
+/* ---- Request loop: continuous batching of chains (an engineering addition; the paper runs
+ * one recursion per momentum transfer, Sec. 3.2).  A scheduler thread admits queued jobs in
+ * arrival order while a slot is free and the job's device footprint fits the HBM budget, runs
+ * every admitted chain on a stream of its own in rounds of `chunk` steps (their kernels
+ * overlap on the GPU), and at a chain's last step evaluates its spectrum on the device and
+ * frees its memory for the next admissions.  A job's results do not depend on the jobs
+ * beside it. */
+typedef struct ll_server ll_server;
+
+enum { LL_JOB_QUEUED = 0, LL_JOB_RUNNING = 1, LL_JOB_DONE = 2, LL_JOB_FAILED = 3 };
+
+typedef struct {
+  ll_system_desc sys;       /* copied at submit; sys.max_steps >= n_steps                   */
+  int n_steps;              /* Lanczos steps of the job                                    */
+  const double* omega_ev;   /* [n_omega] spectrum grid (eV); n_omega = 0: coefficients only */
+  int n_omega;
+  double eta_ev;            /* broadening (eV)                                             */
+} ll_job_desc;
+
+typedef struct {
+  int status;               /* LL_OK, or the error that ended the job                      */
+  int steps_done;
+  double queue_s, run_s;    /* seconds waiting for admission; from admission to the end    */
+  double* beta;             /* optional caller buffers, filled once the job has ended:     */
+  double* gamma;            /*   beta [n_steps]; gamma, z complex [n_steps]                */
+  double* z;
+  double* chi;              /*   chi, eps_inv, eps complex [n_omega]                       */
+  double* eps_inv;
+  double* eps;
+} ll_job_result;
+
+/* hbm_budget_bytes caps the summed device footprint of running chains; max_slots caps their
+ * number.  The scheduler thread uses the device current at this call. */
+int ll_server_create(size_t hbm_budget_bytes, int max_slots, ll_server** out);
+/* Steps queued per chain per round (default 64). */
+int ll_server_set_chunk(ll_server* s, int steps);
+/* Copies the job; LL_ENOMEM when its footprint exceeds the whole budget, LL_EINVAL when the
+ * descriptor is malformed (further checks happen at admission and end the job FAILED). */
+int ll_submit(ll_server* s, const ll_job_desc* job, uint64_t* job_id);
+/* *state = LL_JOB_*; when res is given, fills it (results once the job has ended). */
+int ll_poll(ll_server* s, uint64_t job_id, int* state, ll_job_result* res);
+/* Device bytes held by running chains now and at most so far; running and queued jobs. */
+int ll_server_stats(ll_server* s, size_t* used, size_t* peak, int* running, int* queued);
+const char* ll_server_last_error(void);
+/* Stops the scheduler after its current round; queued jobs end FAILED. */
+int ll_server_destroy(ll_server* s);
 
 #ifdef __cplusplus
 }

@@ -12,7 +12,7 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB_PATH = os.path.join(HERE, "libll.so")
-UNITS = ("ll_api", "ll_f64", "ll_f32")
+UNITS = ("ll_api", "ll_f64", "ll_f32", "ll_server")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]
 

@@ -18,6 +18,11 @@ struct ChainBase {
   virtual ~ChainBase() {}
   virtual int create(const ll_system_desc* d, cudaStream_t st, std::string& err) = 0;
   virtual int lanczos(int n, double* beta, double* gamma, double* z, int* done, std::string& err) = 0;
+  // asynchronous halves of lanczos(): queue n steps on the chain's stream / wait for them and
+  // fetch every coefficient so far
+  virtual int enqueue(int n, std::string& err) = 0;
+  virtual int collect(double* beta, double* gamma, double* z, int* done, std::string& err) = 0;
+  virtual int steps_queued() const = 0;
   virtual int spectrum(int m, const double* w_ev, int nw, double eta_ev, double* chi, double* ei, double* e,
                        std::string& err) = 0;
   virtual int apply(int upper, const double* x, double* out, std::string& err) = 0;
@@ -167,7 +172,12 @@ static inline void recip(const double a[3][3], double b[3][3]) {
   }
 }
 
-template <int N> struct BO { static constexpr int v = (128 / N) < 1 ? 1 : 128 / N; };
+// Orbitals per batch of the per-plane kernel: enough axis-1 lines for the 128 threads when
+// orbital-grid planes are staged (their shared memory is the limit), three rounds otherwise
+// so that the axis-2 passes (a sphere's rows, ~N/3 lines per orbital) also fill the block.
+template <int N, int MODE> struct BO {
+  static constexpr int v = (MODE == XY_PASS1_DENS || MODE == XY_PASS2) ? (128 / N < 1 ? 1 : 128 / N) : 384 / N;
+};
 
 template <typename T>
 class Chain : public ChainBase {
@@ -262,7 +272,7 @@ class Chain : public ChainBase {
         (rc = alloc(&dij_, std::max(1, nproj_))) || (rc = alloc(&vloc_, n3)) || (rc = alloc(&rho_, n3)) ||
         (rc = alloc(&fxc_, n3)) || (rc = alloc(&ur_, (long)nks_ * nbnd_ * n3)) ||
         (rc = alloc(&cbuf_, (long)norb * n * cb_ncol_)) || (rc = alloc(&nprt_, (long)ngroups_ * n3)) ||
-        (rc = alloc(&nr_, n3)) || (rc = alloc(&ng_, n3)) || (rc = alloc(&vpr_, n3)) || (rc = alloc(&tbuf_, nvec_ * vq)) ||
+        (rc = alloc(&nr_, n3)) || (rc = alloc(&ng_, n3)) || (rc = alloc(&vpr_, n3)) ||
         (rc = alloc(&y_, vq)) || (rc = alloc(&map_, (long)nks_ * pq)) || (rc = alloc(&part_, 2L * nks_)) ||
         (rc = alloc(&spart_, (long)nks_)) || (rc = alloc(&vecs_, 3L * nvec_ * vq)) ||
         (rc = alloc(&beta_, cap_ + 2)) || (rc = alloc(&gamma_, cap_ + 2)) || (rc = alloc(&z_, cap_ + 1)) ||
@@ -341,33 +351,40 @@ class Chain : public ChainBase {
     }
     LL_CK(cudaStreamSynchronize(st_));
     steps_ = 0;
+    queued_ = 0;
     return LL_OK;
   }
 
   int lanczos(int n, double* beta, double* gamma, double* z, int* done, std::string& err) override {
-    if (n < 0 || steps_ + n > cap_) { err = "more steps than max_steps"; return LL_EINVAL; }
-    if (stopped_) {
+    int rc = enqueue(n, err);
+    if (rc != LL_OK) {
       if (done) *done = steps_;
-      err = "the chain stopped at a breakdown";
-      return LL_EBREAKDOWN;
+      return rc;
     }
+    return collect(beta, gamma, z, done, err);
+  }
+
+  int steps_queued() const override { return queued_; }
+
+  int enqueue(int n, std::string& err) override {
+    if (n < 0 || queued_ + n > cap_) { err = "more steps than max_steps"; return LL_EINVAL; }
+    if (stopped_) { err = "the chain stopped at a breakdown"; return LL_EBREAKDOWN; }
     int rc;
     const int pq = hq_.npw_pad;
-    const size_t smem_upd = (size_t)nbnd_ * pq * sizeof(cplx<T>) + (size_t)(nbnd_ * nbnd_ + 1) * sizeof(cplx<double>);
-    const size_t smem_nh = 2 * (size_t)nbnd_ * pq * sizeof(cplx<T>) + 2 * (size_t)nbnd_ * nbnd_ * sizeof(cplx<double>);
+    const size_t smem_nh = 2 * (size_t)nbnd_ * pq * sizeof(cplx<T>) + (size_t)nbnd_ * nbnd_ * sizeof(cplx<double>) +
+                           16 * 4 * sizeof(double);
     Coef co{beta_, gamma_, zpart_, err_};
     for (int s = 0; s < n; ++s) {
-      const int j = steps_ + s + 1;
+      const int j = queued_ + s + 1;
       if (flavour_ == LL_FLAVOUR_PH) {
-        if ((rc = set_smem(k_update_ph<T>, smem_upd, err))) return rc;
+        // update of the Lanczos vectors fused with the axis-3 inverse FFT of r_{j+1}
         const int u0 = prof_.mark(st_);
-        k_update_ph<T><<<nks_, 128, smem_upd, st_>>>(j, (j % 2 == 0) ? 1 : 0, nks_, nbnd_, pq, dq_.npw, part_, R(), X(),
-                                                     Vp(), y_, ukq_, co, tol_);
-        prof_.count(LL_PROF_UPDATE);
-        prof_.span(LL_PROF_UPDATE, u0, prof_.mark(st_));
+        if ((rc = launch_zinv_ph(j, err))) return rc;
+        prof_.count(LL_PROF_ZINV);
+        prof_.span(LL_PROF_ZINV, u0, prof_.mark(st_));
         // r_{j+1} is upper when j is odd; the upper half gets D + K
         const int dens = (j % 2 == 1 && approx_ != LL_APPROX_IPA) ? 0 : -1;
-        if ((rc = op(1, R(), X(), dens, err))) return rc;
+        if ((rc = op_rest(1, R(), X(), dens, err))) return rc;
       } else {
         const int upper = (j % 2 == 0) ? 1 : 0;
         // L v_j: D + K on an upper v; L^dag w_j: D + K on a lower w
@@ -385,17 +402,23 @@ class Chain : public ChainBase {
       LL_CK(cudaGetLastError());
     }
     if (n > 0) {
-      k_reduce_z<<<(n + 127) / 128, 128, 0, st_>>>(zpart_, nks_, steps_, steps_ + n, z_);
+      k_reduce_z<<<(n + 127) / 128, 128, 0, st_>>>(zpart_, nks_, queued_, queued_ + n, z_);
       LL_CK(cudaGetLastError());
       prof_.count(LL_PROF_UPDATE);
     }
+    queued_ += n;
+    return LL_OK;
+  }
+
+  int collect(double* beta, double* gamma, double* z, int* done, std::string& err) override {
     int herr[2];
     LL_CK(cudaMemcpyAsync(herr, err_, sizeof(herr), cudaMemcpyDeviceToHost, st_));
     LL_CK(cudaStreamSynchronize(st_));
-    steps_ += n;
+    steps_ = queued_;
     int status = LL_OK;
     if (herr[0] != DEV_OK) {
       steps_ = std::min(steps_, herr[1] - 1);
+      queued_ = steps_;
       status = (herr[0] == DEV_NOTPD) ? LL_ENOTPD : LL_EBREAKDOWN;
       err = (status == LL_ENOTPD) ? "pseudo-Hermitian metric not positive" : "Lanczos breakdown";
       stopped_ = true;
@@ -498,8 +521,15 @@ class Chain : public ChainBase {
     const int e0 = prof_.mark(st_);
     if ((rc = launch_zinv(dq_, in, nvec))) { err = "zinv launch"; return rc; }
     prof_.count(LL_PROF_ZINV);
+    prof_.span(LL_PROF_ZINV, e0, prof_.mark(st_));
+    return op_rest(nvec, in, out, dens_vec, err);
+  }
+
+  // everything after the axis-3 inverse FFT: planes, response potential, axis-3 forward FFT
+  // fused with the per-k projections
+  int op_rest(int nvec, const cplx<T>* in, cplx<T>* out, int dens_vec, std::string& err) {
+    int rc;
     const int e1 = prof_.mark(st_);
-    prof_.span(LL_PROF_ZINV, e0, e1);
     if ((rc = launch_xy(dq_, nvec * nks_ * nbnd_, 0, dens_vec, 0, err))) return rc;
     prof_.count(LL_PROF_XY1);
     int e2 = prof_.mark(st_);
@@ -514,19 +544,63 @@ class Chain : public ChainBase {
       e2 = prof_.mark(st_);
       prof_.span(LL_PROF_XY2, e3, e2);
     }
-    if ((rc = launch_zfwd(nvec))) { err = "zfwd launch"; return rc; }
+    if ((rc = launch_zfwd_proj(nvec, in, out, err))) return rc;
     prof_.count(LL_PROF_ZFWD);
-    const int e4 = prof_.mark(st_);
-    prof_.span(LL_PROF_ZFWD, e2, e4);
-    const size_t smem = 2 * (size_t)nbnd_ * hq_.npw_pad * sizeof(cplx<T>) +
-                        (size_t)std::max(nproj_, nbnd_) * nbnd_ * sizeof(cplx<double>);
-    if ((rc = set_smem(k_proj<T>, smem, err))) return rc;
-    k_proj<T><<<dim3(nks_, nvec), 128, smem, st_>>>(nks_, nbnd_, hq_.npw_pad, dq_.npw, in, tbuf_, kin_, eps_, ukq_, bkq_,
-                                                   dij_, nproj_, out, part_);
-    LL_CK(cudaGetLastError());
-    prof_.count(LL_PROF_PROJ);
-    prof_.span(LL_PROF_PROJ, e4, prof_.mark(st_));
+    prof_.span(LL_PROF_ZFWD, e2, prof_.mark(st_));
     return LL_OK;
+  }
+
+  // reduction scratch of the per-k dot routines: max(16, 2*ni*nj) doubles per warp
+  size_t red_bytes(int threads) const {
+    const int pairs = std::max(std::max(nproj_, nbnd_) * nbnd_, 8);
+    return (size_t)(threads / 32) * 2 * pairs * sizeof(double);
+  }
+  template <int N>
+  int zfwd_proj_n(int nvec, const cplx<T>* in, cplx<T>* out, std::string& err) {
+    const size_t smem = 2 * (size_t)nbnd_ * hq_.npw_pad * sizeof(cplx<T>) +
+                        (size_t)std::max(nproj_, nbnd_) * nbnd_ * sizeof(cplx<double>) + red_bytes(256);
+    int rc;
+    if ((rc = set_smem(k_zfwd_proj<T, N>, smem, err))) return rc;
+    k_zfwd_proj<T, N><<<dim3(nks_, nvec), 256, smem, st_>>>(dq_, nbnd_, cbuf_, cb_ncol_, in, kin_, eps_, ukq_, bkq_,
+                                                             dij_, nproj_, out, part_);
+    LL_CK(cudaGetLastError());
+    return LL_OK;
+  }
+  int launch_zfwd_proj(int nvec, const cplx<T>* in, cplx<T>* out, std::string& err) {
+    switch (N_) {
+      case 12: return zfwd_proj_n<12>(nvec, in, out, err);
+      case 16: return zfwd_proj_n<16>(nvec, in, out, err);
+      case 18: return zfwd_proj_n<18>(nvec, in, out, err);
+      case 24: return zfwd_proj_n<24>(nvec, in, out, err);
+      case 32: return zfwd_proj_n<32>(nvec, in, out, err);
+      case 36: return zfwd_proj_n<36>(nvec, in, out, err);
+      case 48: return zfwd_proj_n<48>(nvec, in, out, err);
+    }
+    return LL_EUNSUPPORTED;
+  }
+  template <int N>
+  int zinv_ph_n(int j, std::string& err) {
+    const size_t smem = (size_t)nbnd_ * hq_.npw_pad * sizeof(cplx<T>) + (size_t)nbnd_ * nbnd_ * sizeof(cplx<double>) +
+                        red_bytes(256);
+    int rc;
+    if ((rc = set_smem(k_zinv_ph<T, N>, smem, err))) return rc;
+    Coef co{beta_, gamma_, zpart_, err_};
+    k_zinv_ph<T, N><<<nks_, 256, smem, st_>>>(j, (j % 2 == 0) ? 1 : 0, dq_, nbnd_, part_, R(), X(), Vp(), y_, ukq_,
+                                              co, tol_, cbuf_, cb_ncol_);
+    LL_CK(cudaGetLastError());
+    return LL_OK;
+  }
+  int launch_zinv_ph(int j, std::string& err) {
+    switch (N_) {
+      case 12: return zinv_ph_n<12>(j, err);
+      case 16: return zinv_ph_n<16>(j, err);
+      case 18: return zinv_ph_n<18>(j, err);
+      case 24: return zinv_ph_n<24>(j, err);
+      case 32: return zinv_ph_n<32>(j, err);
+      case 36: return zinv_ph_n<36>(j, err);
+      case 48: return zinv_ph_n<48>(j, err);
+    }
+    return LL_EUNSUPPORTED;
   }
 
   template <int N>
@@ -546,31 +620,14 @@ class Chain : public ChainBase {
     }
     return LL_EUNSUPPORTED;
   }
-  template <int N>
-  int zfwd_n(int nvec) {
-    k_zfwd<T, N><<<dim3(nks_, nvec), 128, 0, st_>>>(dq_, cbuf_, cb_ncol_, nbnd_, tbuf_);
-    return cudaGetLastError() == cudaSuccess ? LL_OK : LL_ECUDA;
-  }
-  int launch_zfwd(int nvec) {
-    switch (N_) {
-      case 12: return zfwd_n<12>(nvec);
-      case 16: return zfwd_n<16>(nvec);
-      case 18: return zfwd_n<18>(nvec);
-      case 24: return zfwd_n<24>(nvec);
-      case 32: return zfwd_n<32>(nvec);
-      case 36: return zfwd_n<36>(nvec);
-      case 48: return zfwd_n<48>(nvec);
-    }
-    return LL_EUNSUPPORTED;
-  }
   int groups_for(int norb) const {
     const int target = 4 * 152;
     int g = std::max(1, (target + N_ - 1) / N_);
     return std::min(g, norb);
   }
-  template <int N>
-  int xy_n(const SphereDev& s, int norb, int o_off, int dens_vec, int mode, std::string& err) {
-    constexpr int B = BO<N>::v;
+  template <int N, int MODE>
+  int xy_nm(const SphereDev& s, int norb, int o_off, int dens_vec, std::string& err) {
+    constexpr int B = BO<N, MODE>::v;
     const int ng = std::min(ngroups_, norb);
     XYArgs a;
     a.s = s;
@@ -579,20 +636,29 @@ class Chain : public ChainBase {
     a.cb_ncol = cb_ncol_;
     a.per_group = (norb + ng - 1) / ng;
     a.o_off = o_off;
-    a.dens_vec = (mode == 0) ? dens_vec : -1;
-    a.mode = mode;
+    a.dens_vec = dens_vec;
     const int NP = N + 1;
     size_t smem = (size_t)B * cb_ncol_ + (size_t)B * s.nrow_max * NP;
-    if (mode == 0 && a.dens_vec >= 0) smem += (size_t)B * N * NP;
-    smem += (size_t)N * NP;
+    if (MODE == XY_PASS2) smem += (size_t)N * NP;
+    if (MODE == XY_PASS1_DENS || MODE == XY_PASS2) smem += 2 * (size_t)B * N * NP;
+    if (MODE == XY_PASS1_DENS) smem += (size_t)N * NP;
     smem *= sizeof(cplx<T>);
+    if (MODE == XY_PASS1 || MODE == XY_PASS1_DENS) smem += (size_t)N * NP * sizeof(T);
     int rc;
-    if ((rc = set_smem(k_xy<T, N, B>, smem, err))) return rc;
-    k_xy<T, N, B><<<dim3(N, ng), 128, smem, st_>>>(a, cbuf_, vloc_, vpr_, ur_, nprt_, ur_);
-    if (mode == 0) last_ng_ = ng;
+    if ((rc = set_smem(k_xy<T, N, B, MODE>, smem, err))) return rc;
+    k_xy<T, N, B, MODE><<<dim3(N, ng), 128, smem, st_>>>(a, cbuf_, vloc_, vpr_, ur_, nprt_, ur_);
+    if (MODE == XY_PASS1_DENS) last_ng_ = ng;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) { err = std::string("k_xy: ") + cudaGetErrorString(e); return LL_ECUDA; }
     return LL_OK;
+  }
+  // mode 0: operator pass 1 (with the density when dens_vec >= 0); 1: pass 2; 2: store x(r)
+  template <int N>
+  int xy_n(const SphereDev& s, int norb, int o_off, int dens_vec, int mode, std::string& err) {
+    if (mode == 0) return dens_vec >= 0 ? xy_nm<N, XY_PASS1_DENS>(s, norb, o_off, dens_vec, err)
+                                        : xy_nm<N, XY_PASS1>(s, norb, o_off, -1, err);
+    if (mode == 1) return xy_nm<N, XY_PASS2>(s, norb, o_off, dens_vec, err);
+    return xy_nm<N, XY_STORE>(s, norb, o_off, -1, err);
   }
   int launch_xy(const SphereDev& s, int norb, int o_off, int dens_vec, int mode, std::string& err) {
     switch (N_) {
@@ -629,11 +695,21 @@ class Chain : public ChainBase {
   }
 
   template <typename F>
+  // Opts the kernel in to `bytes` of dynamic shared memory (static shared memory counts
+  // against the same 48 KB default, so the opt-in is made whenever the sum passes it).
   int set_smem(F* fn, size_t bytes, std::string& err) {
-    if (bytes > 48 * 1024) {
-      if (bytes > 227 * 1024) { err = "shared-memory tile exceeds 227 KB for this system"; return LL_EUNSUPPORTED; }
-      LL_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    const void* key = reinterpret_cast<const void*>(fn);
+    for (auto& e : smem_set_)
+      if (e.first == key && e.second >= bytes) return LL_OK;
+    cudaFuncAttributes at;
+    LL_CK(cudaFuncGetAttributes(&at, fn));
+    if (bytes + at.sharedSizeBytes > 227 * 1024) {
+      err = "shared-memory tile exceeds 227 KB for this system";
+      return LL_EUNSUPPORTED;
     }
+    if (bytes + at.sharedSizeBytes > 48 * 1024)
+      LL_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    smem_set_.push_back({key, bytes});
     return LL_OK;
   }
 
@@ -715,9 +791,10 @@ class Chain : public ChainBase {
 
   cudaStream_t st_ = nullptr;
   int N_ = 0, nks_ = 0, nbnd_ = 0, nproj_ = 0, approx_ = 0, flavour_ = 0, cap_ = 0, nvec_ = 1, ngroups_ = 1;
-  int cb_ncol_ = 0, steps_ = 0, spec_cap_ = 0, last_ng_ = 1;
+  int cb_ncol_ = 0, steps_ = 0, queued_ = 0, spec_cap_ = 0, last_ng_ = 1;
   bool stopped_ = false;
   Profiler prof_;
+  std::vector<std::pair<const void*, size_t>> smem_set_;
   double omega_ = 0, q_[3] = {0, 0, 0}, tol_ = 0;
   HostSphere hk_, hq_;
   SphereDev dk_{}, dq_{};
@@ -726,7 +803,7 @@ class Chain : public ChainBase {
   T *whart_ = nullptr, *kin_ = nullptr, *vloc_ = nullptr, *fxc_ = nullptr;
   double *rho_ = nullptr, *eps_ = nullptr, *dij_ = nullptr, *part_ = nullptr, *beta_ = nullptr;
   cplx<T> *uk_ = nullptr, *ukq_ = nullptr, *bkq_ = nullptr, *ur_ = nullptr, *cbuf_ = nullptr, *nprt_ = nullptr;
-  cplx<T> *nr_ = nullptr, *ng_ = nullptr, *vpr_ = nullptr, *tbuf_ = nullptr, *y_ = nullptr, *vecs_ = nullptr;
+  cplx<T> *nr_ = nullptr, *ng_ = nullptr, *vpr_ = nullptr, *y_ = nullptr, *vecs_ = nullptr;
   cplx<T>* scratch_ = nullptr;
   cplx<double> *spart_ = nullptr, *gamma_ = nullptr, *z_ = nullptr, *zpart_ = nullptr, *spec_out_ = nullptr;
   double* spec_w_ = nullptr;

@@ -25,10 +25,9 @@ struct SphereDev {
   const int4* row;      // [nks][nrow_max]  (m1, first column, m2 of the first column, columns)
 };
 
-__device__ __forceinline__ int wrap(int m, int n) { int r = m % n; return r < 0 ? r + n : r; }
-
-template <typename T>
-__device__ __forceinline__ cplx<T> ldc(const cplx<T>* p) { return *p; }
+// m mod N for m >= -N (a mask when N is a power of two)
+template <int N>
+__device__ __forceinline__ int wrapn(int m) { return (int)((unsigned)(m + N) % (unsigned)N); }
 
 // ---------------------------------------------------------------------------------------
 // Sphere -> columns: scatter each column's points and inverse-FFT along axis 3.
@@ -47,7 +46,7 @@ __global__ void __launch_bounds__(128) k_zinv(SphereDev s, const cplx<T>* __rest
     cplx<T> a[N];
 #pragma unroll
     for (int p = 0; p < N; ++p) {
-      const int i = wrap(p - cl.z, N);
+      const int i = wrapn<N>(p - cl.z);
       a[p] = (i < cl.w) ? src[i] : czero<T>();
     }
     fft_line<T, N, +1>(a);
@@ -57,86 +56,91 @@ __global__ void __launch_bounds__(128) k_zinv(SphereDev s, const cplx<T>* __rest
   }
 }
 
-// Columns -> sphere: forward FFT along axis 3, gather the column's points, scale 1/N^3.
-template <typename T, int N>
-__global__ void __launch_bounds__(128) k_zfwd(SphereDev s, const cplx<T>* __restrict__ cbuf, int cb_ncol,
-                                              int nbnd, cplx<T>* __restrict__ out) {
-  const int k = blockIdx.x, vec = blockIdx.y;
-  const int nc = s.ncol[k];
-  const T scale = T(1) / T(N * N * N);
-  for (int it = threadIdx.x; it < nbnd * nc; it += blockDim.x) {
-    const int v = it / nc, c = it - v * nc;
-    const long o = ((long)vec * s.nks + k) * nbnd + v;
-    const int4 cl = s.col[k * s.ncol_max + c];
-    const int st = s.colstart[k * s.ncol_max + c];
-    const cplx<T>* src = cbuf + o * (long)N * cb_ncol + c;
-    cplx<T> a[N];
-#pragma unroll
-    for (int p = 0; p < N; ++p) a[p] = src[(long)p * cb_ncol];
-    fft_line<T, N, -1>(a);
-    cplx<T>* dst = out + o * s.npw_pad + st;
-#pragma unroll
-    for (int p = 0; p < N; ++p) {
-      const int i = wrap(p - cl.z, N);
-      if (i < cl.w) dst[i] = a[p] * scale;
-    }
-  }
-  // zero the padding of every orbital of this k
-  const int np = s.npw[k];
-  for (int it = threadIdx.x; it < nbnd * (s.npw_pad - np); it += blockDim.x) {
-    const int v = it / (s.npw_pad - np), i = np + it % (s.npw_pad - np);
-    out[(((long)vec * s.nks + k) * nbnd + v) * s.npw_pad + i] = czero<T>();
-  }
+// ---------------------------------------------------------------------------------------
+// Asynchronous global -> shared copies (cp.async) of BYTES per thread.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem_dst, const void* gmem_src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(gmem_src), "n"(BYTES));
 }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+// every committed group but the most recent one has landed
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::); }
 
 // ---------------------------------------------------------------------------------------
 // Per-plane pass of one operator application.  grid (N planes, groups), block 128.
-// For every orbital of the group (BO at a time): inverse 2D FFT of the plane's columns,
-// t(r) = V(r) x(r), optional response-density accumulation conj(u(r)) x(r), forward 2D FFT
-// back to the columns (in place).  mode 0: pass 1 (V x, density if dens_vec matches);
-// mode 1: pass 2 (t(r) = v'(r) u(r) from the orbital grid, added into the columns);
-// mode 2: inverse only, store x(r) into `grid_out` (orbital grids at set-up).
+// For every orbital of the group (BO at a time), at plane j3 = blockIdx.x:
+//   XY_PASS1       inverse 2D FFT of the plane's columns, t(r) = V(r) x(r), forward 2D FFT
+//                  back to the columns (in place);
+//   XY_PASS1_DENS  the same plus the response-density partial sum_o conj(u_o(r)) x_o(r) of the
+//                  orbitals of vector dens_vec, written per (group, plane) to nprt;
+//   XY_PASS2       t(r) = v'(r) u(r) from the orbital grid, forward 2D FFT, added into the
+//                  columns (linearity: one axis-3 transform serves both passes);
+//   XY_STORE       inverse 2D FFT only, x(r) stored to grid_out (orbital grids at set-up).
+// The orbital-grid planes (contiguous N^2 in HBM) are staged into shared memory with
+// cp.async, double-buffered: the next batch's planes stream in while the current batch is
+// transformed, and every global load is coalesced.
+enum XYMode { XY_PASS1 = 0, XY_PASS1_DENS = 1, XY_PASS2 = 2, XY_STORE = 3 };
+
 struct XYArgs {
   SphereDev s;
   int nbnd, norb;              // orbitals handled by this launch
   int cb_ncol;
   int per_group;               // orbitals per group
   int o_off;                   // first orbital of this launch (orbital o = o_off + local index)
-  int dens_vec;                // vector whose orbitals feed the density (-1: none)
-  int mode;
+  int dens_vec;                // vector whose orbitals feed the density (XY_PASS1_DENS)
 };
 
-template <typename T, int N, int BO>
-__global__ void __launch_bounds__(128) k_xy(XYArgs a, cplx<T>* __restrict__ cbuf, const T* __restrict__ vloc,
-                                            const cplx<T>* __restrict__ vpr, const cplx<T>* __restrict__ ur,
-                                            cplx<T>* __restrict__ nprt, cplx<T>* __restrict__ grid_out) {
+template <typename T, int N, int BO, int MODE>
+__global__ void __launch_bounds__(128, 4) k_xy(XYArgs a, cplx<T>* __restrict__ cbuf, const T* __restrict__ vloc,
+                                               const cplx<T>* __restrict__ vpr, const cplx<T>* __restrict__ ur,
+                                               cplx<T>* __restrict__ nprt, cplx<T>* __restrict__ grid_out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int NP = N + 1;
+  constexpr bool kUseU = (MODE == XY_PASS1_DENS || MODE == XY_PASS2);
   const int iz = blockIdx.x, g = blockIdx.y;
   const SphereDev& s = a.s;
-  constexpr int NP = N + 1;
   cplx<T>* Cs = reinterpret_cast<cplx<T>*>(smem_raw);                 // [BO][cb_ncol]
   cplx<T>* Ys = Cs + BO * a.cb_ncol;                                    // [BO][nrow_max][NP]
-  cplx<T>* Ds = Ys + BO * s.nrow_max * NP;                              // [BO][N][NP] (density)
-  cplx<T>* Pl = Ds + ((a.mode == 0 && a.dens_vec >= 0) ? BO * N * NP : 0);  // plane [N][NP]
-  const bool want_dens = (a.mode == 0 && a.dens_vec >= 0);
+  cplx<T>* Pl = Ys + BO * s.nrow_max * NP;                              // [N][NP]  v' (pass 2)
+  cplx<T>* Us = Pl + (MODE == XY_PASS2 ? N * NP : 0);                   // [2][BO][N][NP] u planes
+  cplx<T>* Dacc = Us + (kUseU ? 2 * BO * N * NP : 0);                   // [N][NP] density
+  T* Pv = reinterpret_cast<T*>(Dacc + (MODE == XY_PASS1_DENS ? N * NP : 0));  // [N][NP] V (real)
   const long plane = (long)N * N;
+  const int per_vec = s.nks * a.nbnd;
 
-  // the plane of V (mode 0) or v' (mode 1)
-  if (a.mode == 0) {
-    for (int i = threadIdx.x; i < N * N; i += blockDim.x) Pl[(i / N) * NP + i % N] = mk(vloc[iz * plane + i], T(0));
-  } else if (a.mode == 1) {
+  if (MODE == XY_PASS1 || MODE == XY_PASS1_DENS) {
+    for (int i = threadIdx.x; i < N * N; i += blockDim.x) Pv[(i / N) * NP + i % N] = vloc[iz * plane + i];
+  } else if (MODE == XY_PASS2) {
     for (int i = threadIdx.x; i < N * N; i += blockDim.x) Pl[(i / N) * NP + i % N] = vpr[iz * plane + i];
   }
-  if (want_dens)
-    for (int i = threadIdx.x; i < BO * N * NP; i += blockDim.x) Ds[i] = czero<T>();
+  if (MODE == XY_PASS1_DENS)
+    for (int i = threadIdx.x; i < N * NP; i += blockDim.x) Dacc[i] = czero<T>();
 
   const int o_begin = a.o_off + g * a.per_group;
   const int o_end = a.o_off + min(a.norb, g * a.per_group + a.per_group);
-  for (int ob = o_begin; ob < o_end; ob += BO) {
+  auto stage_u = [&](int obatch, int stage) {
+    const int nbb = min(BO, o_end - obatch);
+    cplx<T>* dst = Us + stage * (BO * N * NP);
+    for (int i = threadIdx.x; i < nbb * N * N; i += blockDim.x) {
+      const int b = i / (N * N), r = i - b * N * N;
+      const int ko = (obatch + b) % per_vec;
+      cp_async<sizeof(cplx<T>)>(dst + (b * N + r / N) * NP + r % N, ur + (long)ko * N * plane + iz * plane + r);
+    }
+  };
+  if (kUseU && o_begin < o_end) {
+    stage_u(o_begin, 0);
+    cp_async_commit();
+  }
+  int stage = 0;
+  for (int ob = o_begin; ob < o_end; ob += BO, stage ^= 1) {
     const int nb = min(BO, o_end - ob);
     __syncthreads();
-    // load the plane's column values of each orbital
-    if (a.mode != 1) {
+    if (kUseU) {
+      if (ob + BO < o_end) stage_u(ob + BO, stage ^ 1);
+      cp_async_commit();
+    }
+    if (MODE != XY_PASS2) {
       for (int i = threadIdx.x; i < nb * a.cb_ncol; i += blockDim.x) {
         const int b = i / a.cb_ncol, c = i - b * a.cb_ncol;
         const int o = ob + b, k = (o / a.nbnd) % s.nks;
@@ -153,7 +157,7 @@ __global__ void __launch_bounds__(128) k_xy(XYArgs a, cplx<T>* __restrict__ cbuf
         const cplx<T>* cs = Cs + b * a.cb_ncol + rw.y;
 #pragma unroll
         for (int p = 0; p < N; ++p) {
-          const int j = wrap(p - rw.z, N);
+          const int j = wrapn<N>(p - rw.z);
           l[p] = (j < rw.w) ? cs[j] : czero<T>();
         }
         fft_line<T, N, +1>(l);
@@ -161,51 +165,61 @@ __global__ void __launch_bounds__(128) k_xy(XYArgs a, cplx<T>* __restrict__ cbuf
 #pragma unroll
         for (int p = 0; p < N; ++p) ys[p] = l[p];
       }
-      __syncthreads();
     }
+    if (kUseU) cp_async_wait_prev();
+    __syncthreads();
+    cplx<T>* Ub = Us + stage * (BO * N * NP);
     // axis 1: one line per (orbital, j2)
     for (int i = threadIdx.x; i < nb * N; i += blockDim.x) {
       const int b = i / N, j2 = i - b * N;
       const int o = ob + b, k = (o / a.nbnd) % s.nks;
       const int nr = s.nrow[k];
       const int m1min = s.row[k * s.nrow_max].x;
-      const int ko = o % (s.nks * a.nbnd);   // orbital index within its vector
       cplx<T> l[N];
-      if (a.mode == 1) {
-        const cplx<T>* u = ur + (long)ko * N * plane + iz * plane + (long)j2 * N;
+      if (MODE == XY_PASS2) {
+        const cplx<T>* u = Ub + (b * N + j2) * NP;
 #pragma unroll
         for (int p = 0; p < N; ++p) l[p] = cmul(Pl[j2 * NP + p], u[p]);
       } else {
 #pragma unroll
         for (int p = 0; p < N; ++p) {
-          const int r = wrap(p - m1min, N);
+          const int r = wrapn<N>(p - m1min);
           l[p] = (r < nr) ? Ys[(b * s.nrow_max + r) * NP + j2] : czero<T>();
         }
         fft_line<T, N, +1>(l);
-        if (a.mode == 2) {
+        if (MODE == XY_STORE) {
           cplx<T>* dst = grid_out + (long)o * N * plane + iz * plane + (long)j2 * N;
 #pragma unroll
           for (int p = 0; p < N; ++p) dst[p] = l[p];
           continue;
         }
-        if (want_dens && o / (s.nks * a.nbnd) == a.dens_vec) {
-          const cplx<T>* u = ur + (long)ko * N * plane + iz * plane + (long)j2 * N;
-          cplx<T>* d = Ds + (b * N + j2) * NP;
+        if (MODE == XY_PASS1_DENS) {
+          // conj(u) x replaces this thread's own u line in place (reduced after the barrier)
+          cplx<T>* u = Ub + (b * N + j2) * NP;
+          const bool on = (o / per_vec) == a.dens_vec;
 #pragma unroll
-          for (int p = 0; p < N; ++p) d[p] = d[p] + cjmul(u[p], l[p]);
+          for (int p = 0; p < N; ++p) u[p] = on ? cjmul(u[p], l[p]) : czero<T>();
         }
 #pragma unroll
-        for (int p = 0; p < N; ++p) l[p] = l[p] * Pl[j2 * NP + p].x;
+        for (int p = 0; p < N; ++p) l[p] = l[p] * Pv[j2 * NP + p];
       }
       fft_line<T, N, -1>(l);
 #pragma unroll
       for (int p = 0; p < N; ++p) {
-        const int r = wrap(p - m1min, N);
+        const int r = wrapn<N>(p - m1min);
         if (r < nr) Ys[(b * s.nrow_max + r) * NP + j2] = l[p];
       }
     }
     __syncthreads();
-    if (a.mode == 2) continue;
+    if (MODE == XY_STORE) continue;
+    if (MODE == XY_PASS1_DENS) {  // density of the batch, orbitals summed in a fixed order
+      for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
+        const int q = (i / N) * NP + i % N;
+        cplx<T> acc = Dacc[q];
+        for (int b = 0; b < nb; ++b) acc = acc + Ub[b * N * NP + q];
+        Dacc[q] = acc;
+      }
+    }
     // forward FFT along axis 2 of every row, keep the row's columns
     for (int i = threadIdx.x; i < nb * s.nrow_max; i += blockDim.x) {
       const int b = i / s.nrow_max, r = i - b * s.nrow_max;
@@ -220,7 +234,7 @@ __global__ void __launch_bounds__(128) k_xy(XYArgs a, cplx<T>* __restrict__ cbuf
       cplx<T>* cs = Cs + b * a.cb_ncol + rw.y;
 #pragma unroll
       for (int p = 0; p < N; ++p) {
-        const int j = wrap(p - rw.z, N);
+        const int j = wrapn<N>(p - rw.z);
         if (j < rw.w) cs[j] = l[p];
       }
     }
@@ -230,17 +244,13 @@ __global__ void __launch_bounds__(128) k_xy(XYArgs a, cplx<T>* __restrict__ cbuf
       const int o = ob + b, k = (o / a.nbnd) % s.nks;
       if (c >= s.ncol[k]) continue;
       cplx<T>* dst = cbuf + (long)o * N * a.cb_ncol + (long)iz * a.cb_ncol + c;
-      *dst = (a.mode == 1) ? *dst + Cs[i] : Cs[i];
+      *dst = (MODE == XY_PASS2) ? *dst + Cs[i] : Cs[i];
     }
   }
-  if (want_dens) {
+  if (MODE == XY_PASS1_DENS) {
     __syncthreads();
-    for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
-      const int j2 = i / N, j1 = i - j2 * N;
-      cplx<T> acc = czero<T>();
-      for (int b = 0; b < BO; ++b) acc = acc + Ds[(b * N + j2) * NP + j1];
-      nprt[(long)g * N * plane + iz * plane + i] = acc;
-    }
+    for (int i = threadIdx.x; i < N * N; i += blockDim.x)
+      nprt[(long)g * N * plane + iz * plane + i] = Dacc[(i / N) * NP + i % N];
   }
 }
 
@@ -329,101 +339,139 @@ __global__ void __launch_bounds__(64) k_hxc_inv(const cplx<T>* __restrict__ ng, 
 }
 
 // ---------------------------------------------------------------------------------------
-// Block reductions in double (fixed order: lanes, then warps) -> deterministic.
+// Reductions.  Every sum below runs in a fixed order (per-thread strided partial sums, lanes,
+// then warps), so results are bitwise reproducible.
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;
 }
 
-// Dots conj(A_i) . B_j over npw for a list of (i, j) pairs, one warp per pair.  Results
-// (times `mult[i]` when given) into out[pair] as complex double.
 template <typename T>
-__device__ void pair_dots(const cplx<T>* A, int lda, const cplx<T>* B, int ldb, int npw, int ni, int nj,
-                          const double* mult, cplx<double>* out) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int pr = warp; pr < ni * nj; pr += nw) {
-    const int i = pr / nj, j = pr - i * nj;
-    const cplx<T>* a = A + (long)i * lda;
-    const cplx<T>* b = B + (long)j * ldb;
-    T re = 0, im = 0;
-    for (int g = lane; g < npw; g += 32) {
-      const cplx<T> t = cjmul(a[g], b[g]);
-      re += t.x;
-      im += t.y;
+__device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// All-pairs dots out[i*nj + j] = mult[i] * sum_g conj(A[i*lda + g]) B[j*ldb + g] over g < npw,
+// eight pairs at a time: per-thread partial sums in T, warp sums in T, warps summed in
+// double.  `red`: 16 doubles per warp.  Called by the whole block; ends synchronised.
+template <typename T>
+__device__ void block_dots(const cplx<T>* A, long lda, const cplx<T>* B, long ldb, int npw, int ni, int nj,
+                           const double* mult, cplx<double>* out, double* red) {
+  const int np = ni * nj;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int c0 = 0; c0 < np; c0 += 8) {
+    T acc[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[q] = T(0);
+    for (int g = threadIdx.x; g < npw; g += blockDim.x) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int pr = c0 + q;
+        if (pr < np) {
+          const int i = pr / nj, j = pr - i * nj;
+          const cplx<T> t = cjmul(A[i * lda + g], B[j * ldb + g]);
+          acc[2 * q] += t.x;
+          acc[2 * q + 1] += t.y;
+        }
+      }
     }
-    double dr = warp_sum((double)re), di = warp_sum((double)im);
-    if (lane == 0) {
-      const double m = mult ? mult[i] : 1.0;
-      out[pr] = mk(dr * m, di * m);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const T v = warp_sum_t(acc[q]);
+      if (lane == 0) red[warp * 16 + q] = (double)v;
     }
+    __syncthreads();
+    if (threadIdx.x < 8 && c0 + (int)threadIdx.x < np) {
+      const int pr = c0 + threadIdx.x;
+      double re = 0.0, im = 0.0;
+      for (int w = 0; w < nw; ++w) {
+        re += red[w * 16 + 2 * threadIdx.x];
+        im += red[w * 16 + 2 * threadIdx.x + 1];
+      }
+      const double m = mult ? mult[pr / nj] : 1.0;
+      out[pr] = mk(re * m, im * m);
+    }
+    __syncthreads();
   }
 }
 
-// The rest of the operator per k-point: kinetic and -eps, KB projectors, P_c, and the
-// partial Re(x^H X) of the pseudo-Hermitian norm.  grid (nks, nvec), block 128.
-// smem: xs, ts [nbnd][npw_pad], coefficient scratch.
-template <typename T>
-__global__ void __launch_bounds__(128) k_proj(int nks, int nbnd, int npw_pad, const int* __restrict__ npw,
-                                              const cplx<T>* __restrict__ xin, const cplx<T>* __restrict__ tin,
-                                              const T* __restrict__ kin, const double* __restrict__ eps,
-                                              const cplx<T>* __restrict__ ukq, const cplx<T>* __restrict__ bkq,
-                                              const double* __restrict__ dij, int nproj, cplx<T>* __restrict__ xout,
-                                              double* __restrict__ part) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int k = blockIdx.x, vec = blockIdx.y;
-  const int np = npw[k];
-  cplx<T>* xs = reinterpret_cast<cplx<T>*>(smem_raw);
-  cplx<T>* ts = xs + nbnd * npw_pad;
-  cplx<double>* cf = reinterpret_cast<cplx<double>*>(ts + nbnd * npw_pad);   // [max(nproj,nbnd) * nbnd]
-  __shared__ double red[4];
-  const long base = ((long)vec * nks + k) * nbnd * npw_pad;
-  for (int i = threadIdx.x; i < nbnd * npw_pad; i += blockDim.x) {
-    const int v = i / npw_pad, gi = i - v * npw_pad;
-    const cplx<T> xv = xin[base + i];
-    xs[i] = xv;
-    const T d = kin[(long)k * npw_pad + gi] - (T)eps[k * nbnd + v];
-    ts[i] = tin[base + i] + xv * d;
-  }
-  __syncthreads();
-  if (nproj > 0) {
-    const cplx<T>* bk = bkq + (long)k * nproj * npw_pad;
-    pair_dots<T>(bk, npw_pad, xs, npw_pad, np, nproj, nbnd, dij, cf);   // D_p <beta_p|x_v>
-    __syncthreads();
-    for (int i = threadIdx.x; i < nbnd * npw_pad; i += blockDim.x) {
-      const int v = i / npw_pad, gi = i - v * npw_pad;
-      cplx<T> acc = ts[i];
-      for (int p = 0; p < nproj; ++p) {
-        const cplx<double> c = cf[p * nbnd + v];
-        acc = acc + cmul(bk[(long)p * npw_pad + gi], mk((T)c.x, (T)c.y));
+// The same for compile-time NI x NJ (the common small shapes) in one pass: every thread keeps
+// all NI*NJ complex partial sums in registers.  `red`: 2*NI*NJ doubles per warp.
+template <typename T, int NI, int NJ>
+__device__ void block_dots_fixed(const cplx<T>* A, long lda, const cplx<T>* B, long ldb, int npw,
+                                 const double* mult, cplx<double>* out, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  T acc[NI][NJ][2];
+#pragma unroll
+  for (int i = 0; i < NI; ++i)
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) acc[i][j][0] = acc[i][j][1] = T(0);
+  for (int g = threadIdx.x; g < npw; g += blockDim.x) {
+    cplx<T> a[NI], b[NJ];
+#pragma unroll
+    for (int i = 0; i < NI; ++i) a[i] = A[i * lda + g];
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) b[j] = B[j * ldb + g];
+#pragma unroll
+    for (int i = 0; i < NI; ++i)
+#pragma unroll
+      for (int j = 0; j < NJ; ++j) {
+        acc[i][j][0] += a[i].x * b[j].x + a[i].y * b[j].y;
+        acc[i][j][1] += a[i].x * b[j].y - a[i].y * b[j].x;
       }
-      ts[i] = acc;
-    }
-    __syncthreads();
   }
-  const cplx<T>* uk = ukq + (long)k * nbnd * npw_pad;
-  pair_dots<T>(uk, npw_pad, ts, npw_pad, np, nbnd, nbnd, nullptr, cf);       // S = U^H t
+#pragma unroll
+  for (int i = 0; i < NI; ++i)
+#pragma unroll
+    for (int j = 0; j < NJ; ++j)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const T v = warp_sum_t(acc[i][j][c]);
+        if (lane == 0) red[warp * (2 * NI * NJ) + (i * NJ + j) * 2 + c] = (double)v;
+      }
   __syncthreads();
-  double acc = 0.0;
+  if (threadIdx.x < NI * NJ) {
+    double re = 0.0, im = 0.0;
+    for (int w = 0; w < nw; ++w) {
+      re += red[w * (2 * NI * NJ) + 2 * threadIdx.x];
+      im += red[w * (2 * NI * NJ) + 2 * threadIdx.x + 1];
+    }
+    const double m = mult ? mult[threadIdx.x / NJ] : 1.0;
+    out[threadIdx.x] = mk(re * m, im * m);
+  }
+  __syncthreads();
+}
+
+// Fixed-shape dots when (ni, nj) is one of the compiled shapes, else the chunked form.
+// `red` must hold max(16, 2*ni*nj) doubles per warp.
+template <typename T>
+__device__ __forceinline__ void small_dots(const cplx<T>* A, long lda, const cplx<T>* B, long ldb, int npw, int ni,
+                                           int nj, const double* mult, cplx<double>* out, double* red) {
+  if (ni == 4 && nj == 4) block_dots_fixed<T, 4, 4>(A, lda, B, ldb, npw, mult, out, red);
+  else if (ni == 8 && nj == 4) block_dots_fixed<T, 8, 4>(A, lda, B, ldb, npw, mult, out, red);
+  else if (ni == 2 && nj == 4) block_dots_fixed<T, 2, 4>(A, lda, B, ldb, npw, mult, out, red);
+  else if (ni == 1 && nj == 1) block_dots_fixed<T, 1, 1>(A, lda, B, ldb, npw, mult, out, red);
+  else block_dots<T>(A, lda, B, ldb, npw, ni, nj, mult, out, red);
+}
+
+// x[v][g] -= sum_w U[w][g] S[w][v] for the nbnd orbitals of one k (S = U^H x).  The
+// coefficients are rounded to T once: conversions from double run on the slow FP64 pipe.
+template <typename T>
+__device__ __forceinline__ void subtract_projection(cplx<T>* x, const cplx<T>* uk, const cplx<double>* S, int nbnd,
+                                                    int npw_pad) {
+  __shared__ cplx<T> St[32 * 32];
+  for (int i = threadIdx.x; i < nbnd * nbnd; i += blockDim.x) St[i] = mk((T)S[i].x, (T)S[i].y);
+  __syncthreads();
   for (int i = threadIdx.x; i < nbnd * npw_pad; i += blockDim.x) {
     const int v = i / npw_pad, gi = i - v * npw_pad;
-    cplx<T> t = ts[i];
-    for (int w = 0; w < nbnd; ++w) {
-      const cplx<double> c = cf[w * nbnd + v];
-      t = t - cmul(uk[(long)w * npw_pad + gi], mk((T)c.x, (T)c.y));
-    }
-    xout[base + i] = t;
-    const cplx<T> xv = xs[i];
-    acc += (double)(xv.x * t.x + xv.y * t.y);
+    cplx<T> t = x[i];
+    for (int w = 0; w < nbnd; ++w) t = t - cmul(uk[(long)w * npw_pad + gi], St[w * nbnd + v]);
+    x[i] = t;
   }
-  acc = warp_sum(acc);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-    part[vec * nks + k] = s;
-  }
 }
 
 // x <- P_c x for every orbital of k (in place).  grid (nks, nvec), block 128.
@@ -431,20 +479,12 @@ template <typename T>
 __global__ void __launch_bounds__(128) k_project(int nks, int nbnd, int npw_pad, const int* __restrict__ npw,
                                                  const cplx<T>* __restrict__ ukq, cplx<T>* __restrict__ x) {
   __shared__ cplx<double> cf[32 * 32];
+  __shared__ double red[4 * 16];
   const int k = blockIdx.x, vec = blockIdx.y;
   const long base = ((long)vec * nks + k) * nbnd * npw_pad;
   const cplx<T>* uk = ukq + (long)k * nbnd * npw_pad;
-  pair_dots<T>(uk, npw_pad, x + base, npw_pad, npw[k], nbnd, nbnd, nullptr, cf);
-  __syncthreads();
-  for (int i = threadIdx.x; i < nbnd * npw_pad; i += blockDim.x) {
-    const int v = i / npw_pad, gi = i - v * npw_pad;
-    cplx<T> t = x[base + i];
-    for (int w = 0; w < nbnd; ++w) {
-      const cplx<double> c = cf[w * nbnd + v];
-      t = t - cmul(uk[(long)w * npw_pad + gi], mk((T)c.x, (T)c.y));
-    }
-    x[base + i] = t;
-  }
+  block_dots<T>(uk, npw_pad, x + base, npw_pad, npw[k], nbnd, nbnd, nullptr, cf, red);
+  subtract_projection<T>(x + base, uk, cf, nbnd, npw_pad);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -460,92 +500,160 @@ __device__ __forceinline__ void flag_error(int* err, int code, int step) {
   if (atomicCAS(err, 0, code) == 0) err[1] = step;
 }
 
-// Sum of per-k partials in a fixed order, times 1/nks.
-__device__ __forceinline__ double sum_parts(const double* p, int nks) {
+// (1/n) sum_i p[i*stride + offset], i < n, by the whole block in a fixed order; every thread
+// gets the result.
+__device__ __forceinline__ double block_mean(const double* p, int n, int stride = 1, int offset = 0) {
+  __shared__ double wsum[32];
   double s = 0.0;
-  for (int i = 0; i < nks; ++i) s += p[i];
-  return s / nks;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += p[(long)i * stride + offset];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = s;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w];
+  __syncthreads();
+  return t / n;
 }
 
-// Pseudo-Hermitian step j (1-based) before the operator: beta_j from the partials of
-// Re(r_j^H X_j); v_j = r_j/beta_j; z_j partial; r_{j+1} = P_c(X_j/beta_j - beta_j v_{j-1}).
-// grid nks, block 128.
-template <typename T>
-__global__ void __launch_bounds__(128) k_update_ph(int j, int r_upper, int nks, int nbnd, int npw_pad,
-                                                   const int* __restrict__ npw, const double* __restrict__ part,
-                                                   cplx<T>* __restrict__ R, const cplx<T>* __restrict__ X,
-                                                   cplx<T>* __restrict__ Vp, const cplx<T>* __restrict__ y,
-                                                   const cplx<T>* __restrict__ ukq, Coef co, double tol) {
+// Pseudo-Hermitian step j fused with the first stage of the operator: beta_j from the
+// partials of Re(r_j^H X_j) (every block re-reduces them in the same order), z_j partial,
+// r_{j+1} = P_c(X_j/beta_j - beta_j v_{j-1}), v_j = r_j/beta_j, then the sphere columns of
+// r_{j+1} inverse-FFT'd along axis 3 straight from shared memory.  grid nks, block 256.
+// smem: r [nbnd][npw_pad], S [nbnd*nbnd] (double complex), reduction scratch.
+template <typename T, int N>
+__global__ void __launch_bounds__(256) k_zinv_ph(int j, int r_upper, SphereDev s, int nbnd,
+                                                 const double* __restrict__ part, cplx<T>* __restrict__ R,
+                                                 const cplx<T>* __restrict__ X, cplx<T>* __restrict__ Vp,
+                                                 const cplx<T>* __restrict__ y, const cplx<T>* __restrict__ ukq,
+                                                 Coef co, double tol, cplx<T>* __restrict__ cbuf, int cb_ncol) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cplx<T>* rs = reinterpret_cast<cplx<T>*>(smem_raw);          // [nbnd][npw_pad]
-  cplx<double>* cf = reinterpret_cast<cplx<double>*>(rs + nbnd * npw_pad);   // [nbnd*nbnd + 1]
+  const int npw_pad = s.npw_pad, nks = s.nks;
+  cplx<T>* rs = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<double>* cf = reinterpret_cast<cplx<double>*>(rs + nbnd * npw_pad);
+  double* red = reinterpret_cast<double*>(cf + nbnd * nbnd);
   __shared__ double sbeta;
   const int k = blockIdx.x;
+  const double b2 = block_mean(part, nks);
   if (threadIdx.x == 0) {
-    const double b2 = sum_parts(part, nks);
-    double b = 0.0;
-    if (!(b2 > tol)) {
-      flag_error(co.err, b2 <= 0.0 ? DEV_NOTPD : DEV_BREAKDOWN, j);
-      b = 1.0;
-    } else {
-      b = sqrt(b2);
-    }
+    double b = 1.0;
+    if (!(b2 > tol)) flag_error(co.err, b2 <= 0.0 ? DEV_NOTPD : DEV_BREAKDOWN, j);
+    else b = sqrt(b2);
     sbeta = b;
     if (k == 0) { co.beta[j - 1] = b; co.gamma[j - 1] = mk(b, 0.0); }
   }
   __syncthreads();
   const double b = sbeta;
   const long base = (long)k * nbnd * npw_pad;
-  const int np = npw[k];
-  // z_j partial: (y, r_j) / beta_j when r_j is upper
-  if (r_upper) {
-    // one warp per band, then the bands summed in order
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int v = warp; v < nbnd; v += nw) {
-      T re = 0, im = 0;
-      for (int g = lane; g < np; g += 32) {
-        const cplx<T> t = cjmul(y[base + (long)v * npw_pad + g], R[base + (long)v * npw_pad + g]);
-        re += t.x; im += t.y;
-      }
-      const double dr = warp_sum((double)re), di = warp_sum((double)im);
-      if (lane == 0) cf[v] = mk(dr, di);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double zr = 0, zi = 0;
-      for (int v = 0; v < nbnd; ++v) { zr += cf[v].x; zi += cf[v].y; }
-      co.zpart[(long)(j - 1) * nks + k] = mk(zr / b, zi / b);
-    }
-    __syncthreads();
+  const int np = s.npw[k];
+  if (r_upper) {  // z_j = (y, r_j)/beta_j, the whole k block as one vector
+    small_dots<T>(y + base, 0, R + base, 0, nbnd * npw_pad, 1, 1, nullptr, cf, red);
+    if (threadIdx.x == 0) co.zpart[(long)(j - 1) * nks + k] = mk(cf[0].x / b, cf[0].y / b);
   } else if (threadIdx.x == 0) {
     co.zpart[(long)(j - 1) * nks + k] = mk(0.0, 0.0);
   }
   const T ib = (T)(1.0 / b), bb = (T)b;
   for (int i = threadIdx.x; i < nbnd * npw_pad; i += blockDim.x) {
     const cplx<T> r = R[base + i];
-    const cplx<T> xv = X[base + i];
-    const cplx<T> vp = Vp[base + i];
-    rs[i] = xv * ib - vp * bb;
+    rs[i] = X[base + i] * ib - Vp[base + i] * bb;
     Vp[base + i] = r * ib;
   }
   __syncthreads();
   const cplx<T>* uk = ukq + base;
-  pair_dots<T>(uk, npw_pad, rs, npw_pad, np, nbnd, nbnd, nullptr, cf);
+  small_dots<T>(uk, npw_pad, rs, npw_pad, np, nbnd, nbnd, nullptr, cf, red);
+  subtract_projection<T>(rs, uk, cf, nbnd, npw_pad);
+  for (int i = threadIdx.x; i < nbnd * npw_pad; i += blockDim.x) R[base + i] = rs[i];
+  const int nc = s.ncol[k];
+  for (int it = threadIdx.x; it < nbnd * nc; it += blockDim.x) {
+    const int v = it / nc, c = it - v * nc;
+    const int4 cl = s.col[k * s.ncol_max + c];
+    const cplx<T>* src = rs + v * npw_pad + s.colstart[k * s.ncol_max + c];
+    cplx<T> a[N];
+#pragma unroll
+    for (int p = 0; p < N; ++p) {
+      const int i = wrapn<N>(p - cl.z);
+      a[p] = (i < cl.w) ? src[i] : czero<T>();
+    }
+    fft_line<T, N, +1>(a);
+    cplx<T>* dst = cbuf + ((long)k * nbnd + v) * N * cb_ncol + c;
+#pragma unroll
+    for (int p = 0; p < N; ++p) dst[(long)p * cb_ncol] = a[p];
+  }
+}
+
+// Last stage of the operator fused with the per-k projections: forward FFT of the columns
+// along axis 3 and gather of the sphere (1/N^3), + (1/2|k+Q+G|^2 - eps_vk) x, + KB
+// sum_p beta_p D_p <beta_p|x>, then P_c, the output X and the partial Re(x^H X).
+// grid (nks, nvec), block 256.  smem: x, t [nbnd][npw_pad]; coefficients; reduction scratch.
+template <typename T, int N>
+__global__ void __launch_bounds__(256) k_zfwd_proj(SphereDev s, int nbnd, const cplx<T>* __restrict__ cbuf,
+                                                   int cb_ncol, const cplx<T>* __restrict__ xin,
+                                                   const T* __restrict__ kin, const double* __restrict__ eps,
+                                                   const cplx<T>* __restrict__ ukq, const cplx<T>* __restrict__ bkq,
+                                                   const double* __restrict__ dij, int nproj,
+                                                   cplx<T>* __restrict__ xout, double* __restrict__ part) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int npw_pad = s.npw_pad, nks = s.nks;
+  const int k = blockIdx.x, vec = blockIdx.y;
+  cplx<T>* xs = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* ts = xs + nbnd * npw_pad;
+  cplx<double>* cf = reinterpret_cast<cplx<double>*>(ts + nbnd * npw_pad);   // [max(nproj, nbnd) * nbnd]
+  double* red = reinterpret_cast<double*>(cf + (nproj > nbnd ? nproj : nbnd) * nbnd);
+  __shared__ T epsk[32];
+  const long base = ((long)vec * nks + k) * nbnd * npw_pad;
+  const int np = s.npw[k];
+  if (threadIdx.x < nbnd) epsk[threadIdx.x] = (T)eps[k * nbnd + threadIdx.x];
   __syncthreads();
   for (int i = threadIdx.x; i < nbnd * npw_pad; i += blockDim.x) {
     const int v = i / npw_pad, gi = i - v * npw_pad;
-    cplx<T> t = rs[i];
-    for (int w = 0; w < nbnd; ++w) {
-      const cplx<double> c = cf[w * nbnd + v];
-      t = t - cmul(uk[(long)w * npw_pad + gi], mk((T)c.x, (T)c.y));
-    }
-    R[base + i] = t;
+    const cplx<T> xv = xin[base + i];
+    xs[i] = xv;
+    ts[i] = xv * (kin[(long)k * npw_pad + gi] - epsk[v]);
   }
+  __syncthreads();
+  const int nc = s.ncol[k];
+  const T scale = T(1) / T(N * N * N);
+  for (int it = threadIdx.x; it < nbnd * nc; it += blockDim.x) {
+    const int v = it / nc, c = it - v * nc;
+    const long o = ((long)vec * nks + k) * nbnd + v;
+    const int4 cl = s.col[k * s.ncol_max + c];
+    const cplx<T>* src = cbuf + o * (long)N * cb_ncol + c;
+    cplx<T> a[N];
+#pragma unroll
+    for (int p = 0; p < N; ++p) a[p] = src[(long)p * cb_ncol];
+    fft_line<T, N, -1>(a);
+    cplx<T>* dst = ts + v * npw_pad + s.colstart[k * s.ncol_max + c];
+#pragma unroll
+    for (int p = 0; p < N; ++p) {
+      const int i = wrapn<N>(p - cl.z);
+      if (i < cl.w) dst[i] = dst[i] + a[p] * scale;
+    }
+  }
+  __syncthreads();
+  if (nproj > 0) {
+    const cplx<T>* bk = bkq + (long)k * nproj * npw_pad;
+    small_dots<T>(bk, npw_pad, xs, npw_pad, np, nproj, nbnd, dij, cf, red);   // D_p <beta_p|x_v>
+    cplx<T>* ct = reinterpret_cast<cplx<T>*>(red);    // the coefficients in T (red is free now)
+    for (int i = threadIdx.x; i < nproj * nbnd; i += blockDim.x) ct[i] = mk((T)cf[i].x, (T)cf[i].y);
+    __syncthreads();
+    for (int i = threadIdx.x; i < nbnd * npw_pad; i += blockDim.x) {
+      const int v = i / npw_pad, gi = i - v * npw_pad;
+      cplx<T> acc = ts[i];
+      for (int p = 0; p < nproj; ++p) acc = acc + cmul(bk[(long)p * npw_pad + gi], ct[p * nbnd + v]);
+      ts[i] = acc;
+    }
+    __syncthreads();
+  }
+  const cplx<T>* uk = ukq + (long)k * nbnd * npw_pad;
+  small_dots<T>(uk, npw_pad, ts, npw_pad, np, nbnd, nbnd, nullptr, cf, red);
+  subtract_projection<T>(ts, uk, cf, nbnd, npw_pad);
+  for (int i = threadIdx.x; i < nbnd * npw_pad; i += blockDim.x) xout[base + i] = ts[i];
+  small_dots<T>(xs, 0, ts, 0, nbnd * npw_pad, 1, 1, nullptr, cf, red);
+  if (threadIdx.x == 0) part[vec * nks + k] = cf[0].x;
 }
 
 // Non-Hermitian step j after the two operator applications XV = L v_j, XW = L^dag w_j:
 // v_hat = P_c(XV - gamma_j v_{j-1}), w_hat = P_c(XW - conj(beta_j) w_{j-1}) (stored in
-// XV, XW), per-k partials of s = (w_hat, v_hat) and of z_j = (y, v_j).  grid nks.
+// XV, XW), per-k partials of s = (w_hat, v_hat) and of z_j = (y, v_j).  grid nks, block 128.
 template <typename T>
 __global__ void __launch_bounds__(128) k_nh_update(int j, int upper, int nks, int nbnd, int npw_pad,
                                                    const int* __restrict__ npw, cplx<T>* __restrict__ XV,
@@ -556,68 +664,36 @@ __global__ void __launch_bounds__(128) k_nh_update(int j, int upper, int nks, in
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx<T>* vs = reinterpret_cast<cplx<T>*>(smem_raw);          // [nbnd][npw_pad]
   cplx<T>* ws = vs + nbnd * npw_pad;
-  cplx<double>* cf = reinterpret_cast<cplx<double>*>(ws + nbnd * npw_pad);   // [2 * nbnd * nbnd]
-  __shared__ double red[2][4];
+  cplx<double>* cf = reinterpret_cast<cplx<double>*>(ws + nbnd * npw_pad);   // [nbnd * nbnd]
+  double* red = reinterpret_cast<double*>(cf + nbnd * nbnd);
   const int k = blockIdx.x;
   const long base = (long)k * nbnd * npw_pad;
   const int np = npw[k];
   const double bj = co.beta[j - 1];
   const cplx<double> gj = co.gamma[j - 1];
   const cplx<T> g = mk((T)gj.x, (T)gj.y), bc = mk((T)bj, (T)0);
+  if (upper) {  // z_j = (y, v_j), the whole k block as one vector
+    block_dots<T>(y + base, 0, Vc + base, 0, nbnd * npw_pad, 1, 1, nullptr, cf, red);
+    if (threadIdx.x == 0) co.zpart[(long)(j - 1) * nks + k] = cf[0];
+  } else if (threadIdx.x == 0) {
+    co.zpart[(long)(j - 1) * nks + k] = mk(0.0, 0.0);
+  }
   for (int i = threadIdx.x; i < nbnd * npw_pad; i += blockDim.x) {
     vs[i] = XV[base + i] - cmul(g, Vp[base + i]);
     ws[i] = XW[base + i] - cmul(bc, Wp[base + i]);
   }
   __syncthreads();
   const cplx<T>* uk = ukq + base;
-  pair_dots<T>(uk, npw_pad, vs, npw_pad, np, nbnd, nbnd, nullptr, cf);
-  pair_dots<T>(uk, npw_pad, ws, npw_pad, np, nbnd, nbnd, nullptr, cf + nbnd * nbnd);
-  __syncthreads();
-  double sr = 0.0, si = 0.0;
+  block_dots<T>(uk, npw_pad, vs, npw_pad, np, nbnd, nbnd, nullptr, cf, red);
+  subtract_projection<T>(vs, uk, cf, nbnd, npw_pad);
+  block_dots<T>(uk, npw_pad, ws, npw_pad, np, nbnd, nbnd, nullptr, cf, red);
+  subtract_projection<T>(ws, uk, cf, nbnd, npw_pad);
   for (int i = threadIdx.x; i < nbnd * npw_pad; i += blockDim.x) {
-    const int v = i / npw_pad, gi = i - v * npw_pad;
-    cplx<T> a = vs[i], b2 = ws[i];
-    for (int w = 0; w < nbnd; ++w) {
-      const cplx<double> c = cf[w * nbnd + v], d = cf[nbnd * nbnd + w * nbnd + v];
-      const cplx<T> u = uk[(long)w * npw_pad + gi];
-      a = a - cmul(u, mk((T)c.x, (T)c.y));
-      b2 = b2 - cmul(u, mk((T)d.x, (T)d.y));
-    }
-    XV[base + i] = a;
-    XW[base + i] = b2;
-    const cplx<T> t = cjmul(b2, a);
-    sr += (double)t.x;
-    si += (double)t.y;
+    XV[base + i] = vs[i];
+    XW[base + i] = ws[i];
   }
-  sr = warp_sum(sr);
-  si = warp_sum(si);
-  if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = sr; red[1][threadIdx.x >> 5] = si; }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = 0, b3 = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += red[0][w]; b3 += red[1][w]; }
-    spart[k] = mk(a, b3);
-  }
-  // z_j = (y, v_j) when v_j is upper
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  if (upper) {
-    for (int v = warp; v < nbnd; v += nw) {
-      T re = 0, im = 0;
-      for (int gg = lane; gg < np; gg += 32) {
-        const cplx<T> t = cjmul(y[base + (long)v * npw_pad + gg], Vc[base + (long)v * npw_pad + gg]);
-        re += t.x; im += t.y;
-      }
-      const double dr = warp_sum((double)re), di = warp_sum((double)im);
-      if (lane == 0) cf[v] = mk(dr, di);
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double zr = 0, zi = 0;
-    if (upper) for (int v = 0; v < nbnd; ++v) { zr += cf[v].x; zi += cf[v].y; }
-    co.zpart[(long)(j - 1) * nks + k] = mk(zr, zi);
-  }
+  block_dots<T>(ws, 0, vs, 0, nbnd * npw_pad, 1, 1, nullptr, cf, red);
+  if (threadIdx.x == 0) spart[k] = cf[0];
 }
 
 // Non-Hermitian normalisation at the end of step j: beta_{j+1} = sqrt|s|, gamma_{j+1} =
@@ -631,11 +707,9 @@ __global__ void __launch_bounds__(128) k_nh_normalize(int j, int nks, int nbnd, 
                                                       double tol) {
   __shared__ cplx<double> sc[2];
   const int k = blockIdx.x;
+  const double sr = block_mean(reinterpret_cast<const double*>(spart), nks, 2, 0);
+  const double si = block_mean(reinterpret_cast<const double*>(spart), nks, 2, 1);
   if (threadIdx.x == 0) {
-    double sr = 0, si = 0;
-    for (int i = 0; i < nks; ++i) { sr += spart[i].x; si += spart[i].y; }
-    sr /= nks;
-    si /= nks;
     const double a = sqrt(sr * sr + si * si);
     double b = sqrt(a);
     cplx<double> gm = mk(sr / b, si / b);
@@ -662,7 +736,7 @@ __global__ void __launch_bounds__(128) k_nh_normalize(int j, int nks, int nbnd, 
 
 // z_j = (1/nks) sum_k zpart[j][k] for j in [j0, j1).
 static __global__ void k_reduce_z(const cplx<double>* __restrict__ zpart, int nks, int j0, int j1,
-                           cplx<double>* __restrict__ z) {
+                                  cplx<double>* __restrict__ z) {
   const int j = j0 + blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= j1) return;
   double zr = 0, zi = 0;

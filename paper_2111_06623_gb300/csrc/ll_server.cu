@@ -1,0 +1,348 @@
+// Request loop of libll.so: continuous batching of Lanczos chains of different sizes.
+//
+// A scheduler thread owns every running chain.  Each round it (1) admits queued jobs, in
+// arrival order, while a slot is free and the job's device footprint fits the remaining HBM
+// budget, creating the chain on a stream of its own; (2) queues the next chunk of Lanczos steps
+// of every running chain on that chain's stream, so that the chains' kernels overlap on the
+// GPU; (3) waits for the round, and finishes the chains that reached their step count: the
+// spectrum on the device, the coefficients and spectrum copied to the job, the chain's memory
+// released for the next admissions.  Jobs are independent: a chain's result does not depend
+// on what runs beside it (deterministic kernels, no shared state).
+#include <string.h>
+
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "chain.cuh"
+
+namespace {
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct Job {
+  uint64_t id = 0;
+  int state = LL_JOB_QUEUED;
+  int status = LL_OK;
+  std::string err;
+  // deep copy of the system (dropped when the job ends)
+  std::vector<double> kcart, u_k, u_kq, eps_k, vloc, rho, beta_kq, dij, omega;
+  std::vector<int> npw_k, miller_k, npw_kq, miller_kq;
+  ll_system_desc desc{};
+  int n_steps = 0;
+  double eta = 0.0;
+  size_t footprint = 0;
+  ll::ChainBase* chain = nullptr;
+  cudaStream_t stream = nullptr;
+  int steps_done = 0;
+  std::vector<double> beta;
+  std::vector<double> gamma, z, chi, eps_inv, eps;  // complex interleaved
+  double t_submit = 0, t_start = 0, t_done = 0;
+};
+
+}  // namespace
+
+struct ll_server {
+  size_t budget = 0, used = 0, peak = 0;
+  int max_slots = 1, chunk = 64, device = 0;
+  std::mutex mu;
+  std::condition_variable cv;
+  bool stop = false;
+  std::deque<Job*> queue;
+  std::vector<Job*> running;
+  std::map<uint64_t, Job*> jobs;
+  uint64_t next_id = 1;
+  std::thread th;
+};
+
+namespace {
+
+thread_local std::string g_srv_err;
+int sfail(int code, const std::string& m) {
+  g_srv_err = m;
+  return code;
+}
+
+template <typename V>
+void copy_in(std::vector<V>& dst, const V* src, size_t n) {
+  dst.assign(src, src + n);
+}
+
+void finish(ll_server* s, Job* j, int status, const std::string& err) {
+  if (j->chain) {
+    delete j->chain;
+    j->chain = nullptr;
+  }
+  if (j->stream) {
+    cudaStreamDestroy(j->stream);
+    j->stream = nullptr;
+  }
+  std::lock_guard<std::mutex> lock(s->mu);
+  s->used -= j->footprint;
+  j->status = status;
+  j->err = err;
+  j->state = (status == LL_OK) ? LL_JOB_DONE : LL_JOB_FAILED;
+  j->t_done = now_s();
+  for (auto* v : {&j->u_k, &j->u_kq, &j->beta_kq, &j->vloc, &j->rho}) std::vector<double>().swap(*v);
+  std::vector<int>().swap(j->miller_k);
+  std::vector<int>().swap(j->miller_kq);
+  s->cv.notify_all();
+}
+
+void start_job(ll_server* s, Job* j) {
+  std::string err;
+  j->t_start = now_s();
+  if (cudaStreamCreateWithFlags(&j->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    finish(s, j, LL_ECUDA, "stream creation failed");
+    return;
+  }
+  j->chain = (j->desc.precision == LL_PREC_FP64) ? ll::make_chain_f64() : ll::make_chain_f32();
+  const int rc = j->chain->create(&j->desc, j->stream, err);
+  if (rc != LL_OK) {
+    finish(s, j, rc, "create: " + err);
+    return;
+  }
+  std::lock_guard<std::mutex> lock(s->mu);
+  // account the real allocation instead of the estimate
+  const size_t real = j->chain->bytes();
+  s->used = s->used - j->footprint + real;
+  j->footprint = real;
+  s->peak = std::max(s->peak, s->used);
+  j->state = LL_JOB_RUNNING;
+}
+
+void complete_job(ll_server* s, Job* j, int lanczos_rc, const std::string& lerr) {
+  std::string err;
+  const int m = j->steps_done;
+  if (m > 0) {
+    j->beta.resize(m);
+    j->gamma.resize(2 * (size_t)m);
+    j->z.resize(2 * (size_t)m);
+    int done = 0;
+    j->chain->collect(j->beta.data(), j->gamma.data(), j->z.data(), &done, err);
+    const int nw = (int)j->omega.size();
+    if (nw > 0) {
+      j->chi.resize(2 * (size_t)nw);
+      j->eps_inv.resize(2 * (size_t)nw);
+      j->eps.resize(2 * (size_t)nw);
+      const int rc = j->chain->spectrum(m, j->omega.data(), nw, j->eta, j->chi.data(), j->eps_inv.data(),
+                                        j->eps.data(), err);
+      if (rc != LL_OK && lanczos_rc == LL_OK) {
+        finish(s, j, rc, "spectrum: " + err);
+        return;
+      }
+    }
+  }
+  finish(s, j, lanczos_rc, lerr);
+}
+
+void scheduler(ll_server* s) {
+  cudaSetDevice(s->device);
+  while (true) {
+    std::vector<Job*> admit;
+    {
+      std::unique_lock<std::mutex> lock(s->mu);
+      if (s->running.empty() && s->queue.empty())
+        s->cv.wait_for(lock, std::chrono::milliseconds(50), [&] { return s->stop || !s->queue.empty(); });
+      if (s->stop) break;
+      while (!s->queue.empty() && (int)s->running.size() + (int)admit.size() < s->max_slots &&
+             s->queue.front()->footprint <= s->budget - s->used) {
+        Job* j = s->queue.front();
+        s->queue.pop_front();
+        s->used += j->footprint;
+        s->peak = std::max(s->peak, s->used);
+        admit.push_back(j);
+      }
+    }
+    for (Job* j : admit) {
+      start_job(s, j);
+      if (j->state == LL_JOB_RUNNING) {
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->running.push_back(j);
+      }
+    }
+    std::vector<Job*> run;
+    int chunk;
+    {
+      std::lock_guard<std::mutex> lock(s->mu);
+      run = s->running;
+      chunk = s->chunk;
+    }
+    if (run.empty()) continue;
+    // one round: queue a chunk of steps on every running chain, then wait for each
+    std::vector<int> rcs(run.size(), LL_OK);
+    std::vector<std::string> errs(run.size());
+    for (size_t i = 0; i < run.size(); ++i) {
+      const int n = std::min(chunk, run[i]->n_steps - run[i]->chain->steps_queued());
+      if (n > 0) rcs[i] = run[i]->chain->enqueue(n, errs[i]);
+    }
+    std::vector<Job*> still;
+    for (size_t i = 0; i < run.size(); ++i) {
+      Job* j = run[i];
+      int done = 0;
+      std::string err = errs[i];
+      int rc = rcs[i];
+      if (rc == LL_OK) rc = j->chain->collect(nullptr, nullptr, nullptr, &done, err);
+      j->steps_done = done;
+      if (rc != LL_OK || done >= j->n_steps) complete_job(s, j, rc, err);
+      else still.push_back(j);
+    }
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->running.swap(still);
+  }
+  std::vector<Job*> left;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    left.swap(s->running);
+  }
+  for (Job* j : left) finish(s, j, LL_ECUDA, "server destroyed");
+}
+
+}  // namespace
+
+extern "C" {
+
+int ll_server_create(size_t hbm_budget_bytes, int max_slots, ll_server** out) {
+  if (!out || hbm_budget_bytes == 0 || max_slots < 1) return sfail(LL_EINVAL, "bad server arguments");
+  ll_server* s = new ll_server();
+  s->budget = hbm_budget_bytes;
+  s->max_slots = max_slots;
+  cudaGetDevice(&s->device);
+  cudaGetLastError();
+  s->th = std::thread(scheduler, s);
+  *out = s;
+  return LL_OK;
+}
+
+int ll_server_set_chunk(ll_server* s, int steps) {
+  if (!s || steps < 1) return sfail(LL_EINVAL, "bad chunk");
+  std::lock_guard<std::mutex> lock(s->mu);
+  s->chunk = steps;
+  return LL_OK;
+}
+
+int ll_submit(ll_server* s, const ll_job_desc* jd, uint64_t* job_id) {
+  if (!s || !jd || !job_id) return sfail(LL_EINVAL, "bad submit arguments");
+  const ll_system_desc* d = &jd->sys;
+  if (jd->n_steps < 1 || jd->n_steps > d->max_steps) return sfail(LL_EINVAL, "n_steps outside [1, max_steps]");
+  if (d->nks < 1 || d->nbnd < 1 || d->nfft < 1 || d->nproj < 0 || !d->npw_k || !d->npw_kq || !d->kcart ||
+      !d->miller_k || !d->miller_kq || !d->u_k || !d->u_kq || !d->eps_k || !d->vloc_r || !d->rho_r ||
+      (d->nproj > 0 && (!d->beta_kq || !d->dij)) || (jd->n_omega > 0 && !jd->omega_ev))
+    return sfail(LL_EINVAL, "malformed job");
+  size_t fp = 0;
+  if (ll_footprint(d, &fp) != LL_OK) return sfail(LL_EINVAL, "footprint");
+  if (fp > s->budget) return sfail(LL_ENOMEM, "job footprint exceeds the whole HBM budget");
+  Job* j = new Job();
+  size_t sk = 0, sq = 0;
+  for (int k = 0; k < d->nks; ++k) {
+    sk += d->npw_k[k];
+    sq += d->npw_kq[k];
+  }
+  const size_t n3 = (size_t)d->nfft * d->nfft * d->nfft;
+  copy_in(j->kcart, d->kcart, 3 * (size_t)d->nks);
+  copy_in(j->npw_k, d->npw_k, d->nks);
+  copy_in(j->npw_kq, d->npw_kq, d->nks);
+  copy_in(j->miller_k, d->miller_k, 3 * sk);
+  copy_in(j->miller_kq, d->miller_kq, 3 * sq);
+  copy_in(j->u_k, d->u_k, 2 * sk * d->nbnd);
+  copy_in(j->u_kq, d->u_kq, 2 * sq * d->nbnd);
+  copy_in(j->eps_k, d->eps_k, (size_t)d->nks * d->nbnd);
+  copy_in(j->vloc, d->vloc_r, n3);
+  copy_in(j->rho, d->rho_r, n3);
+  if (d->nproj > 0) {
+    copy_in(j->beta_kq, d->beta_kq, 2 * sq * d->nproj);
+    copy_in(j->dij, d->dij, d->nproj);
+  }
+  if (jd->n_omega > 0) copy_in(j->omega, jd->omega_ev, jd->n_omega);
+  j->desc = *d;
+  j->desc.kcart = j->kcart.data();
+  j->desc.npw_k = j->npw_k.data();
+  j->desc.npw_kq = j->npw_kq.data();
+  j->desc.miller_k = j->miller_k.data();
+  j->desc.miller_kq = j->miller_kq.data();
+  j->desc.u_k = j->u_k.data();
+  j->desc.u_kq = j->u_kq.data();
+  j->desc.eps_k = j->eps_k.data();
+  j->desc.vloc_r = j->vloc.data();
+  j->desc.rho_r = j->rho.data();
+  j->desc.beta_kq = d->nproj > 0 ? j->beta_kq.data() : nullptr;
+  j->desc.dij = d->nproj > 0 ? j->dij.data() : nullptr;
+  j->n_steps = jd->n_steps;
+  j->eta = jd->eta_ev;
+  j->footprint = fp;
+  j->t_submit = now_s();
+  std::lock_guard<std::mutex> lock(s->mu);
+  j->id = s->next_id++;
+  s->jobs[j->id] = j;
+  s->queue.push_back(j);
+  *job_id = j->id;
+  s->cv.notify_all();
+  return LL_OK;
+}
+
+int ll_poll(ll_server* s, uint64_t id, int* state, ll_job_result* res) {
+  if (!s || !state) return sfail(LL_EINVAL, "bad poll arguments");
+  std::lock_guard<std::mutex> lock(s->mu);
+  auto it = s->jobs.find(id);
+  if (it == s->jobs.end()) return sfail(LL_ENOTFOUND, "unknown job id");
+  Job* j = it->second;
+  *state = j->state;
+  if (!res) return LL_OK;
+  const double t = now_s();
+  res->status = j->status;
+  res->steps_done = j->steps_done;
+  res->queue_s = (j->t_start > 0 ? j->t_start : t) - j->t_submit;
+  res->run_s = j->t_start > 0 ? (j->t_done > 0 ? j->t_done : t) - j->t_start : 0.0;
+  if (j->state == LL_JOB_DONE || j->state == LL_JOB_FAILED) {
+    const size_t m = j->beta.size(), nw = j->chi.size() / 2;
+    if (res->beta && m) memcpy(res->beta, j->beta.data(), m * sizeof(double));
+    if (res->gamma && m) memcpy(res->gamma, j->gamma.data(), 2 * m * sizeof(double));
+    if (res->z && m) memcpy(res->z, j->z.data(), 2 * m * sizeof(double));
+    if (res->chi && nw) memcpy(res->chi, j->chi.data(), 2 * nw * sizeof(double));
+    if (res->eps_inv && nw) memcpy(res->eps_inv, j->eps_inv.data(), 2 * nw * sizeof(double));
+    if (res->eps && nw) memcpy(res->eps, j->eps.data(), 2 * nw * sizeof(double));
+    if (j->state == LL_JOB_FAILED) g_srv_err = j->err;
+  }
+  return LL_OK;
+}
+
+int ll_server_stats(ll_server* s, size_t* used, size_t* peak, int* running, int* queued) {
+  if (!s) return sfail(LL_EINVAL, "null server");
+  std::lock_guard<std::mutex> lock(s->mu);
+  if (used) *used = s->used;
+  if (peak) *peak = s->peak;
+  if (running) *running = (int)s->running.size();
+  if (queued) *queued = (int)s->queue.size();
+  return LL_OK;
+}
+
+const char* ll_server_last_error(void) { return g_srv_err.c_str(); }
+
+int ll_server_destroy(ll_server* s) {
+  if (!s) return LL_OK;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->stop = true;
+    for (Job* j : s->queue) {
+      j->state = LL_JOB_FAILED;
+      j->status = LL_ECUDA;
+      j->err = "server destroyed before admission";
+    }
+    s->queue.clear();
+    s->cv.notify_all();
+  }
+  if (s->th.joinable()) s->th.join();
+  for (auto& kv : s->jobs) delete kv.second;
+  delete s;
+  return LL_OK;
+}
+
+}  // extern "C"

@@ -60,6 +60,14 @@ def _load():
         "ll_footprint": (C.c_int, [C.POINTER(SystemDesc), C.POINTER(C.c_size_t)]),
         "ll_profile": (C.c_int, [vp, C.c_int]),
         "ll_profile_read": (C.c_int, [vp, _dp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
+        "ll_server_create": (C.c_int, [C.c_size_t, C.c_int, C.POINTER(vp)]),
+        "ll_server_set_chunk": (C.c_int, [vp, C.c_int]),
+        "ll_submit": (C.c_int, [vp, vp, C.POINTER(C.c_uint64)]),
+        "ll_poll": (C.c_int, [vp, C.c_uint64, C.POINTER(C.c_int), vp]),
+        "ll_server_stats": (C.c_int, [vp, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t), C.POINTER(C.c_int),
+                                      C.POINTER(C.c_int)]),
+        "ll_server_last_error": (C.c_char_p, []),
+        "ll_server_destroy": (C.c_int, [vp]),
         "ll_last_error": (C.c_char_p, []),
         "ll_version": (C.c_char_p, []),
     }
@@ -72,8 +80,10 @@ def _load():
 _lib = _load()
 EXPORTS = ("ll_create", "ll_destroy", "ll_lanczos", "ll_lanczos_spectrum", "ll_spectrum", "ll_spectrum_static",
            "ll_apply", "ll_get_map", "ll_get_start", "ll_footprint", "ll_profile", "ll_profile_read", "ll_last_error",
-           "ll_version")
-PROF_CLASSES = ("zinv", "xy1", "hxc", "xy2", "zfwd", "proj", "update")
+           "ll_version", "ll_server_create",
+           "ll_server_set_chunk", "ll_submit", "ll_poll", "ll_server_stats", "ll_server_last_error",
+           "ll_server_destroy")
+PROF_CLASSES = ("zinv", "xy1", "hxc", "xy2", "zfwd", "update")
 
 
 def version() -> str:
@@ -97,48 +107,53 @@ def _cat_complex(blocks) -> np.ndarray:
     return np.ascontiguousarray(np.concatenate([np.ascontiguousarray(b, dtype=np.complex128).ravel() for b in blocks]))
 
 
+def _make_desc(*, lattice, nfft, kcart, miller_k, miller_kq, u_k, u_kq, eps_k, vloc_r, rho_r, beta_kq=None,
+               dij=None, q_cart, approx="tddft", flavour="ph", precision="fp64", max_steps=1000):
+    """An ll_system_desc and the arrays it points into (keep them alive while it is used)."""
+    nks = len(miller_k)
+    nbnd = int(u_k[0].shape[0])
+    nproj = int(beta_kq[0].shape[0]) if beta_kq is not None and len(beta_kq) and beta_kq[0].shape[0] else 0
+    k = dict(
+        kcart=np.ascontiguousarray(kcart, dtype=np.float64),
+        npw_k=np.array([len(m) for m in miller_k], dtype=np.int32),
+        miller_k=np.ascontiguousarray(np.concatenate(miller_k), dtype=np.int32),
+        npw_kq=np.array([len(m) for m in miller_kq], dtype=np.int32),
+        miller_kq=np.ascontiguousarray(np.concatenate(miller_kq), dtype=np.int32),
+        u_k=_cat_complex(u_k), u_kq=_cat_complex(u_kq),
+        eps_k=np.ascontiguousarray(eps_k, dtype=np.float64),
+        vloc_r=np.ascontiguousarray(vloc_r, dtype=np.float64),
+        rho_r=np.ascontiguousarray(rho_r, dtype=np.float64),
+        beta_kq=_cat_complex(beta_kq) if nproj else np.zeros(2),
+        dij=np.ascontiguousarray(dij if nproj else np.zeros(1), dtype=np.float64),
+    )
+    d = SystemDesc()
+    for i in range(3):
+        for j in range(3):
+            d.lattice[i][j] = float(lattice[i][j])
+        d.q_cart[i] = float(q_cart[i])
+    d.nfft, d.nks, d.nbnd, d.nproj = int(nfft), nks, nbnd, nproj
+    d.kcart, d.npw_k, d.miller_k = _d(k["kcart"]), _i(k["npw_k"]), _i(k["miller_k"])
+    d.npw_kq, d.miller_kq = _i(k["npw_kq"]), _i(k["miller_kq"])
+    d.u_k, d.u_kq, d.eps_k = _d(k["u_k"].view(np.float64)), _d(k["u_kq"].view(np.float64)), _d(k["eps_k"])
+    d.vloc_r, d.rho_r = _d(k["vloc_r"]), _d(k["rho_r"])
+    d.beta_kq = _d(k["beta_kq"].view(np.float64)) if nproj else None
+    d.dij = _d(k["dij"])
+    d.approx, d.flavour, d.precision = APPROX[approx], FLAVOUR[flavour], PRECISION[precision]
+    d.max_steps = int(max_steps)
+    return d, k
+
+
 class Chain:
     """One Lanczos chain resident on the device (ll_create ... ll_destroy)."""
 
-    def __init__(self, *, lattice, nfft, kcart, miller_k, miller_kq, u_k, u_kq, eps_k, vloc_r, rho_r,
-                 beta_kq=None, dij=None, q_cart, approx="tddft", flavour="ph", precision="fp64",
-                 max_steps=1000, stream=None):
-        nks = len(miller_k)
-        nbnd = int(u_k[0].shape[0])
-        nproj = int(beta_kq[0].shape[0]) if beta_kq is not None and len(beta_kq) and beta_kq[0].shape[0] else 0
-        self._keep = dict(
-            kcart=np.ascontiguousarray(kcart, dtype=np.float64),
-            npw_k=np.array([len(m) for m in miller_k], dtype=np.int32),
-            miller_k=np.ascontiguousarray(np.concatenate(miller_k), dtype=np.int32),
-            npw_kq=np.array([len(m) for m in miller_kq], dtype=np.int32),
-            miller_kq=np.ascontiguousarray(np.concatenate(miller_kq), dtype=np.int32),
-            u_k=_cat_complex(u_k), u_kq=_cat_complex(u_kq),
-            eps_k=np.ascontiguousarray(eps_k, dtype=np.float64),
-            vloc_r=np.ascontiguousarray(vloc_r, dtype=np.float64),
-            rho_r=np.ascontiguousarray(rho_r, dtype=np.float64),
-            beta_kq=_cat_complex(beta_kq) if nproj else np.zeros(2),
-            dij=np.ascontiguousarray(dij if nproj else np.zeros(1), dtype=np.float64),
-        )
-        k = self._keep
-        d = SystemDesc()
-        for i in range(3):
-            for j in range(3):
-                d.lattice[i][j] = float(lattice[i][j])
-            d.q_cart[i] = float(q_cart[i])
-        d.nfft, d.nks, d.nbnd, d.nproj = int(nfft), nks, nbnd, nproj
-        d.kcart, d.npw_k, d.miller_k = _d(k["kcart"]), _i(k["npw_k"]), _i(k["miller_k"])
-        d.npw_kq, d.miller_kq = _i(k["npw_kq"]), _i(k["miller_kq"])
-        d.u_k, d.u_kq, d.eps_k = _d(k["u_k"].view(np.float64)), _d(k["u_kq"].view(np.float64)), _d(k["eps_k"])
-        d.vloc_r, d.rho_r = _d(k["vloc_r"]), _d(k["rho_r"])
-        d.beta_kq = _d(k["beta_kq"].view(np.float64)) if nproj else None
-        d.dij = _d(k["dij"])
-        d.approx, d.flavour, d.precision = APPROX[approx], FLAVOUR[flavour], PRECISION[precision]
-        d.max_steps = int(max_steps)
+    def __init__(self, *, stream=None, **system):
+        d, k = _make_desc(**system)
+        self._keep = k
         self.desc = d
-        self.nks, self.nbnd, self.max_steps = nks, nbnd, int(max_steps)
+        self.nks, self.nbnd, self.max_steps = d.nks, d.nbnd, d.max_steps
         self.npw_kq = k["npw_kq"].copy()
-        self.lattice = np.asarray(lattice, dtype=np.float64)
-        self.q_cart = np.asarray(q_cart, dtype=np.float64)
+        self.lattice = np.asarray(system["lattice"], dtype=np.float64)
+        self.q_cart = np.asarray(system["q_cart"], dtype=np.float64)
         h = C.c_void_p()
         _check(_lib.ll_create(C.byref(d), C.c_void_p(stream) if stream else None, C.byref(h)))
         self._h = h
@@ -253,3 +268,85 @@ def spectrum_static(beta, gamma, z, omega_cell, q_cart, omega_ev, eta_ev, stream
                                    float(omega_cell), _d(q), _d(w), len(w), float(eta_ev),
                                    *[_d(o.view(np.float64)) for o in out], C.c_void_p(stream) if stream else None))
     return tuple(out)
+
+
+class JobDesc(C.Structure):
+    _fields_ = [("sys", SystemDesc), ("n_steps", C.c_int), ("omega_ev", _dp), ("n_omega", C.c_int),
+                ("eta_ev", C.c_double)]
+
+
+class JobResult(C.Structure):
+    _fields_ = [("status", C.c_int), ("steps_done", C.c_int), ("queue_s", C.c_double), ("run_s", C.c_double),
+                ("beta", _dp), ("gamma", _dp), ("z", _dp), ("chi", _dp), ("eps_inv", _dp), ("eps", _dp)]
+
+
+JOB_QUEUED, JOB_RUNNING, JOB_DONE, JOB_FAILED = 0, 1, 2, 3
+
+
+def _srv_check(rc: int):
+    if rc != LL_OK:
+        raise LLError(rc, _lib.ll_server_last_error().decode())
+
+
+class Server:
+    """The request loop (ll_server_*): continuous batching of chains under an HBM budget."""
+
+    def __init__(self, hbm_budget_bytes: int, max_slots: int, chunk: int | None = None):
+        h = C.c_void_p()
+        _srv_check(_lib.ll_server_create(C.c_size_t(int(hbm_budget_bytes)), int(max_slots), C.byref(h)))
+        self._h = h
+        self._jobs = {}
+        if chunk:
+            _srv_check(_lib.ll_server_set_chunk(self._h, int(chunk)))
+
+    def submit(self, n_steps: int, omega_ev, eta_ev: float, **system) -> int:
+        d, keep = _make_desc(**system)
+        w = np.ascontiguousarray(omega_ev if omega_ev is not None else np.zeros(0), dtype=np.float64)
+        jd = JobDesc()
+        jd.sys = d
+        jd.n_steps = int(n_steps)
+        jd.omega_ev = _d(w) if len(w) else None
+        jd.n_omega = len(w)
+        jd.eta_ev = float(eta_ev)
+        jid = C.c_uint64(0)
+        _srv_check(_lib.ll_submit(self._h, C.byref(jd), C.byref(jid)))
+        self._jobs[jid.value] = (int(n_steps), len(w))
+        return jid.value
+
+    def poll(self, job_id: int):
+        """(state, result dict): status, steps_done, queue_s, run_s, and once the job has ended
+        its coefficients and spectrum."""
+        n, nw = self._jobs.get(job_id, (0, 0))
+        out = dict(beta=np.zeros(n), gamma=np.zeros(n, dtype=np.complex128), z=np.zeros(n, dtype=np.complex128),
+                   chi=np.zeros(nw, dtype=np.complex128), eps_inv=np.zeros(nw, dtype=np.complex128),
+                   eps=np.zeros(nw, dtype=np.complex128))
+        r = JobResult()
+        for key in ("beta", "gamma", "z", "chi", "eps_inv", "eps"):
+            setattr(r, key, _d(out[key].view(np.float64)) if out[key].size else None)
+        st = C.c_int(0)
+        _srv_check(_lib.ll_poll(self._h, C.c_uint64(job_id), C.byref(st), C.byref(r)))
+        res = dict(status=r.status, steps_done=r.steps_done, queue_s=r.queue_s, run_s=r.run_s)
+        if st.value in (JOB_DONE, JOB_FAILED):
+            m = r.steps_done
+            res.update(beta=out["beta"][:m], gamma=out["gamma"][:m], z=out["z"][:m], chi=out["chi"],
+                       eps_inv=out["eps_inv"], eps=out["eps"])
+            if st.value == JOB_FAILED:
+                res["error"] = _lib.ll_server_last_error().decode()
+        return st.value, res
+
+    def stats(self):
+        used, peak = C.c_size_t(0), C.c_size_t(0)
+        run, q = C.c_int(0), C.c_int(0)
+        _srv_check(_lib.ll_server_stats(self._h, C.byref(used), C.byref(peak), C.byref(run), C.byref(q)))
+        return dict(used=used.value, peak=peak.value, running=run.value, queued=q.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.ll_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

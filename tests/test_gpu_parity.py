@@ -182,3 +182,29 @@ def test_indefinite_metric_reported(lib, tiny):
     with pytest.raises(lib.LLError) as e:
         chain_from_bundle(b, max_steps=4)
     assert e.value.code == lib.LL_ENOTPD
+
+
+@pytest.fixture(scope="module")
+def kb():
+    return w.get_bundle(w.config_kb())
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+def test_kb_workload_single_application(lib, kb, precision, tol):
+    """The benchmark workload at full size (2048 orbitals, 32^3, 8 KB projectors per k), in
+    the launch configuration the benchmark times: both operator halves against the oracle."""
+    sys = System(kb)
+    ch = chain_from_bundle(kb, precision=precision, max_steps=4)
+    x = _rand(sys, 11)
+    for upper in (False, True):
+        assert rel_batch(ch.apply(x, upper), sys.apply_op(x, upper)) < tol
+
+
+def test_kb_workload_first_coefficients(lib, kb):
+    """First 6 pseudo-Hermitian steps of the benchmark workload, FP64 and FP32 paths."""
+    sys = System(kb)
+    ref = lanczos.pseudo_hermitian(sys, 6)
+    got64 = chain_from_bundle(kb, max_steps=6).lanczos(6)
+    assert _coef_rel(got64, ref, 6) < 1e-10
+    got32 = chain_from_bundle(kb, precision="fp32", max_steps=6).lanczos(6)
+    assert _coef_rel(got32, ref, 6) < 1e-4

@@ -1,0 +1,50 @@
+"""Host-side behaviour of the request loop that needs no GPU: refusals at submit."""
+import numpy as np
+import pytest
+
+import workloads as w
+
+
+@pytest.fixture(scope="module")
+def ll():
+    from paper_2111_06623_gb300.build import build_library
+    build_library()
+    from paper_2111_06623_gb300 import ll as mod
+    return mod
+
+
+def _system(b, **kw):
+    s = b.spec
+    d = dict(lattice=s.lattice, nfft=s.nfft, kcart=b.kcart, miller_k=b.miller_k, miller_kq=b.miller_kq, u_k=b.u_k,
+             u_kq=b.u_kq, eps_k=b.eps_k, vloc_r=b.vloc_r, rho_r=b.rho_r, beta_kq=b.beta_kq, dij=b.dij,
+             q_cart=s.q_cart, max_steps=50)
+    d.update(kw)
+    return d
+
+
+def test_over_budget_job_refused_at_submit(ll):
+    b = w.get_bundle(w.config_tiny())
+    srv = ll.Server(hbm_budget_bytes=1 << 16, max_slots=2)
+    with pytest.raises(ll.LLError) as e:
+        srv.submit(20, np.linspace(0, 40, 11), 0.1, **_system(b))
+    assert e.value.code == ll.LL_ENOMEM and "budget" in str(e.value)
+    srv.close()
+
+
+def test_bad_step_count_and_unknown_job(ll):
+    b = w.get_bundle(w.config_tiny())
+    srv = ll.Server(hbm_budget_bytes=1 << 34, max_slots=2)
+    with pytest.raises(ll.LLError) as e:
+        srv.submit(80, None, 0.1, **_system(b, max_steps=50))
+    assert e.value.code == ll.LL_EINVAL
+    with pytest.raises(ll.LLError) as e:
+        srv.poll(12345)
+    assert e.value.code == ll.LL_ENOTFOUND
+    srv.close()
+
+
+def test_server_arguments(ll):
+    with pytest.raises(ll.LLError):
+        ll.Server(hbm_budget_bytes=0, max_slots=1)
+    with pytest.raises(ll.LLError):
+        ll.Server(hbm_budget_bytes=1 << 30, max_slots=0)
