@@ -675,7 +675,7 @@ class Chain : public ChainBase {
   template <int N>
   int hxc_n(std::string& err) {
     const T scale = (T)(4.0 / (omega_ * nks_));
-    k_hxc_fwd<T, N><<<N, 64, 0, st_>>>(nprt_, last_ng_, scale, nr_, ng_);
+    k_hxc_fwd<T, N><<<N, 256, 0, st_>>>(nprt_, last_ng_, scale, nr_, ng_);
     k_hxc_z<T, N><<<(N * N + 63) / 64, 64, 0, st_>>>(ng_, whart_);
     k_hxc_inv<T, N><<<N, 64, 0, st_>>>(ng_, nr_, fxc_, vpr_);
     LL_CK(cudaGetLastError());

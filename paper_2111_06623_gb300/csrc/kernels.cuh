@@ -66,6 +66,7 @@ __device__ __forceinline__ void cp_async(void* smem_dst, const void* gmem_src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 // every committed group but the most recent one has landed
 __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
 
 // ---------------------------------------------------------------------------------------
 // Per-plane pass of one operator application.  grid (N planes, groups), block 128.
@@ -121,11 +122,13 @@ __global__ void __launch_bounds__(128, 4) k_xy(XYArgs a, cplx<T>* __restrict__ c
   const int o_end = a.o_off + min(a.norb, g * a.per_group + a.per_group);
   auto stage_u = [&](int obatch, int stage) {
     const int nbb = min(BO, o_end - obatch);
-    cplx<T>* dst = Us + stage * (BO * N * NP);
-    for (int i = threadIdx.x; i < nbb * N * N; i += blockDim.x) {
-      const int b = i / (N * N), r = i - b * N * N;
-      const int ko = (obatch + b) % per_vec;
-      cp_async<sizeof(cplx<T>)>(dst + (b * N + r / N) * NP + r % N, ur + (long)ko * N * plane + iz * plane + r);
+    for (int b = 0; b < nbb; ++b) {
+      const cplx<T>* src = ur + (long)((obatch + b) % per_vec) * N * plane + iz * plane;
+      cplx<T>* dst = Us + (stage * BO + b) * N * NP;
+      for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
+        const int row = e / N, col = e - row * N;
+        cp_async<sizeof(cplx<T>)>(dst + row * NP + col, src + e);
+      }
     }
   };
   if (kUseU && o_begin < o_end) {
@@ -258,7 +261,7 @@ __global__ void __launch_bounds__(128, 4) k_xy(XYArgs a, cplx<T>* __restrict__ c
 // Response potential of one density (Eqs. 12-13): n'(r) from the group partials, 3D FFT,
 // Hartree 4 pi/|Q+G|^2, inverse FFT, plus f_xc(n0) n'.  Three launches over the grid.
 template <typename T, int N>
-__global__ void __launch_bounds__(64) k_hxc_fwd(const cplx<T>* __restrict__ nprt, int ngroups, T scale,
+__global__ void __launch_bounds__(256) k_hxc_fwd(const cplx<T>* __restrict__ nprt, int ngroups, T scale,
                                                 cplx<T>* __restrict__ nr, cplx<T>* __restrict__ ng) {
   __shared__ cplx<T> P[N][N + 1];
   const int iz = blockIdx.x;
@@ -601,6 +604,8 @@ __global__ void __launch_bounds__(256) k_zfwd_proj(SphereDev s, int nbnd, const 
   __shared__ T epsk[32];
   const long base = ((long)vec * nks + k) * nbnd * npw_pad;
   const int np = s.npw[k];
+  const cplx<T>* bk = bkq + (long)k * nproj * npw_pad;
+  const cplx<T>* uk = ukq + (long)k * nbnd * npw_pad;
   if (threadIdx.x < nbnd) epsk[threadIdx.x] = (T)eps[k * nbnd + threadIdx.x];
   __syncthreads();
   for (int i = threadIdx.x; i < nbnd * npw_pad; i += blockDim.x) {
@@ -630,7 +635,6 @@ __global__ void __launch_bounds__(256) k_zfwd_proj(SphereDev s, int nbnd, const 
   }
   __syncthreads();
   if (nproj > 0) {
-    const cplx<T>* bk = bkq + (long)k * nproj * npw_pad;
     small_dots<T>(bk, npw_pad, xs, npw_pad, np, nproj, nbnd, dij, cf, red);   // D_p <beta_p|x_v>
     cplx<T>* ct = reinterpret_cast<cplx<T>*>(red);    // the coefficients in T (red is free now)
     for (int i = threadIdx.x; i < nproj * nbnd; i += blockDim.x) ct[i] = mk((T)cf[i].x, (T)cf[i].y);
@@ -643,7 +647,6 @@ __global__ void __launch_bounds__(256) k_zfwd_proj(SphereDev s, int nbnd, const 
     }
     __syncthreads();
   }
-  const cplx<T>* uk = ukq + (long)k * nbnd * npw_pad;
   small_dots<T>(uk, npw_pad, ts, npw_pad, np, nbnd, nbnd, nullptr, cf, red);
   subtract_projection<T>(ts, uk, cf, nbnd, npw_pad);
   for (int i = threadIdx.x; i < nbnd * npw_pad; i += blockDim.x) xout[base + i] = ts[i];
