@@ -219,7 +219,7 @@ def run_reference(args):
     if rank != 0:
         return
     b = _bundle()
-    nk = 4
+    nk = 8
     t0 = time.perf_counter()
     _oracle_sample(b, nk, max(1, args.warmup))
     per_step = _oracle_sample(b, nk, args.steps)

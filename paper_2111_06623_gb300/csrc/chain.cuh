@@ -3,6 +3,7 @@
 // orbitals and FFTs with FP64 Lanczos scalars).
 #pragma once
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -319,6 +320,8 @@ class Chain : public ChainBase {
     if ((rc = launch_zinv(dk_, uk_, 1)) || (rc = launch_xy(dk_, nks_ * nbnd_, 0, -1, 2, err))) return rc;
     LL_CK(cudaGetLastError());
 
+    if ((rc = tune_planes(err))) return rc;
+
     // start of the recursion
     if (flavour_ == LL_FLAVOUR_PH) {
       LL_CK(cudaMemcpyAsync(R(), y_, vq * sizeof(cplx<T>), cudaMemcpyDeviceToDevice, st_));
@@ -550,6 +553,42 @@ class Chain : public ChainBase {
     return LL_OK;
   }
 
+  // Autotuner of the orbital-plane staging depth of the two passes that read u(r): both
+  // variants give bitwise-identical results; each is timed once on this system (after a
+  // warm-up launch) and the faster kept.  LL_PLANE_STAGES=1|2 in the environment fixes it.
+  int tune_planes(std::string& err) {
+    const char* env = getenv("LL_PLANE_STAGES");
+    if (env && (env[0] == '1' || env[0] == '2') && env[1] == 0) {
+      nst_dens_ = nst_pass2_ = env[0] - '0';
+      return LL_OK;
+    }
+    if (approx_ == LL_APPROX_IPA) return LL_OK;
+    int rc;
+    cudaEvent_t e0, e1;
+    LL_CK(cudaEventCreate(&e0));
+    LL_CK(cudaEventCreate(&e1));
+    float best[2][2] = {{0, 0}, {0, 0}};
+    if ((rc = launch_zinv(dq_, y_, 1))) { err = "zinv launch"; return rc; }
+    for (int mode = 0; mode < 2; ++mode) {
+      for (int nst = 1; nst <= 2; ++nst) {
+        if (mode == 0) nst_dens_ = nst; else nst_pass2_ = nst;
+        for (int rep = 0; rep < 2; ++rep) {
+          LL_CK(cudaEventRecord(e0, st_));
+          if ((rc = launch_xy(dq_, nks_ * nbnd_, 0, 0, mode, err))) return rc;
+          LL_CK(cudaEventRecord(e1, st_));
+          if (mode == 0 && nst == 2 && rep == 1 && (rc = launch_hxc(err))) return rc;   // v' for pass 2
+        }
+        LL_CK(cudaEventSynchronize(e1));
+        LL_CK(cudaEventElapsedTime(&best[mode][nst - 1], e0, e1));
+      }
+      const int pick = best[mode][0] < best[mode][1] ? 1 : 2;
+      if (mode == 0) nst_dens_ = pick; else nst_pass2_ = pick;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return LL_OK;
+  }
+
   // reduction scratch of the per-k dot routines: max(16, 2*ni*nj) doubles per warp
   size_t red_bytes(int threads) const {
     const int pairs = std::max(std::max(nproj_, nbnd_) * nbnd_, 8);
@@ -625,8 +664,8 @@ class Chain : public ChainBase {
     int g = std::max(1, (target + N_ - 1) / N_);
     return std::min(g, norb);
   }
-  template <int N, int MODE>
-  int xy_nm(const SphereDev& s, int norb, int o_off, int dens_vec, std::string& err) {
+  template <int N, int MODE, int NST>
+  int xy_nms(const SphereDev& s, int norb, int o_off, int dens_vec, std::string& err) {
     constexpr int B = BO<N, MODE>::v;
     const int ng = std::min(ngroups_, norb);
     XYArgs a;
@@ -640,17 +679,23 @@ class Chain : public ChainBase {
     const int NP = N + 1;
     size_t smem = (size_t)B * cb_ncol_ + (size_t)B * s.nrow_max * NP;
     if (MODE == XY_PASS2) smem += (size_t)N * NP;
-    if (MODE == XY_PASS1_DENS || MODE == XY_PASS2) smem += 2 * (size_t)B * N * NP;
+    if (MODE == XY_PASS1_DENS || MODE == XY_PASS2) smem += (size_t)NST * B * N * NP;
     if (MODE == XY_PASS1_DENS) smem += (size_t)N * NP;
     smem *= sizeof(cplx<T>);
     if (MODE == XY_PASS1 || MODE == XY_PASS1_DENS) smem += (size_t)N * NP * sizeof(T);
     int rc;
-    if ((rc = set_smem(k_xy<T, N, B, MODE>, smem, err))) return rc;
-    k_xy<T, N, B, MODE><<<dim3(N, ng), 128, smem, st_>>>(a, cbuf_, vloc_, vpr_, ur_, nprt_, ur_);
+    if ((rc = set_smem(k_xy<T, N, B, MODE, NST>, smem, err))) return rc;
+    k_xy<T, N, B, MODE, NST><<<dim3(N, ng), 128, smem, st_>>>(a, cbuf_, vloc_, vpr_, ur_, nprt_, ur_);
     if (MODE == XY_PASS1_DENS) last_ng_ = ng;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) { err = std::string("k_xy: ") + cudaGetErrorString(e); return LL_ECUDA; }
     return LL_OK;
+  }
+  template <int N, int MODE>
+  int xy_nm(const SphereDev& s, int norb, int o_off, int dens_vec, std::string& err) {
+    const int nst = (MODE == XY_PASS1_DENS) ? nst_dens_ : (MODE == XY_PASS2 ? nst_pass2_ : 2);
+    return nst == 1 ? xy_nms<N, MODE, 1>(s, norb, o_off, dens_vec, err)
+                    : xy_nms<N, MODE, 2>(s, norb, o_off, dens_vec, err);
   }
   // mode 0: operator pass 1 (with the density when dens_vec >= 0); 1: pass 2; 2: store x(r)
   template <int N>
@@ -794,6 +839,7 @@ class Chain : public ChainBase {
   int cb_ncol_ = 0, steps_ = 0, queued_ = 0, spec_cap_ = 0, last_ng_ = 1;
   bool stopped_ = false;
   Profiler prof_;
+  int nst_dens_ = 2, nst_pass2_ = 2;   // orbital-plane staging of the two passes that read u(r)
   std::vector<std::pair<const void*, size_t>> smem_set_;
   double omega_ = 0, q_[3] = {0, 0, 0}, tol_ = 0;
   HostSphere hk_, hq_;

@@ -79,8 +79,10 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 //                  columns (linearity: one axis-3 transform serves both passes);
 //   XY_STORE       inverse 2D FFT only, x(r) stored to grid_out (orbital grids at set-up).
 // The orbital-grid planes (contiguous N^2 in HBM) are staged into shared memory with
-// cp.async, double-buffered: the next batch's planes stream in while the current batch is
-// transformed, and every global load is coalesced.
+// coalesced cp.async copies, either double-buffered (NST = 2: the next batch's planes stream
+// in while the current batch is transformed) or single-buffered (NST = 1: the next batch's
+// copies are issued once the current planes are consumed and overlap the axis-2 passes; less
+// shared memory, more resident blocks).  Both give bitwise-identical results.
 enum XYMode { XY_PASS1 = 0, XY_PASS1_DENS = 1, XY_PASS2 = 2, XY_STORE = 3 };
 
 struct XYArgs {
@@ -92,7 +94,7 @@ struct XYArgs {
   int dens_vec;                // vector whose orbitals feed the density (XY_PASS1_DENS)
 };
 
-template <typename T, int N, int BO, int MODE>
+template <typename T, int N, int BO, int MODE, int NST>
 __global__ void __launch_bounds__(128, 4) k_xy(XYArgs a, cplx<T>* __restrict__ cbuf, const T* __restrict__ vloc,
                                                const cplx<T>* __restrict__ vpr, const cplx<T>* __restrict__ ur,
                                                cplx<T>* __restrict__ nprt, cplx<T>* __restrict__ grid_out) {
@@ -104,8 +106,8 @@ __global__ void __launch_bounds__(128, 4) k_xy(XYArgs a, cplx<T>* __restrict__ c
   cplx<T>* Cs = reinterpret_cast<cplx<T>*>(smem_raw);                 // [BO][cb_ncol]
   cplx<T>* Ys = Cs + BO * a.cb_ncol;                                    // [BO][nrow_max][NP]
   cplx<T>* Pl = Ys + BO * s.nrow_max * NP;                              // [N][NP]  v' (pass 2)
-  cplx<T>* Us = Pl + (MODE == XY_PASS2 ? N * NP : 0);                   // [2][BO][N][NP] u planes
-  cplx<T>* Dacc = Us + (kUseU ? 2 * BO * N * NP : 0);                   // [N][NP] density
+  cplx<T>* Us = Pl + (MODE == XY_PASS2 ? N * NP : 0);                   // [NST][BO][N][NP] u planes
+  cplx<T>* Dacc = Us + (kUseU ? NST * BO * N * NP : 0);                 // [N][NP] density
   T* Pv = reinterpret_cast<T*>(Dacc + (MODE == XY_PASS1_DENS ? N * NP : 0));  // [N][NP] V (real)
   const long plane = (long)N * N;
   const int per_vec = s.nks * a.nbnd;
@@ -136,10 +138,10 @@ __global__ void __launch_bounds__(128, 4) k_xy(XYArgs a, cplx<T>* __restrict__ c
     cp_async_commit();
   }
   int stage = 0;
-  for (int ob = o_begin; ob < o_end; ob += BO, stage ^= 1) {
+  for (int ob = o_begin; ob < o_end; ob += BO, stage = (NST == 2) ? (stage ^ 1) : 0) {
     const int nb = min(BO, o_end - ob);
     __syncthreads();
-    if (kUseU) {
+    if (kUseU && NST == 2) {
       if (ob + BO < o_end) stage_u(ob + BO, stage ^ 1);
       cp_async_commit();
     }
@@ -169,7 +171,10 @@ __global__ void __launch_bounds__(128, 4) k_xy(XYArgs a, cplx<T>* __restrict__ c
         for (int p = 0; p < N; ++p) ys[p] = l[p];
       }
     }
-    if (kUseU) cp_async_wait_prev();
+    if (kUseU) {
+      if (NST == 2) cp_async_wait_prev();
+      else cp_async_wait_all();
+    }
     __syncthreads();
     cplx<T>* Ub = Us + stage * (BO * N * NP);
     // axis 1: one line per (orbital, j2)
@@ -222,6 +227,11 @@ __global__ void __launch_bounds__(128, 4) k_xy(XYArgs a, cplx<T>* __restrict__ c
         for (int b = 0; b < nb; ++b) acc = acc + Ub[b * N * NP + q];
         Dacc[q] = acc;
       }
+    }
+    if (kUseU && NST == 1) {  // the planes are consumed: start the next batch's copies
+      if (MODE == XY_PASS1_DENS) __syncthreads();
+      if (ob + BO < o_end) stage_u(ob + BO, 0);
+      cp_async_commit();
     }
     // forward FFT along axis 2 of every row, keep the row's columns
     for (int i = threadIdx.x; i < nb * s.nrow_max; i += blockDim.x) {

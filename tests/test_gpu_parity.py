@@ -208,3 +208,16 @@ def test_kb_workload_first_coefficients(lib, kb):
     assert _coef_rel(got64, ref, 6) < 1e-10
     got32 = chain_from_bundle(kb, precision="fp32", max_steps=6).lanczos(6)
     assert _coef_rel(got32, ref, 6) < 1e-4
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_plane_staging_depths_bit_identical(lib, small, precision, monkeypatch):
+    """The autotuner chooses between single- and double-buffered orbital-plane staging; both
+    must give the same coefficients bit for bit."""
+    out = []
+    for depth in ("1", "2"):
+        monkeypatch.setenv("LL_PLANE_STAGES", depth)
+        out.append(chain_from_bundle(small, precision=precision, max_steps=30).lanczos(30))
+    monkeypatch.delenv("LL_PLANE_STAGES")
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
