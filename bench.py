@@ -40,6 +40,21 @@ SPEC_WINDOW = 100        # coefficients of the reproducible part of the recursio
 FP32_PEAK_PER_SM_CLK = 128 * 2   # FP32 lanes per SM x 2 flops per FMA
 
 
+def max_over_ranks(ms: float, world: int) -> float:
+    """The slowest rank's timed region (ms); a host collective on the default group."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(steps_per_rank: int, world: int, ms_max: float) -> float:
+    """Steps/s of the whole job: every rank's steps over the slowest rank's time."""
+    return world * steps_per_rank / (ms_max / 1e3)
+
+
 def _bundle():
     import workloads as w
     return w.get_bundle(w.config_kb())
@@ -312,13 +327,9 @@ def main():
     e2e = {"value": K / t_e2e, "unit": "steps/s", "h2d_bytes_per_step": _bundle_bytes(b) / K,
            "d2h_bytes_per_step": (sum(c.nbytes for c in ce) + chi.nbytes + ei.nbytes + eps.nbytes) / K}
 
-    # max over ranks of the timed region
-    tmax = ms32
-    if world > 1:
-        t = torch.tensor([ms32], dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tmax = float(t.item())
-    value = world * K / (tmax / 1e3)
+    # max over ranks of the timed region; the whole job's steps over that time
+    tmax = max_over_ranks(ms32, world)
+    value = whole_job_rate(K, world, tmax)
 
     ms_cls, launches, total = prof
     dom = max(ms_cls, key=ms_cls.get)

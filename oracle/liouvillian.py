@@ -76,10 +76,15 @@ class System:
     def inner(self, a, b) -> complex:
         return sum(np.vdot(ak, bk) for ak, bk in zip(a, b)) / self.nks
 
-    def project_c(self, x):
+    # Every per-k method takes the k index of each entry of its batch in `ks` (default: all
+    # k-points in order), so that a rank holding a block of k-points can apply it to its block.
+    def _ks(self, x, ks):
+        return range(len(x)) if ks is None else ks
+
+    def project_c(self, x, ks=None):
         """P_c^{k+Q} x = x - U (U^H x) with U the occupied states at k+Q (Eq. 16)."""
         out = []
-        for k, xk in enumerate(x):
+        for k, xk in zip(self._ks(x, ks), x):
             u = self.ukq[k]
             out.append(xk - (u.T @ (u.conj() @ xk.T)).T)
         return out
@@ -96,11 +101,11 @@ class System:
         return self.project_c(y)
 
     # ----- operators -----------------------------------------------------------------
-    def apply_h_minus_eps(self, x):
+    def apply_h_minus_eps(self, x, ks=None):
         """(H_{k+Q} - eps_{vk}) x_{vk}, unprojected: kinetic, V_KS(r), KB projectors."""
         n = self.n
         out = []
-        for k, xk in enumerate(x):
+        for k, xk in zip(self._ks(x, ks), x):
             mil = self.mkq[k]
             psi = basis.to_grid(xk, mil, n)
             t = basis.to_sphere(self.vloc[None] * psi, mil, n)
@@ -112,14 +117,15 @@ class System:
             out.append(t)
         return out
 
-    def apply_d(self, x):
-        return self.project_c(self.apply_h_minus_eps(x))
+    def apply_d(self, x, ks=None):
+        return self.project_c(self.apply_h_minus_eps(x, ks), ks)
 
-    def response_density(self, x):
-        """n'(r) = 4 (1/N_k) sum_{vk} u*_{vk}(r) x_{vk}(r), u = psi/sqrt(Omega)."""
+    def response_density(self, x, ks=None):
+        """n'(r) = 4 (1/N_k) sum_{vk} u*_{vk}(r) x_{vk}(r), u = psi/sqrt(Omega); with `ks`,
+        the part of the sum over those k-points."""
         n = self.n
         nr = np.zeros((n, n, n), dtype=np.complex128)
-        for k, xk in enumerate(x):
+        for k, xk in zip(self._ks(x, ks), x):
             psi = basis.to_grid(xk, self.mkq[k], n)
             nr += np.sum(self.ur[k].conj() * psi, axis=0)
         return 4.0 * nr / (self.omega * self.nks)
@@ -132,11 +138,13 @@ class System:
     def apply_k(self, x):
         if self.approx == "ipa":
             return self.zeros()
-        v = self.hxc_potential(self.response_density(x))
-        out = []
-        for k in range(self.nks):
-            out.append(basis.to_sphere(v[None] * self.ur[k], self.mkq[k], self.n))
-        return self.project_c(out)
+        return self.apply_v(self.hxc_potential(self.response_density(x)))
+
+    def apply_v(self, v, ks=None):
+        """K's last step: P_c^{k+Q} v'(r) u_{vk}(r) for the k-points ks (default all)."""
+        ks = range(self.nks) if ks is None else ks
+        out = [basis.to_sphere(v[None] * self.ur[k], self.mkq[k], self.n) for k in ks]
+        return self.project_c(out, ks)
 
     def apply_op(self, x, upper: bool):
         """The operator the recursions apply to one half of a batch: D + K on the upper
