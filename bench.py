@@ -129,10 +129,42 @@ def _xy_flops_per_apply(b, with_k: bool) -> float:
     line = 5.0 * n * np.log2(n)
     tot = 0.0
     for m in b.miller_kq:
-        rows = len(np.unique(m[:, 0]))
+        rows = len(np.unique(m[:, 1]))       # sphere rows: columns of equal m2
         per_plane = (2 * rows + 2 * n) * line + (2 + (8 if with_k else 0)) * n * n
         tot += b.spec.nbnd * n * per_plane
     return tot
+
+
+def source_digest() -> str:
+    """sha256 of the CUDA sources and the C header: names the code a profile was taken on."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2111_06623_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)) + ["../../include/ll.h"]:
+        if f.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(f.encode() + b"\0" + fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the dominant kernel class from the committed ncu summary
+    (profiles/roofline_traffic.txt), or None when the sources changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "roofline_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    with open(path) as fh:
+        for line in fh:
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+    if kv.get("source_digest") != source_digest():
+        return None
+    try:
+        return float(kv["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 def _time_chain(b, precision, steps, warmup, stream, profile=False):
@@ -342,7 +374,8 @@ def main():
     if dom == "xy1":
         ach = flops / (ms_cls[dom] / n_dom / 1e3) / 1e12
         roofline = {"bound": "alu", "kernel": "k_xy (pass 1: per-plane 2D FFTs, V x, density)", "achieved": ach,
-                    "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                    "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": profiled_traffic(),
+                    "traffic_unit": "bytes per launch (mean of the D+K and D launches)",
                     "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flops x max SM clock (derived)"}
     else:
         roofline = {"bound": "alu", "kernel": dom, "achieved": None, "peak": peak, "unit": "TFLOP/s",

@@ -11,7 +11,7 @@
 #include <vector>
 
 #include "ll.h"
-#include "kernels.cuh"
+#include "split.cuh"
 
 namespace ll {
 
@@ -126,17 +126,29 @@ static inline bool build_sphere(int nks, const int* npw, const int* mil, int n, 
       starts[k].push_back(i);
       i = j;
     }
-    // rows: runs of columns with equal m1, consecutive m2; the m1 values consecutive
-    int c = 0;
+    // columns ordered by (m2, m1); rows: runs of columns with equal m2 and consecutive m1,
+    // the m2 values consecutive
     const int nc = (int)cols[k].size();
+    std::vector<int> perm(nc);
+    for (int c = 0; c < nc; ++c) perm[c] = c;
+    std::sort(perm.begin(), perm.end(), [&](int x, int y) {
+      const int4 a = cols[k][x], b = cols[k][y];
+      return a.y < b.y || (a.y == b.y && a.x < b.x);
+    });
+    std::vector<int4> pc(nc);
+    std::vector<int> ps(nc);
+    for (int c = 0; c < nc; ++c) { pc[c] = cols[k][perm[c]]; ps[c] = starts[k][perm[c]]; }
+    cols[k].swap(pc);
+    starts[k].swap(ps);
+    int c = 0;
     while (c < nc) {
       int d = c;
-      while (d < nc && cols[k][d].x == cols[k][c].x) {
-        if (d > c && cols[k][d].y != cols[k][d - 1].y + 1) { err = "a sphere row is not a contiguous run"; return false; }
+      while (d < nc && cols[k][d].y == cols[k][c].y) {
+        if (d > c && cols[k][d].x != cols[k][d - 1].x + 1) { err = "a sphere row is not a contiguous run"; return false; }
         ++d;
       }
-      if (!rows[k].empty() && cols[k][c].x != rows[k].back().x + 1) { err = "sphere rows are not consecutive"; return false; }
-      rows[k].push_back(make_int4(cols[k][c].x, c, cols[k][c].y, d - c));
+      if (!rows[k].empty() && cols[k][c].y != rows[k].back().x + 1) { err = "sphere rows are not consecutive"; return false; }
+      rows[k].push_back(make_int4(cols[k][c].y, c, cols[k][c].x, d - c));
       c = d;
     }
     h.ncol_max = std::max(h.ncol_max, nc);
@@ -177,7 +189,7 @@ static inline void recip(const double a[3][3], double b[3][3]) {
 // orbital-grid planes are staged (their shared memory is the limit), three rounds otherwise
 // so that the axis-2 passes (a sphere's rows, ~N/3 lines per orbital) also fill the block.
 template <int N, int MODE> struct BO {
-  static constexpr int v = (MODE == XY_PASS1_DENS || MODE == XY_PASS2) ? (128 / N < 1 ? 1 : 128 / N) : 384 / N;
+  static constexpr int v = MODE == XY_PASS1_DENS ? (128 / N < 1 ? 1 : 128 / N) : (MODE == XY_PASS2 ? 256 / N : 384 / N);
 };
 
 template <typename T>
@@ -268,16 +280,35 @@ class Chain : public ChainBase {
     cb_ncol_ = std::max(hk_.ncol_max, hq_.ncol_max);
     const int norb = nvec_ * nks_ * nbnd_;
     ngroups_ = groups_for(norb);
+    // per-k work: fused (one CTA holds a k block) when it fits in shared memory, else split
+    // over chunks of plane waves (LL_SPLIT_PERK=1 in the environment forces the split path)
+    {
+      // dynamic part of k_zfwd_proj, plus its static arrays (projection coefficients, eps)
+      const size_t fused = 2 * (size_t)nbnd_ * pq * sizeof(cplx<T>) +
+                           (size_t)std::max(nproj_, nbnd_) * nbnd_ * sizeof(cplx<double>) + red_bytes(256) +
+                           32 * 32 * sizeof(cplx<T>) + 4096;
+      const char* env = getenv("LL_SPLIT_PERK");
+      split_ = fused > 227 * 1024 || (env && env[0] == '1' && env[1] == 0);
+      nchunk_ = split_ ? (pq + kChunk - 1) / kChunk : 1;
+      if (split_ && flavour_ == LL_FLAVOUR_NH) {
+        err = "the non-Hermitian recursion needs k blocks (2 nbnd npw values) that fit one CTA's shared memory";
+        return LL_EUNSUPPORTED;
+      }
+    }
+    const long nzp = (long)nks_ * nchunk_;
     if ((rc = alloc(&whart_, n3)) || (rc = alloc(&kin_, (long)nks_ * pq)) || (rc = alloc(&uk_, (long)nks_ * nbnd_ * pk)) ||
         (rc = alloc(&ukq_, vq)) || (rc = alloc(&bkq_, (long)bkq.size())) || (rc = alloc(&eps_, (long)nks_ * nbnd_)) ||
         (rc = alloc(&dij_, std::max(1, nproj_))) || (rc = alloc(&vloc_, n3)) || (rc = alloc(&rho_, n3)) ||
         (rc = alloc(&fxc_, n3)) || (rc = alloc(&ur_, (long)nks_ * nbnd_ * n3)) ||
         (rc = alloc(&cbuf_, (long)norb * n * cb_ncol_)) || (rc = alloc(&nprt_, (long)ngroups_ * n3)) ||
         (rc = alloc(&nr_, n3)) || (rc = alloc(&ng_, n3)) || (rc = alloc(&vpr_, n3)) ||
-        (rc = alloc(&y_, vq)) || (rc = alloc(&map_, (long)nks_ * pq)) || (rc = alloc(&part_, 2L * nks_)) ||
+        (rc = alloc(&y_, vq)) || (rc = alloc(&map_, (long)nks_ * pq)) || (rc = alloc(&part_, std::max(2L * nks_, nzp))) ||
         (rc = alloc(&spart_, (long)nks_)) || (rc = alloc(&vecs_, 3L * nvec_ * vq)) ||
         (rc = alloc(&beta_, cap_ + 2)) || (rc = alloc(&gamma_, cap_ + 2)) || (rc = alloc(&z_, cap_ + 1)) ||
-        (rc = alloc(&zpart_, (long)(cap_ + 1) * nks_)) || (rc = alloc(&err_, 2)))
+        (rc = alloc(&zpart_, (long)(cap_ + 1) * nzp)) || (rc = alloc(&err_, 2)))
+      return rc;
+    if (split_ && ((rc = alloc(&sp_s_, nzp * nbnd_ * nbnd_)) || (rc = alloc(&sp_c_, nzp * std::max(1, nproj_ * nbnd_))) ||
+                   (rc = alloc(&ub_, (long)nks_ * nbnd_ * std::max(1, nproj_)))))
       return rc;
     (void)err;
     LL_CK(cudaMemcpyAsync(whart_, wh.data(), n3 * sizeof(T), cudaMemcpyHostToDevice, st_));
@@ -291,9 +322,16 @@ class Chain : public ChainBase {
     LL_CK(cudaMemcpyAsync(rho_, rh.data(), n3 * sizeof(double), cudaMemcpyHostToDevice, st_));
     LL_CK(cudaMemsetAsync(err_, 0, 2 * sizeof(int), st_));
     LL_CK(cudaMemsetAsync(vecs_, 0, 3L * nvec_ * vq * sizeof(cplx<T>), st_));
-    LL_CK(cudaMemsetAsync(zpart_, 0, (long)(cap_ + 1) * nks_ * sizeof(cplx<double>), st_));
+    LL_CK(cudaMemsetAsync(zpart_, 0, (long)(cap_ + 1) * nzp * sizeof(cplx<double>), st_));
     k_fxc<T><<<256, 256, 0, st_>>>(n3, rho_, fxc_, approx_ == LL_APPROX_TDDFT ? 1 : 0);
     LL_CK(cudaGetLastError());
+    if (split_ && nproj_ > 0) {  // U^H B per k (the KB part of P_c on the split path)
+      const size_t sm = (size_t)(nbnd_ + nproj_) * kTileP * sizeof(cplx<T>);
+      if ((rc = set_smem(k_sp_ub<T>, sm, err))) return rc;
+      k_sp_ub<T><<<dim3(nks_, nchunk_), 256, sm, st_>>>(nbnd_, pq, dq_.npw, nchunk_, nproj_, ukq_, bkq_, sp_c_);
+      k_sp_reduce<<<nks_, 256, 0, st_>>>(nchunk_, nbnd_ * nproj_, sp_c_, ub_);
+      LL_CK(cudaGetLastError());
+    }
 
     // index map sphere(k+Q) -> sphere(k) (on the device, from the Miller lists)
     {
@@ -320,14 +358,13 @@ class Chain : public ChainBase {
     if ((rc = launch_zinv(dk_, uk_, 1)) || (rc = launch_xy(dk_, nks_ * nbnd_, 0, -1, 2, err))) return rc;
     LL_CK(cudaGetLastError());
 
-    if ((rc = tune_planes(err))) return rc;
 
     // start of the recursion
     if (flavour_ == LL_FLAVOUR_PH) {
       LL_CK(cudaMemcpyAsync(R(), y_, vq * sizeof(cplx<T>), cudaMemcpyDeviceToDevice, st_));
       if ((rc = op(1, R(), X(), -1, err))) return rc;               // X_1 = D y
-      std::vector<double> hp(nks_);
-      LL_CK(cudaMemcpyAsync(hp.data(), part_, nks_ * sizeof(double), cudaMemcpyDeviceToHost, st_));
+      std::vector<double> hp(nzp);
+      LL_CK(cudaMemcpyAsync(hp.data(), part_, nzp * sizeof(double), cudaMemcpyDeviceToHost, st_));
       LL_CK(cudaStreamSynchronize(st_));
       double s = 0;
       for (double v : hp) s += v;
@@ -383,7 +420,7 @@ class Chain : public ChainBase {
         // update of the Lanczos vectors fused with the axis-3 inverse FFT of r_{j+1}
         const int u0 = prof_.mark(st_);
         if ((rc = launch_zinv_ph(j, err))) return rc;
-        prof_.count(LL_PROF_ZINV);
+        prof_.count(LL_PROF_ZINV, split_ ? 2 : 1);
         prof_.span(LL_PROF_ZINV, u0, prof_.mark(st_));
         // r_{j+1} is upper when j is odd; the upper half gets D + K
         const int dens = (j % 2 == 1 && approx_ != LL_APPROX_IPA) ? 0 : -1;
@@ -405,7 +442,7 @@ class Chain : public ChainBase {
       LL_CK(cudaGetLastError());
     }
     if (n > 0) {
-      k_reduce_z<<<(n + 127) / 128, 128, 0, st_>>>(zpart_, nks_, queued_, queued_ + n, z_);
+      k_reduce_z<<<(n + 127) / 128, 128, 0, st_>>>(zpart_, nks_ * nchunk_, nks_, queued_, queued_ + n, z_);
       LL_CK(cudaGetLastError());
       prof_.count(LL_PROF_UPDATE);
     }
@@ -548,44 +585,8 @@ class Chain : public ChainBase {
       prof_.span(LL_PROF_XY2, e3, e2);
     }
     if ((rc = launch_zfwd_proj(nvec, in, out, err))) return rc;
-    prof_.count(LL_PROF_ZFWD);
+    prof_.count(LL_PROF_ZFWD, split_ ? 3 : 1);
     prof_.span(LL_PROF_ZFWD, e2, prof_.mark(st_));
-    return LL_OK;
-  }
-
-  // Autotuner of the orbital-plane staging depth of the two passes that read u(r): both
-  // variants give bitwise-identical results; each is timed once on this system (after a
-  // warm-up launch) and the faster kept.  LL_PLANE_STAGES=1|2 in the environment fixes it.
-  int tune_planes(std::string& err) {
-    const char* env = getenv("LL_PLANE_STAGES");
-    if (env && (env[0] == '1' || env[0] == '2') && env[1] == 0) {
-      nst_dens_ = nst_pass2_ = env[0] - '0';
-      return LL_OK;
-    }
-    if (approx_ == LL_APPROX_IPA) return LL_OK;
-    int rc;
-    cudaEvent_t e0, e1;
-    LL_CK(cudaEventCreate(&e0));
-    LL_CK(cudaEventCreate(&e1));
-    float best[2][2] = {{0, 0}, {0, 0}};
-    if ((rc = launch_zinv(dq_, y_, 1))) { err = "zinv launch"; return rc; }
-    for (int mode = 0; mode < 2; ++mode) {
-      for (int nst = 1; nst <= 2; ++nst) {
-        if (mode == 0) nst_dens_ = nst; else nst_pass2_ = nst;
-        for (int rep = 0; rep < 2; ++rep) {
-          LL_CK(cudaEventRecord(e0, st_));
-          if ((rc = launch_xy(dq_, nks_ * nbnd_, 0, 0, mode, err))) return rc;
-          LL_CK(cudaEventRecord(e1, st_));
-          if (mode == 0 && nst == 2 && rep == 1 && (rc = launch_hxc(err))) return rc;   // v' for pass 2
-        }
-        LL_CK(cudaEventSynchronize(e1));
-        LL_CK(cudaEventElapsedTime(&best[mode][nst - 1], e0, e1));
-      }
-      const int pick = best[mode][0] < best[mode][1] ? 1 : 2;
-      if (mode == 0) nst_dens_ = pick; else nst_pass2_ = pick;
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     return LL_OK;
   }
 
@@ -596,6 +597,7 @@ class Chain : public ChainBase {
   }
   template <int N>
   int zfwd_proj_n(int nvec, const cplx<T>* in, cplx<T>* out, std::string& err) {
+    if (split_) return zfwd_split_n<N>(nvec, in, out, err);
     const size_t smem = 2 * (size_t)nbnd_ * hq_.npw_pad * sizeof(cplx<T>) +
                         (size_t)std::max(nproj_, nbnd_) * nbnd_ * sizeof(cplx<double>) + red_bytes(256);
     int rc;
@@ -617,8 +619,42 @@ class Chain : public ChainBase {
     }
     return LL_EUNSUPPORTED;
   }
+  // split per-k path (split.cuh): several CTAs per k-point, chunk partials reduced in order
+  template <int N>
+  int zfwd_split_n(int nvec, const cplx<T>* in, cplx<T>* out, std::string& err) {
+    const int pq = hq_.npw_pad;
+    const int lines = (nbnd_ * hq_.ncol_max + kLines - 1) / kLines;
+    k_sp_zfwd<T, N><<<dim3(nks_, nvec, lines), kLines, 0, st_>>>(dq_, nbnd_, cbuf_, cb_ncol_, in, kin_, eps_, out);
+    const size_t sm_d = (size_t)(std::max(nproj_, nbnd_) + nbnd_) * kTileP * sizeof(cplx<T>);
+    const size_t sm_a = (size_t)nproj_ * nbnd_ * (sizeof(cplx<double>) + sizeof(cplx<T>)) +
+                        (size_t)nbnd_ * nbnd_ * sizeof(cplx<T>);
+    int rc;
+    if ((rc = set_smem(k_sp_dots<T>, sm_d, err)) || (rc = set_smem(k_sp_apply<T>, sm_a, err))) return rc;
+    k_sp_dots<T><<<dim3(nks_, nvec, nchunk_), 256, sm_d, st_>>>(nks_, nbnd_, pq, dq_.npw, nchunk_, nproj_, in, out,
+                                                                ukq_, bkq_, sp_c_, sp_s_);
+    k_sp_apply<T><<<dim3(nks_, nvec, nchunk_), 256, sm_a, st_>>>(nks_, nbnd_, pq, dq_.npw, nchunk_, nproj_, in, out,
+                                                                 ukq_, bkq_, dij_, ub_, sp_c_, sp_s_, part_);
+    LL_CK(cudaGetLastError());
+    return LL_OK;
+  }
+  template <int N>
+  int zinv_split_n(int j, std::string& err) {
+    const int pq = hq_.npw_pad;
+    const size_t sm = (size_t)(2 * nbnd_) * kTileP * sizeof(cplx<T>);
+    int rc;
+    if ((rc = set_smem(k_sp_start<T>, sm, err))) return rc;
+    Coef co{beta_, gamma_, zpart_, err_};
+    k_sp_start<T><<<dim3(nks_, nchunk_), 256, sm, st_>>>(j, (j % 2 == 0) ? 1 : 0, nks_, nbnd_, pq, dq_.npw, nchunk_,
+                                                         part_, R(), X(), Vp(), y_, ukq_, co, tol_, sp_s_);
+    const int lines = (nbnd_ * hq_.ncol_max + kLines - 1) / kLines;
+    k_sp_proj_cols<T, N><<<dim3(nks_, lines), kLines, 0, st_>>>(dq_, nbnd_, nchunk_, sp_s_, R(), ukq_, cbuf_,
+                                                                cb_ncol_);
+    LL_CK(cudaGetLastError());
+    return LL_OK;
+  }
   template <int N>
   int zinv_ph_n(int j, std::string& err) {
+    if (split_) return zinv_split_n<N>(j, err);
     const size_t smem = (size_t)nbnd_ * hq_.npw_pad * sizeof(cplx<T>) + (size_t)nbnd_ * nbnd_ * sizeof(cplx<double>) +
                         red_bytes(256);
     int rc;
@@ -664,8 +700,8 @@ class Chain : public ChainBase {
     int g = std::max(1, (target + N_ - 1) / N_);
     return std::min(g, norb);
   }
-  template <int N, int MODE, int NST>
-  int xy_nms(const SphereDev& s, int norb, int o_off, int dens_vec, std::string& err) {
+  template <int N, int MODE>
+  int xy_nm(const SphereDev& s, int norb, int o_off, int dens_vec, std::string& err) {
     constexpr int B = BO<N, MODE>::v;
     const int ng = std::min(ngroups_, norb);
     XYArgs a;
@@ -676,26 +712,24 @@ class Chain : public ChainBase {
     a.per_group = (norb + ng - 1) / ng;
     a.o_off = o_off;
     a.dens_vec = dens_vec;
+    a.f_ncol = FastDiv((unsigned)cb_ncol_);
+    a.f_nrow = FastDiv((unsigned)s.nrow_max);
+    a.f_nbnd = FastDiv((unsigned)nbnd_);
+    a.f_nks = FastDiv((unsigned)s.nks);
+    a.f_pervec = FastDiv((unsigned)(s.nks * nbnd_));
     const int NP = N + 1;
     size_t smem = (size_t)B * cb_ncol_ + (size_t)B * s.nrow_max * NP;
-    if (MODE == XY_PASS2) smem += (size_t)N * NP;
-    if (MODE == XY_PASS1_DENS || MODE == XY_PASS2) smem += (size_t)NST * B * N * NP;
-    if (MODE == XY_PASS1_DENS) smem += (size_t)N * NP;
+    if (MODE == XY_PASS2) smem += (size_t)N * N;
+    if (MODE == XY_PASS1_DENS) smem += (size_t)(B + 1) * N * N + 1;   // + alignment of the u planes
     smem *= sizeof(cplx<T>);
-    if (MODE == XY_PASS1 || MODE == XY_PASS1_DENS) smem += (size_t)N * NP * sizeof(T);
+    if (MODE == XY_PASS1 || MODE == XY_PASS1_DENS) smem += (size_t)N * N * sizeof(T);
     int rc;
-    if ((rc = set_smem(k_xy<T, N, B, MODE, NST>, smem, err))) return rc;
-    k_xy<T, N, B, MODE, NST><<<dim3(N, ng), 128, smem, st_>>>(a, cbuf_, vloc_, vpr_, ur_, nprt_, ur_);
+    if ((rc = set_smem(k_xy<T, N, B, MODE>, smem, err))) return rc;
+    k_xy<T, N, B, MODE><<<dim3(N, ng), 128, smem, st_>>>(a, cbuf_, vloc_, vpr_, ur_, nprt_, ur_);
     if (MODE == XY_PASS1_DENS) last_ng_ = ng;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) { err = std::string("k_xy: ") + cudaGetErrorString(e); return LL_ECUDA; }
     return LL_OK;
-  }
-  template <int N, int MODE>
-  int xy_nm(const SphereDev& s, int norb, int o_off, int dens_vec, std::string& err) {
-    const int nst = (MODE == XY_PASS1_DENS) ? nst_dens_ : (MODE == XY_PASS2 ? nst_pass2_ : 2);
-    return nst == 1 ? xy_nms<N, MODE, 1>(s, norb, o_off, dens_vec, err)
-                    : xy_nms<N, MODE, 2>(s, norb, o_off, dens_vec, err);
   }
   // mode 0: operator pass 1 (with the density when dens_vec >= 0); 1: pass 2; 2: store x(r)
   template <int N>
@@ -839,7 +873,6 @@ class Chain : public ChainBase {
   int cb_ncol_ = 0, steps_ = 0, queued_ = 0, spec_cap_ = 0, last_ng_ = 1;
   bool stopped_ = false;
   Profiler prof_;
-  int nst_dens_ = 2, nst_pass2_ = 2;   // orbital-plane staging of the two passes that read u(r)
   std::vector<std::pair<const void*, size_t>> smem_set_;
   double omega_ = 0, q_[3] = {0, 0, 0}, tol_ = 0;
   HostSphere hk_, hq_;
@@ -852,6 +885,9 @@ class Chain : public ChainBase {
   cplx<T> *nr_ = nullptr, *ng_ = nullptr, *vpr_ = nullptr, *y_ = nullptr, *vecs_ = nullptr;
   cplx<T>* scratch_ = nullptr;
   cplx<double> *spart_ = nullptr, *gamma_ = nullptr, *z_ = nullptr, *zpart_ = nullptr, *spec_out_ = nullptr;
+  bool split_ = false;      // per-k work split over chunks of plane waves (split.cuh)
+  int nchunk_ = 1;          // plane-wave chunks per k on the split path
+  cplx<double> *sp_s_ = nullptr, *sp_c_ = nullptr, *ub_ = nullptr;   // chunk partials of U^H r, B^H x; U^H B
   double* spec_w_ = nullptr;
   int *map_ = nullptr, *err_ = nullptr;
 };

@@ -33,6 +33,21 @@ template <> struct TwOff<48> { static constexpr int v = 138; };
 constexpr int kTwTotal = 186;
 constexpr int kGridSides[] = {12, 16, 18, 24, 32, 36, 48};
 
+// Division by a divisor fixed at launch, as a multiply-high and a shift (Granlund and
+// Montgomery, "Division by invariant integers using multiplication", PLDI 1994, Sec. 4):
+// with l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1, n / d = (mulhi(m, n) + n) >> l
+// for every 0 <= n < 2^31 (the sum then cannot overflow 32 bits).
+struct FastDiv {
+  unsigned d, m, l;
+  FastDiv() : d(1), m(1), l(0) {}
+  explicit FastDiv(unsigned dv) : d(dv ? dv : 1), m(1), l(0) {  // d = 0 is taken as 1
+    while ((1ull << l) < d) ++l;
+    m = (unsigned)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+  }
+  __device__ __forceinline__ int div(int n) const { return (int)((__umulhi((unsigned)n, m) + (unsigned)n) >> l); }
+  __device__ __forceinline__ int mod(int n) const { return n - div(n) * (int)d; }
+};
+
 // Device status word: the kernels never trap; a detected fault sets a code here and the
 // host turns it into an ll_status after the call.
 enum DevErr : int { DEV_OK = 0, DEV_NOTPD = 1, DEV_BREAKDOWN = 2, DEV_BOUNDS = 3 };

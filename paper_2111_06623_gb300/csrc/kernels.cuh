@@ -20,9 +20,11 @@ struct SphereDev {
   const int* npw;       // [nks]
   const int* ncol;      // [nks]
   const int* nrow;      // [nks]
-  const int4* col;      // [nks][ncol_max]  (m1, m2, m3 of the first point, point count)
+  const int4* col;      // [nks][ncol_max]  (m1, m2, m3 of the first point, point count),
+                        //                  ordered by (m2, m1)
   const int* colstart;  // [nks][ncol_max]  first point of the column in the sphere order
-  const int4* row;      // [nks][nrow_max]  (m1, first column, m2 of the first column, columns)
+  const int4* row;      // [nks][nrow_max]  (m2, first column, m1 of the first column, columns),
+                        //                  consecutive m2, each row's m1 consecutive
 };
 
 // m mod N for m >= -N (a mask when N is a power of two)
@@ -57,32 +59,35 @@ __global__ void __launch_bounds__(128) k_zinv(SphereDev s, const cplx<T>* __rest
 }
 
 // ---------------------------------------------------------------------------------------
-// Asynchronous global -> shared copies (cp.async) of BYTES per thread.
-template <int BYTES>
-__device__ __forceinline__ void cp_async(void* smem_dst, const void* gmem_src) {
+// Asynchronous 16-byte global -> shared copies (cp.async, L2 only), their commit and wait.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(gmem_src), "n"(BYTES));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src));
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-// every committed group but the most recent one has landed
-__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
 
 // ---------------------------------------------------------------------------------------
 // Per-plane pass of one operator application.  grid (N planes, groups), block 128.
-// For every orbital of the group (BO at a time), at plane j3 = blockIdx.x:
+// The sphere's columns are ordered by (m2, m1) and grouped in rows of equal m2 (consecutive
+// m1).  For every orbital of the group (BO at a time), at plane j3 = blockIdx.x:
+//   rows     1D FFT along axis 1 (m1 <-> j1) of every sphere row, between the column buffer
+//            Cs and the row buffer Ys[row][j1];
+//   lines    one thread per (orbital, j1): 1D FFT along axis 2 (m2 <-> j2) of the line
+//            x(j2, j1), j2 = 0..N-1, held in registers.  Consecutive threads take consecutive
+//            j1, so every real-space plane (V, v', u, the density) is read and written with
+//            unit stride across a warp straight from HBM: no staging copies.
+// Modes:
 //   XY_PASS1       inverse 2D FFT of the plane's columns, t(r) = V(r) x(r), forward 2D FFT
 //                  back to the columns (in place);
 //   XY_PASS1_DENS  the same plus the response-density partial sum_o conj(u_o(r)) x_o(r) of the
-//                  orbitals of vector dens_vec, written per (group, plane) to nprt;
+//                  orbitals of vector dens_vec, written per (group, plane) to nprt (orbitals
+//                  summed in a fixed order).  The batch's u planes are copied into the product
+//                  planes Pb with cp.async while the rows are transformed, and each line
+//                  replaces its u values there by conj(u) x;
 //   XY_PASS2       t(r) = v'(r) u(r) from the orbital grid, forward 2D FFT, added into the
 //                  columns (linearity: one axis-3 transform serves both passes);
 //   XY_STORE       inverse 2D FFT only, x(r) stored to grid_out (orbital grids at set-up).
-// The orbital-grid planes (contiguous N^2 in HBM) are staged into shared memory with
-// coalesced cp.async copies, either double-buffered (NST = 2: the next batch's planes stream
-// in while the current batch is transformed) or single-buffered (NST = 1: the next batch's
-// copies are issued once the current planes are consumed and overlap the axis-2 passes; less
-// shared memory, more resident blocks).  Both give bitwise-identical results.
 enum XYMode { XY_PASS1 = 0, XY_PASS1_DENS = 1, XY_PASS2 = 2, XY_STORE = 3 };
 
 struct XYArgs {
@@ -92,70 +97,64 @@ struct XYArgs {
   int per_group;               // orbitals per group
   int o_off;                   // first orbital of this launch (orbital o = o_off + local index)
   int dens_vec;                // vector whose orbitals feed the density (XY_PASS1_DENS)
+  FastDiv f_ncol, f_nrow;      // divisions by cb_ncol and by the sphere table's nrow_max
+  FastDiv f_nbnd, f_nks;       // orbital -> k: (o / nbnd) mod nks
+  FastDiv f_pervec;            // orbital -> vector: o / (nks nbnd)
 };
 
-template <typename T, int N, int BO, int MODE, int NST>
-__global__ void __launch_bounds__(128, 4) k_xy(XYArgs a, cplx<T>* __restrict__ cbuf, const T* __restrict__ vloc,
+template <typename T, int N, int BO, int MODE>
+__global__ void __launch_bounds__(128, MODE == XY_PASS1_DENS ? 3 : 4) k_xy(XYArgs a, cplx<T>* __restrict__ cbuf, const T* __restrict__ vloc,
                                                const cplx<T>* __restrict__ vpr, const cplx<T>* __restrict__ ur,
                                                cplx<T>* __restrict__ nprt, cplx<T>* __restrict__ grid_out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int NP = N + 1;
-  constexpr bool kUseU = (MODE == XY_PASS1_DENS || MODE == XY_PASS2);
+  constexpr int NN = N * N;
   const int iz = blockIdx.x, g = blockIdx.y;
   const SphereDev& s = a.s;
   cplx<T>* Cs = reinterpret_cast<cplx<T>*>(smem_raw);                 // [BO][cb_ncol]
   cplx<T>* Ys = Cs + BO * a.cb_ncol;                                    // [BO][nrow_max][NP]
-  cplx<T>* Pl = Ys + BO * s.nrow_max * NP;                              // [N][NP]  v' (pass 2)
-  cplx<T>* Us = Pl + (MODE == XY_PASS2 ? N * NP : 0);                   // [NST][BO][N][NP] u planes
-  cplx<T>* Dacc = Us + (kUseU ? NST * BO * N * NP : 0);                 // [N][NP] density
-  T* Pv = reinterpret_cast<T*>(Dacc + (MODE == XY_PASS1_DENS ? N * NP : 0));  // [N][NP] V (real)
-  const long plane = (long)N * N;
-  const int per_vec = s.nks * a.nbnd;
+  cplx<T>* Pl = Ys + BO * s.nrow_max * NP;                              // [N][N] v' (pass 2)
+  // [BO][N][N] u, then conj(u) x; 16-byte aligned for the cp.async copies
+  cplx<T>* Pb = Pl + (MODE == XY_PASS2 ? NN : 0);
+  Pb += (16 - (reinterpret_cast<size_t>(Pb) & 15)) % 16 / sizeof(cplx<T>);
+  cplx<T>* Dacc = Pb + (MODE == XY_PASS1_DENS ? BO * NN : 0);           // [N][N] density
+  T* Pv = reinterpret_cast<T*>(Dacc + (MODE == XY_PASS1_DENS ? NN : 0));  // [N][N] V (real)
+  const long plane = (long)NN;
 
   if (MODE == XY_PASS1 || MODE == XY_PASS1_DENS) {
-    for (int i = threadIdx.x; i < N * N; i += blockDim.x) Pv[(i / N) * NP + i % N] = vloc[iz * plane + i];
+    for (int i = threadIdx.x; i < NN; i += blockDim.x) Pv[i] = vloc[iz * plane + i];
   } else if (MODE == XY_PASS2) {
-    for (int i = threadIdx.x; i < N * N; i += blockDim.x) Pl[(i / N) * NP + i % N] = vpr[iz * plane + i];
+    for (int i = threadIdx.x; i < NN; i += blockDim.x) Pl[i] = vpr[iz * plane + i];
   }
   if (MODE == XY_PASS1_DENS)
-    for (int i = threadIdx.x; i < N * NP; i += blockDim.x) Dacc[i] = czero<T>();
+    for (int i = threadIdx.x; i < NN; i += blockDim.x) Dacc[i] = czero<T>();
 
   const int o_begin = a.o_off + g * a.per_group;
   const int o_end = a.o_off + min(a.norb, g * a.per_group + a.per_group);
-  auto stage_u = [&](int obatch, int stage) {
-    const int nbb = min(BO, o_end - obatch);
-    for (int b = 0; b < nbb; ++b) {
-      const cplx<T>* src = ur + (long)((obatch + b) % per_vec) * N * plane + iz * plane;
-      cplx<T>* dst = Us + (stage * BO + b) * N * NP;
-      for (int e = threadIdx.x; e < N * N; e += blockDim.x) {
-        const int row = e / N, col = e - row * N;
-        cp_async<sizeof(cplx<T>)>(dst + row * NP + col, src + e);
-      }
-    }
-  };
-  if (kUseU && o_begin < o_end) {
-    stage_u(o_begin, 0);
-    cp_async_commit();
-  }
-  int stage = 0;
-  for (int ob = o_begin; ob < o_end; ob += BO, stage = (NST == 2) ? (stage ^ 1) : 0) {
+  for (int ob = o_begin; ob < o_end; ob += BO) {
     const int nb = min(BO, o_end - ob);
     __syncthreads();
-    if (kUseU && NST == 2) {
-      if (ob + BO < o_end) stage_u(ob + BO, stage ^ 1);
+    if (MODE == XY_PASS1_DENS) {  // u planes of the batch's density orbitals -> Pb
+      constexpr int E = 16 / (int)sizeof(cplx<T>);   // complex values per 16-byte copy
+      for (int e = threadIdx.x; e < nb * (NN / E); e += blockDim.x) {
+        const int b = e / (NN / E), q = (e - b * (NN / E)) * E;
+        const int o = ob + b;
+        if (a.f_pervec.div(o) == a.dens_vec)
+          cp_async16(Pb + b * NN + q, ur + (long)a.f_pervec.mod(o) * N * plane + iz * plane + q);
+      }
       cp_async_commit();
     }
     if (MODE != XY_PASS2) {
       for (int i = threadIdx.x; i < nb * a.cb_ncol; i += blockDim.x) {
-        const int b = i / a.cb_ncol, c = i - b * a.cb_ncol;
-        const int o = ob + b, k = (o / a.nbnd) % s.nks;
+        const int b = a.f_ncol.div(i), c = i - b * a.cb_ncol;
+        const int o = ob + b, k = a.f_nks.mod(a.f_nbnd.div(o));
         Cs[i] = (c < s.ncol[k]) ? cbuf[(long)o * N * a.cb_ncol + (long)iz * a.cb_ncol + c] : czero<T>();
       }
       __syncthreads();
-      // inverse FFT along axis 2 of every sphere row (fixed m1)
+      // inverse FFT along axis 1 of every sphere row (fixed m2)
       for (int i = threadIdx.x; i < nb * s.nrow_max; i += blockDim.x) {
-        const int b = i / s.nrow_max, r = i - b * s.nrow_max;
-        const int o = ob + b, k = (o / a.nbnd) % s.nks;
+        const int b = a.f_nrow.div(i), r = i - b * s.nrow_max;
+        const int o = ob + b, k = a.f_nks.mod(a.f_nbnd.div(o));
         if (r >= s.nrow[k]) continue;
         const int4 rw = s.row[k * s.nrow_max + r];
         cplx<T> l[N];
@@ -170,73 +169,67 @@ __global__ void __launch_bounds__(128, 4) k_xy(XYArgs a, cplx<T>* __restrict__ c
 #pragma unroll
         for (int p = 0; p < N; ++p) ys[p] = l[p];
       }
+      if (MODE == XY_PASS1_DENS) cp_async_wait_all();
+      __syncthreads();
     }
-    if (kUseU) {
-      if (NST == 2) cp_async_wait_prev();
-      else cp_async_wait_all();
-    }
-    __syncthreads();
-    cplx<T>* Ub = Us + stage * (BO * N * NP);
-    // axis 1: one line per (orbital, j2)
+    // axis 2: one line per (orbital, j1), element p of the line at grid point (j2 = p, j1)
     for (int i = threadIdx.x; i < nb * N; i += blockDim.x) {
-      const int b = i / N, j2 = i - b * N;
-      const int o = ob + b, k = (o / a.nbnd) % s.nks;
+      const int b = i / N, j1 = i - b * N;
+      const int o = ob + b, k = a.f_nks.mod(a.f_nbnd.div(o));
       const int nr = s.nrow[k];
-      const int m1min = s.row[k * s.nrow_max].x;
+      const int m2min = s.row[k * s.nrow_max].x;
       cplx<T> l[N];
       if (MODE == XY_PASS2) {
-        const cplx<T>* u = Ub + (b * N + j2) * NP;
+        const cplx<T>* u = ur + (long)a.f_pervec.mod(o) * N * plane + iz * plane + j1;
 #pragma unroll
-        for (int p = 0; p < N; ++p) l[p] = cmul(Pl[j2 * NP + p], u[p]);
+        for (int p = 0; p < N; ++p) l[p] = cmul(Pl[p * N + j1], u[p * N]);
       } else {
 #pragma unroll
         for (int p = 0; p < N; ++p) {
-          const int r = wrapn<N>(p - m1min);
-          l[p] = (r < nr) ? Ys[(b * s.nrow_max + r) * NP + j2] : czero<T>();
+          const int r = wrapn<N>(p - m2min);
+          l[p] = (r < nr) ? Ys[(b * s.nrow_max + r) * NP + j1] : czero<T>();
         }
         fft_line<T, N, +1>(l);
         if (MODE == XY_STORE) {
-          cplx<T>* dst = grid_out + (long)o * N * plane + iz * plane + (long)j2 * N;
+          cplx<T>* dst = grid_out + (long)o * N * plane + iz * plane + j1;
 #pragma unroll
-          for (int p = 0; p < N; ++p) dst[p] = l[p];
+          for (int p = 0; p < N; ++p) dst[p * N] = l[p];
           continue;
         }
         if (MODE == XY_PASS1_DENS) {
-          // conj(u) x replaces this thread's own u line in place (reduced after the barrier)
-          cplx<T>* u = Ub + (b * N + j2) * NP;
-          const bool on = (o / per_vec) == a.dens_vec;
+          // conj(u) x of this line, summed over the batch's orbitals after the barrier
+          cplx<T>* pb = Pb + b * NN + j1;
+          if (a.f_pervec.div(o) == a.dens_vec) {
 #pragma unroll
-          for (int p = 0; p < N; ++p) u[p] = on ? cjmul(u[p], l[p]) : czero<T>();
+            for (int p = 0; p < N; ++p) pb[p * N] = cjmul(pb[p * N], l[p]);
+          } else {
+#pragma unroll
+            for (int p = 0; p < N; ++p) pb[p * N] = czero<T>();
+          }
         }
 #pragma unroll
-        for (int p = 0; p < N; ++p) l[p] = l[p] * Pv[j2 * NP + p];
+        for (int p = 0; p < N; ++p) l[p] = l[p] * Pv[p * N + j1];
       }
       fft_line<T, N, -1>(l);
 #pragma unroll
       for (int p = 0; p < N; ++p) {
-        const int r = wrapn<N>(p - m1min);
-        if (r < nr) Ys[(b * s.nrow_max + r) * NP + j2] = l[p];
+        const int r = wrapn<N>(p - m2min);
+        if (r < nr) Ys[(b * s.nrow_max + r) * NP + j1] = l[p];
       }
     }
     __syncthreads();
     if (MODE == XY_STORE) continue;
     if (MODE == XY_PASS1_DENS) {  // density of the batch, orbitals summed in a fixed order
-      for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
-        const int q = (i / N) * NP + i % N;
-        cplx<T> acc = Dacc[q];
-        for (int b = 0; b < nb; ++b) acc = acc + Ub[b * N * NP + q];
-        Dacc[q] = acc;
+      for (int i = threadIdx.x; i < NN; i += blockDim.x) {
+        cplx<T> acc = Dacc[i];
+        for (int b = 0; b < nb; ++b) acc = acc + Pb[b * NN + i];
+        Dacc[i] = acc;
       }
     }
-    if (kUseU && NST == 1) {  // the planes are consumed: start the next batch's copies
-      if (MODE == XY_PASS1_DENS) __syncthreads();
-      if (ob + BO < o_end) stage_u(ob + BO, 0);
-      cp_async_commit();
-    }
-    // forward FFT along axis 2 of every row, keep the row's columns
+    // forward FFT along axis 1 of every row, keep the row's columns
     for (int i = threadIdx.x; i < nb * s.nrow_max; i += blockDim.x) {
-      const int b = i / s.nrow_max, r = i - b * s.nrow_max;
-      const int o = ob + b, k = (o / a.nbnd) % s.nks;
+      const int b = a.f_nrow.div(i), r = i - b * s.nrow_max;
+      const int o = ob + b, k = a.f_nks.mod(a.f_nbnd.div(o));
       if (r >= s.nrow[k]) continue;
       const int4 rw = s.row[k * s.nrow_max + r];
       cplx<T> l[N];
@@ -253,8 +246,8 @@ __global__ void __launch_bounds__(128, 4) k_xy(XYArgs a, cplx<T>* __restrict__ c
     }
     __syncthreads();
     for (int i = threadIdx.x; i < nb * a.cb_ncol; i += blockDim.x) {
-      const int b = i / a.cb_ncol, c = i - b * a.cb_ncol;
-      const int o = ob + b, k = (o / a.nbnd) % s.nks;
+      const int b = a.f_ncol.div(i), c = i - b * a.cb_ncol;
+      const int o = ob + b, k = a.f_nks.mod(a.f_nbnd.div(o));
       if (c >= s.ncol[k]) continue;
       cplx<T>* dst = cbuf + (long)o * N * a.cb_ncol + (long)iz * a.cb_ncol + c;
       *dst = (MODE == XY_PASS2) ? *dst + Cs[i] : Cs[i];
@@ -262,8 +255,7 @@ __global__ void __launch_bounds__(128, 4) k_xy(XYArgs a, cplx<T>* __restrict__ c
   }
   if (MODE == XY_PASS1_DENS) {
     __syncthreads();
-    for (int i = threadIdx.x; i < N * N; i += blockDim.x)
-      nprt[(long)g * N * plane + iz * plane + i] = Dacc[(i / N) * NP + i % N];
+    for (int i = threadIdx.x; i < NN; i += blockDim.x) nprt[(long)g * N * plane + iz * plane + i] = Dacc[i];
   }
 }
 
@@ -747,13 +739,14 @@ __global__ void __launch_bounds__(128) k_nh_normalize(int j, int nks, int nbnd, 
   }
 }
 
-// z_j = (1/nks) sum_k zpart[j][k] for j in [j0, j1).
-static __global__ void k_reduce_z(const cplx<double>* __restrict__ zpart, int nks, int j0, int j1,
+// z_j = (1/nks) sum_k zpart[j][k] for j in [j0, j1)
+// (nzp partials per step: one per k, or one per (k, chunk) on the split path)
+static __global__ void k_reduce_z(const cplx<double>* __restrict__ zpart, int nzp, int nks, int j0, int j1,
                                   cplx<double>* __restrict__ z) {
   const int j = j0 + blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= j1) return;
   double zr = 0, zi = 0;
-  for (int k = 0; k < nks; ++k) { zr += zpart[(long)j * nks + k].x; zi += zpart[(long)j * nks + k].y; }
+  for (int k = 0; k < nzp; ++k) { zr += zpart[(long)j * nzp + k].x; zi += zpart[(long)j * nzp + k].y; }
   z[j] = mk(zr / nks, zi / nks);
 }
 

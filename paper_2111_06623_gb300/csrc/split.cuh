@@ -1,0 +1,359 @@
+// Per-k work of the pseudo-Hermitian step split over several CTAs per k-point (sm_103a).
+//
+// The fused per-k kernels (k_zinv_ph, k_zfwd_proj) hold a whole k block of two vectors,
+// 2 nbnd npw complex values, in one CTA's shared memory.  Systems whose k blocks do not fit
+// (the eight-atom cell: 16 bands x 1632 plane waves, 420 KB in FP32) take this path: every
+// k block is cut into chunks of kChunk plane waves (for the projections) or of kLines column
+// lines (for the axis-3 transforms), one CTA each, and the small dot blocks of P_c and of
+// the KB projectors are formed as per-chunk partial sums that the next kernel reduces over
+// the chunks in a fixed order (deterministic, no atomics).
+//
+// One pseudo-Hermitian step here: k_sp_start (beta_j, z_j partial, r_{j+1} before P_c,
+// partial U^H r) -> k_sp_proj_cols (P_c, axis-3 inverse FFT) -> planes and response
+// potential as in the fused path -> k_sp_zfwd (axis-3 forward FFT, gather, kinetic - eps)
+// -> k_sp_dots (partial B^H x, U^H t) -> k_sp_apply (KB, P_c, output, norm partial).
+#pragma once
+#include "kernels.cuh"
+
+namespace ll {
+
+constexpr int kChunk = 512;    // plane waves per projection chunk
+constexpr int kLines = 256;    // column lines per axis-3 CTA
+constexpr int kTile = 32;      // plane waves per shared-memory tile of the dot blocks
+constexpr int kTileP = kTile + 1;  // padded row of a tile (conflict-free column reads)
+constexpr int kMaxPairs = 2048;  // ni * nj of one dot block (nproj <= 64, nbnd <= 32)
+
+// sum_i p[i], i < n, by the whole block in a fixed order; every thread gets the result.
+__device__ __forceinline__ double block_sum(const double* p, int n) {
+  __shared__ double wsum[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += p[i];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = s;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w];
+  __syncthreads();
+  return t;
+}
+
+// out[i*nj + j] = sum_{g0 <= g < g1} conj(A[i*lda + g]) B[j*ldb + g] for all ni x nj pairs.
+// Each thread owns up to kMaxPairs/blockDim pairs; the plane waves stream through shared
+// memory in tiles of kTile, each tile summed in T and added to a double accumulator.
+// `tile`: (ni + nj) * kTileP complex T of shared memory.  Called by the whole block.
+template <typename T>
+__device__ void chunk_dots(const cplx<T>* A, long lda, const cplx<T>* B, long ldb, int g0, int g1, int ni, int nj,
+                           cplx<T>* tile, cplx<double>* out) {
+  constexpr int PPT = kMaxPairs / 256;
+  const int np = ni * nj;
+  double ar[PPT], ai[PPT];
+#pragma unroll
+  for (int q = 0; q < PPT; ++q) ar[q] = ai[q] = 0.0;
+  cplx<T>* At = tile;
+  cplx<T>* Bt = tile + ni * kTileP;
+  for (int t0 = g0; t0 < g1; t0 += kTile) {
+    const int nt = min(kTile, g1 - t0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < (ni + nj) * kTile; e += blockDim.x) {
+      const int row = e / kTile, g = e - row * kTile;
+      cplx<T> v = czero<T>();
+      if (g < nt) v = row < ni ? A[(long)row * lda + t0 + g] : B[(long)(row - ni) * ldb + t0 + g];
+      tile[row * kTileP + g] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < PPT; ++q) {
+      const int pr = threadIdx.x + q * blockDim.x;
+      if (pr < np) {
+        const int i = pr / nj, j = pr - i * nj;
+        T sr = T(0), si = T(0);
+        for (int g = 0; g < kTile; ++g) {
+          const cplx<T> a = At[i * kTileP + g], b = Bt[j * kTileP + g];
+          sr += a.x * b.x + a.y * b.y;
+          si += a.x * b.y - a.y * b.x;
+        }
+        ar[q] += (double)sr;
+        ai[q] += (double)si;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < PPT; ++q) {
+    const int pr = threadIdx.x + q * blockDim.x;
+    if (pr < np) out[pr] = mk(ar[q], ai[q]);
+  }
+  __syncthreads();
+}
+
+// Step j, first part: beta_j = sqrt((1/nks) sum of the norm partials), the z_j partial of
+// the chunk, r_{j+1} = X_j/beta_j - beta_j v_{j-1} into R, v_j = r_j/beta_j into Vp, and the
+// chunk's partial U^H r_{j+1}.  grid (nks, nchunk), block 256.
+template <typename T>
+__global__ void __launch_bounds__(256) k_sp_start(int j, int r_upper, int nks, int nbnd, int npw_pad,
+                                                  const int* __restrict__ npw, int nchunk,
+                                                  const double* __restrict__ part, cplx<T>* __restrict__ R,
+                                                  const cplx<T>* __restrict__ X, cplx<T>* __restrict__ Vp,
+                                                  const cplx<T>* __restrict__ y, const cplx<T>* __restrict__ ukq,
+                                                  Coef co, double tol, cplx<double>* __restrict__ spart) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T>* tile = reinterpret_cast<cplx<T>*>(smem_raw);
+  __shared__ double sbeta;
+  __shared__ double zred[2][8];
+  const int k = blockIdx.x, c = blockIdx.y;
+  const int g0 = c * kChunk, g1 = min(npw_pad, g0 + kChunk);
+  const double b2 = block_sum(part, nks * nchunk) / nks;
+  if (threadIdx.x == 0) {
+    double b = 1.0;
+    if (!(b2 > tol)) flag_error(co.err, b2 <= 0.0 ? DEV_NOTPD : DEV_BREAKDOWN, j);
+    else b = sqrt(b2);
+    sbeta = b;
+    if (k == 0 && c == 0) { co.beta[j - 1] = b; co.gamma[j - 1] = mk(b, 0.0); }
+  }
+  __syncthreads();
+  const double b = sbeta;
+  const long base = (long)k * nbnd * npw_pad;
+  const int zi = (j - 1) * nks * nchunk + k * nchunk + c;
+  if (r_upper) {  // z_j partial = (y, r_j)/beta_j over the chunk
+    double zr = 0.0, zim = 0.0;
+    for (int e = threadIdx.x; e < nbnd * (g1 - g0); e += blockDim.x) {
+      const int v = e / (g1 - g0), g = g0 + e - v * (g1 - g0);
+      const cplx<T> a = y[base + (long)v * npw_pad + g], r = R[base + (long)v * npw_pad + g];
+      zr += (double)(a.x * r.x + a.y * r.y);
+      zim += (double)(a.x * r.y - a.y * r.x);
+    }
+    zr = warp_sum(zr);
+    zim = warp_sum(zim);
+    if ((threadIdx.x & 31) == 0) { zred[0][threadIdx.x >> 5] = zr; zred[1][threadIdx.x >> 5] = zim; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sr = 0.0, si = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { sr += zred[0][w]; si += zred[1][w]; }
+      co.zpart[zi] = mk(sr / b, si / b);
+    }
+  } else if (threadIdx.x == 0) {
+    co.zpart[zi] = mk(0.0, 0.0);
+  }
+  __syncthreads();
+  const T ib = (T)(1.0 / b), bb = (T)b;
+  for (int e = threadIdx.x; e < nbnd * (g1 - g0); e += blockDim.x) {
+    const int v = e / (g1 - g0), g = g0 + e - v * (g1 - g0);
+    const long i = base + (long)v * npw_pad + g;
+    const cplx<T> r = R[i];
+    R[i] = X[i] * ib - Vp[i] * bb;
+    Vp[i] = r * ib;
+  }
+  __syncthreads();
+  chunk_dots<T>(ukq + base, npw_pad, R + base, npw_pad, g0, max(g0, min(g1, npw[k])), nbnd, nbnd, tile,
+                spart + ((long)k * nchunk + c) * nbnd * nbnd);
+}
+
+// S = sum over chunks of the partials (fixed order), rounded to T into St[w*nbnd + v].
+template <typename T>
+__device__ __forceinline__ void reduce_coef(const cplx<double>* part, int nchunk, int np, cplx<T>* St,
+                                            const double* mult = nullptr, int nj = 1) {
+  for (int p = threadIdx.x; p < np; p += blockDim.x) {
+    double re = 0.0, im = 0.0;
+    for (int c = 0; c < nchunk; ++c) {
+      re += part[(long)c * np + p].x;
+      im += part[(long)c * np + p].y;
+    }
+    const double m = mult ? mult[p / nj] : 1.0;
+    St[p] = mk((T)(re * m), (T)(im * m));
+  }
+}
+
+// Step j, second part: R <- P_c R (coefficients from the chunk partials), then the sphere
+// columns of R inverse-FFT'd along axis 3 into the column buffer.  One thread per column line
+// (band v, column c); grid (nks, ceil(nbnd ncol_max / kLines)), block kLines.
+template <typename T, int N>
+__global__ void __launch_bounds__(kLines) k_sp_proj_cols(SphereDev s, int nbnd, int nchunk,
+                                                         const cplx<double>* __restrict__ spart,
+                                                         cplx<T>* __restrict__ R, const cplx<T>* __restrict__ ukq,
+                                                         cplx<T>* __restrict__ cbuf, int cb_ncol) {
+  __shared__ cplx<T> St[32 * 32];
+  const int k = blockIdx.x, npw_pad = s.npw_pad;
+  reduce_coef<T>(spart + (long)k * nchunk * nbnd * nbnd, nchunk, nbnd * nbnd, St);
+  __syncthreads();
+  const int nc = s.ncol[k];
+  const int it = blockIdx.y * kLines + threadIdx.x;
+  if (it >= nbnd * nc) return;
+  const int v = it / nc, c = it - v * nc;
+  const int4 cl = s.col[k * s.ncol_max + c];
+  const long base = (long)k * nbnd * npw_pad;
+  cplx<T>* r = R + base + (long)v * npw_pad + s.colstart[k * s.ncol_max + c];
+  const cplx<T>* u = ukq + base + s.colstart[k * s.ncol_max + c];
+  cplx<T> a[N];
+#pragma unroll
+  for (int p = 0; p < N; ++p) {
+    const int i = wrapn<N>(p - cl.z);
+    cplx<T> val = czero<T>();
+    if (i < cl.w) {
+      val = r[i];
+      for (int w = 0; w < nbnd; ++w) val = val - cmul(u[(long)w * npw_pad + i], St[w * nbnd + v]);
+      r[i] = val;
+    }
+    a[p] = val;
+  }
+  fft_line<T, N, +1>(a);
+  cplx<T>* dst = cbuf + ((long)k * nbnd + v) * N * cb_ncol + c;
+#pragma unroll
+  for (int p = 0; p < N; ++p) dst[(long)p * cb_ncol] = a[p];
+}
+
+// Operator, last stage, first part: forward FFT of the columns along axis 3, gather of the
+// sphere (1/N^3) plus (1/2|k+Q+G|^2 - eps_vk) x into t = out.  grid (nks, nvec, lines).
+template <typename T, int N>
+__global__ void __launch_bounds__(kLines) k_sp_zfwd(SphereDev s, int nbnd, const cplx<T>* __restrict__ cbuf,
+                                                    int cb_ncol, const cplx<T>* __restrict__ xin,
+                                                    const T* __restrict__ kin, const double* __restrict__ eps,
+                                                    cplx<T>* __restrict__ xout) {
+  const int k = blockIdx.x, vec = blockIdx.y, nks = s.nks, npw_pad = s.npw_pad;
+  const int nc = s.ncol[k];
+  const int it = blockIdx.z * kLines + threadIdx.x;
+  if (it >= nbnd * nc) return;
+  const int v = it / nc, c = it - v * nc;
+  const long o = ((long)vec * nks + k) * nbnd + v;
+  const int4 cl = s.col[k * s.ncol_max + c];
+  const cplx<T>* src = cbuf + o * (long)N * cb_ncol + c;
+  cplx<T> a[N];
+#pragma unroll
+  for (int p = 0; p < N; ++p) a[p] = src[(long)p * cb_ncol];
+  fft_line<T, N, -1>(a);
+  const T scale = T(1) / T(N * N * N);
+  const T ev = (T)eps[k * nbnd + v];
+  const int st = s.colstart[k * s.ncol_max + c];
+  const cplx<T>* x = xin + o * npw_pad + st;
+  const T* kn = kin + (long)k * npw_pad + st;
+  cplx<T>* t = xout + o * npw_pad + st;
+#pragma unroll
+  for (int p = 0; p < N; ++p) {
+    const int i = wrapn<N>(p - cl.z);
+    if (i < cl.w) t[i] = x[i] * (kn[i] - ev) + a[p] * scale;
+  }
+}
+
+// Partial dot blocks of one chunk: C = B^H x (nproj x nbnd, when nproj > 0) and
+// S1 = U^H t (nbnd x nbnd).  grid (nks, nvec, nchunk), block 256.
+template <typename T>
+__global__ void __launch_bounds__(256) k_sp_dots(int nks, int nbnd, int npw_pad, const int* __restrict__ npw,
+                                                 int nchunk, int nproj,
+                                                 const cplx<T>* __restrict__ xin, const cplx<T>* __restrict__ t,
+                                                 const cplx<T>* __restrict__ ukq, const cplx<T>* __restrict__ bkq,
+                                                 cplx<double>* __restrict__ cpart, cplx<double>* __restrict__ spart) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T>* tile = reinterpret_cast<cplx<T>*>(smem_raw);
+  const int k = blockIdx.x, vec = blockIdx.y, c = blockIdx.z;
+  const int g0 = c * kChunk, g1 = max(g0, min(npw[k], g0 + kChunk));   // sphere points only
+  const long kv = (long)vec * nks + k;
+  const long base = kv * nbnd * npw_pad;
+  if (nproj > 0)
+    chunk_dots<T>(bkq + (long)k * nproj * npw_pad, npw_pad, xin + base, npw_pad, g0, g1, nproj, nbnd, tile,
+                  cpart + (kv * nchunk + c) * nproj * nbnd);
+  chunk_dots<T>(ukq + (long)k * nbnd * npw_pad, npw_pad, t + base, npw_pad, g0, g1, nbnd, nbnd, tile,
+                spart + (kv * nchunk + c) * nbnd * nbnd);
+}
+
+// Operator, last stage, second part: c = D o (B^H x), S = U^H t + (U^H B) c, then
+// t <- t + B c - U S (= P_c (t + B c)), zero on the padding, and the chunk's partial
+// Re(x^H t).  ub: U^H B per k, [nbnd][nproj] (double).  grid (nks, nvec, nchunk), block 256;
+// dynamic shared memory nproj nbnd (16 + sizeof(cplx<T>)) + nbnd^2 sizeof(cplx<T>) bytes.
+template <typename T>
+__global__ void __launch_bounds__(256) k_sp_apply(int nks, int nbnd, int npw_pad, const int* __restrict__ npw,
+                                                  int nchunk, int nproj, const cplx<T>* __restrict__ xin,
+                                                  cplx<T>* __restrict__ t, const cplx<T>* __restrict__ ukq,
+                                                  const cplx<T>* __restrict__ bkq, const double* __restrict__ dij,
+                                                  const cplx<double>* __restrict__ ub,
+                                                  const cplx<double>* __restrict__ cpart,
+                                                  const cplx<double>* __restrict__ spart, double* __restrict__ part) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<double>* cd = reinterpret_cast<cplx<double>*>(smem_raw);     // [nproj * nbnd]
+  cplx<T>* ct = reinterpret_cast<cplx<T>*>(cd + nproj * nbnd);       // [nproj * nbnd]
+  cplx<T>* St = ct + nproj * nbnd;                                    // [nbnd * nbnd]
+  __shared__ double wred[8];
+  const int k = blockIdx.x, vec = blockIdx.y, c = blockIdx.z;
+  const long kv = (long)vec * nks + k;
+  const int np = npw[k];
+  const int g0 = c * kChunk, g1 = min(npw_pad, g0 + kChunk);
+  if (nproj > 0) {
+    for (int p = threadIdx.x; p < nproj * nbnd; p += blockDim.x) {
+      double re = 0.0, im = 0.0;
+      for (int cc = 0; cc < nchunk; ++cc) {
+        re += cpart[(kv * nchunk + cc) * nproj * nbnd + p].x;
+        im += cpart[(kv * nchunk + cc) * nproj * nbnd + p].y;
+      }
+      const double m = dij[p / nbnd];
+      cd[p] = mk(re * m, im * m);
+      ct[p] = mk((T)(re * m), (T)(im * m));
+    }
+    __syncthreads();
+  }
+  for (int p = threadIdx.x; p < nbnd * nbnd; p += blockDim.x) {
+    double re = 0.0, im = 0.0;
+    for (int cc = 0; cc < nchunk; ++cc) {
+      re += spart[(kv * nchunk + cc) * nbnd * nbnd + p].x;
+      im += spart[(kv * nchunk + cc) * nbnd * nbnd + p].y;
+    }
+    const int w = p / nbnd, v = p - w * nbnd;
+    for (int q = 0; q < nproj; ++q) {
+      const cplx<double> a = ub[((long)k * nbnd + w) * nproj + q], d = cd[q * nbnd + v];
+      re += a.x * d.x - a.y * d.y;
+      im += a.x * d.y + a.y * d.x;
+    }
+    St[p] = mk((T)re, (T)im);
+  }
+  __syncthreads();
+  const long base = kv * nbnd * npw_pad;
+  const cplx<T>* uk = ukq + (long)k * nbnd * npw_pad;
+  const cplx<T>* bk = bkq + (long)k * nproj * npw_pad;
+  double nr = 0.0;
+  for (int e = threadIdx.x; e < nbnd * (g1 - g0); e += blockDim.x) {
+    const int v = e / (g1 - g0), g = g0 + e - v * (g1 - g0);
+    const long i = base + (long)v * npw_pad + g;
+    cplx<T> acc = czero<T>();
+    if (g < np) {
+      acc = t[i];
+      for (int q = 0; q < nproj; ++q) acc = acc + cmul(bk[(long)q * npw_pad + g], ct[q * nbnd + v]);
+      for (int w = 0; w < nbnd; ++w) acc = acc - cmul(uk[(long)w * npw_pad + g], St[w * nbnd + v]);
+      const cplx<T> x = xin[i];
+      nr += (double)(x.x * acc.x + x.y * acc.y);
+    }
+    t[i] = acc;
+  }
+  nr = warp_sum(nr);
+  if ((threadIdx.x & 31) == 0) wred[threadIdx.x >> 5] = nr;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += wred[w];
+    part[kv * nchunk + c] = s;
+  }
+}
+
+// Set-up: partial U^H B per (k, chunk).  grid (nks, nchunk), block 256.
+template <typename T>
+__global__ void __launch_bounds__(256) k_sp_ub(int nbnd, int npw_pad, const int* __restrict__ npw, int nchunk,
+                                               int nproj, const cplx<T>* __restrict__ ukq,
+                                               const cplx<T>* __restrict__ bkq, cplx<double>* __restrict__ part) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T>* tile = reinterpret_cast<cplx<T>*>(smem_raw);
+  const int k = blockIdx.x, c = blockIdx.y;
+  const int g0 = c * kChunk, g1 = max(g0, min(npw[k], g0 + kChunk));
+  chunk_dots<T>(ukq + (long)k * nbnd * npw_pad, npw_pad, bkq + (long)k * nproj * npw_pad, npw_pad, g0, g1, nbnd,
+                nproj, tile, part + ((long)k * nchunk + c) * nbnd * nproj);
+}
+
+// Set-up: U^H B per k from the chunk partials (double).  grid nks, block 256.
+static __global__ void k_sp_reduce(int nchunk, int np, const cplx<double>* __restrict__ part,
+                                   cplx<double>* __restrict__ out) {
+  const int k = blockIdx.x;
+  for (int p = threadIdx.x; p < np; p += blockDim.x) {
+    double re = 0.0, im = 0.0;
+    for (int c = 0; c < nchunk; ++c) {
+      re += part[((long)k * nchunk + c) * np + p].x;
+      im += part[((long)k * nchunk + c) * np + p].y;
+    }
+    out[(long)k * np + p] = mk(re, im);
+  }
+}
+
+}  // namespace ll

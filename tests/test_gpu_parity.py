@@ -210,14 +210,56 @@ def test_kb_workload_first_coefficients(lib, kb):
     assert _coef_rel(got32, ref, 6) < 1e-4
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_plane_staging_depths_bit_identical(lib, small, precision, monkeypatch):
-    """The autotuner chooses between single- and double-buffered orbital-plane staging; both
-    must give the same coefficients bit for bit."""
-    out = []
-    for depth in ("1", "2"):
-        monkeypatch.setenv("LL_PLANE_STAGES", depth)
-        out.append(chain_from_bundle(small, precision=precision, max_steps=30).lanczos(30))
-    monkeypatch.delenv("LL_PLANE_STAGES")
-    for a, b in zip(*out):
-        assert np.array_equal(a, b)
+# ---- per-k work split over several CTAs per k-point (systems whose k blocks do not fit one
+# CTA's shared memory; LL_SPLIT_PERK=1 forces it on the smaller cells) ----------------------
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+def test_split_path_single_application(lib, small, kb, precision, tol, monkeypatch):
+    """Forced split path, both operator halves against the oracle, with and without KB."""
+    monkeypatch.setenv("LL_SPLIT_PERK", "1")
+    for b in (small, kb):
+        sys = System(b)
+        ch = chain_from_bundle(b, precision=precision, max_steps=4)
+        x = _rand(sys, 12)
+        for upper in (False, True):
+            assert rel_batch(ch.apply(x, upper), sys.apply_op(x, upper)) < tol
+
+
+def test_split_path_coefficients_small(lib, small, monkeypatch):
+    """Forced split path, 120 pseudo-Hermitian FP64 steps: the oracle's first 100 coefficients."""
+    sys = System(small)
+    ref = lanczos.pseudo_hermitian(sys, 120)
+    monkeypatch.setenv("LL_SPLIT_PERK", "1")
+    got = chain_from_bundle(small, max_steps=120).lanczos(120)
+    assert _coef_rel(got, ref, 100) < 1e-10
+
+
+@pytest.fixture(scope="module")
+def cubic8():
+    return w.get_bundle(w.config_cubic8())
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+def test_cubic8_single_application(lib, cubic8, precision, tol):
+    """Eight-atom cell (16 bands, ~1630 plane waves, 1024 orbitals): its k blocks exceed one
+    CTA's shared memory, so the chain takes the split path by itself."""
+    sys = System(cubic8)
+    ch = chain_from_bundle(cubic8, precision=precision, max_steps=4)
+    x = _rand(sys, 13)
+    for upper in (False, True):
+        assert rel_batch(ch.apply(x, upper), sys.apply_op(x, upper)) < tol
+
+
+def test_cubic8_first_coefficients(lib, cubic8):
+    sys = System(cubic8)
+    ref = lanczos.pseudo_hermitian(sys, 8)
+    got64 = chain_from_bundle(cubic8, max_steps=8).lanczos(8)
+    assert _coef_rel(got64, ref, 8) < 1e-10
+    got32 = chain_from_bundle(cubic8, precision="fp32", max_steps=8).lanczos(8)
+    assert _coef_rel(got32, ref, 8) < 1e-4
+
+
+def test_cubic8_non_hermitian_unsupported(lib, cubic8):
+    with pytest.raises(lib.LLError) as e:
+        chain_from_bundle(cubic8, flavour="nh", max_steps=4)
+    assert e.value.code == lib.LL_EUNSUPPORTED

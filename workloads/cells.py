@@ -107,6 +107,24 @@ def config_kb() -> SystemSpec:
                       approx="tddft", kb=True, scf_kmesh=(4, 4, 4), steps=1000, flavour="ph")
 
 
+def _diamond_cubic(a: float) -> tuple[np.ndarray, np.ndarray]:
+    """Conventional cubic cell of the diamond structure: 8 atoms."""
+    fcc = np.array([[0.0, 0.0, 0.0], [0.0, 0.5, 0.5], [0.5, 0.0, 0.5], [0.5, 0.5, 0.0]])
+    frac = np.concatenate([fcc, fcc + 0.25])
+    return a * np.eye(3), frac * a
+
+
+def config_cubic8(q_cart: np.ndarray | None = None) -> SystemSpec:
+    """Eight-atom conventional cubic cell (Omega = 1080 bohr^3), 20 Ry, 32^3 grid, 4x4x4 mesh,
+    16 bands (8 x 4 electrons / 2), no extra KB channels (the repulsive s channel of every
+    atom still makes 8 projectors), Q = 0.1 (2 pi/a) x unless given.  The self-consistent
+    density is converged on a 2x2x2 mesh."""
+    lat, tau = _diamond_cubic(A_LAT)
+    q = 0.1 * (2 * np.pi / A_LAT) * np.array([1.0, 0.0, 0.0]) if q_cart is None else np.asarray(q_cart, float)
+    return SystemSpec("cubic8_20ry_32", lat, tau, 4.0, 1.0, 20.0, 32, (4, 4, 4), 16, q,
+                      approx="tddft", scf_kmesh=(2, 2, 2), steps=1500, flavour="ph")
+
+
 def config_tiny(kb: bool = False, approx: str = "tddft") -> SystemSpec:
     """A cell small enough for brute-force Casida diagonalisation: 4 Ry, 12^3, 2x2x2 k."""
     lat, tau = _diamond(A_LAT)
@@ -134,7 +152,7 @@ def config_free_electron(nk: int = 6, ecut: float = 3.0, nfft: int = 12,
     return s
 
 
-CONFIGS = {"small": config_small, "kb": config_kb, "tiny": config_tiny}
+CONFIGS = {"small": config_small, "kb": config_kb, "tiny": config_tiny, "cubic8": config_cubic8}
 
 
 def sphere(kcart: np.ndarray, bvec: np.ndarray, ecut_ry: float, guard: float = 1e-9) -> np.ndarray:

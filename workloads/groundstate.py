@@ -308,7 +308,7 @@ def build_bundle(spec: SystemSpec, verbose: bool = False) -> Bundle:
     npw_est = 4.0 / 3.0 * np.pi * spec.ecut_ry ** 1.5 * spec.omega / (2 * np.pi) ** 3
     runner = _Runner(2 * len(kc) * npw_est ** 3 * 10)
     try:
-        v, rho, iters = scf(spec, verbose=verbose, runner=runner)
+        v, rho, iters = _scf_cached(spec, verbose, runner)
         vbox = np.fft.fftn(v) / n ** 3
         if spec.free_electron:
             res_k = [_feg_states(spec, k) for k in kc]
@@ -332,6 +332,25 @@ def build_bundle(spec: SystemSpec, verbose: bool = False) -> Bundle:
                   eps_k=np.array([r[1][:nb] for r in res_k]),
                   eps_kq=np.array([r[1][:nb] for r in res_q]),
                   vloc_r=v, rho_r=rho, beta_kq=beta, dij=dij, scf_iters=iters, gap_min=gap)
+
+
+def _scf_cached(spec: SystemSpec, verbose: bool, runner) -> tuple:
+    """scf() once per crystal: the self-consistent potential does not depend on Q, so every
+    momentum transfer of one system reuses it (npz under .ll_cache/)."""
+    d = {k: (np.asarray(v).round(12).tolist() if isinstance(v, np.ndarray) else v)
+         for k, v in spec.__dict__.items()
+         if k not in ("steps", "flavour", "approx", "extra", "q_cart", "kmesh", "name", "scf_kmesh")}
+    d["scf_mesh"] = list(spec.scf_kmesh or spec.kmesh)
+    key = hashlib.sha1(json.dumps(d, sort_keys=True, default=str).encode()).hexdigest()[:16]
+    path = os.path.join(cache_dir(), f"scf_{key}.npz")
+    if os.path.exists(path):
+        z = np.load(path)
+        return z["v"], z["rho"], int(z["iters"])
+    v, rho, iters = scf(spec, verbose=verbose, runner=runner)
+    tmp = path + f".{os.getpid()}.tmp.npz"
+    np.savez(tmp, v=v, rho=rho, iters=iters)
+    os.replace(tmp, path)
+    return v, rho, iters
 
 
 def _spec_key(spec: SystemSpec) -> str:
