@@ -261,6 +261,92 @@ def _serving(b_kb, n_jobs: int, seed: int = 7):
             "stream": "Poisson 20 jobs/s (seed 7), small cell at 4 Q + KB workload, 500-1500 FP32 PH steps"}
 
 
+def q_pool(n: int = 64) -> np.ndarray:
+    """Momentum transfers of the many-Q batch: |q| ~ U(0.05, 0.6) 2 pi/a, direction a
+    normalised Gaussian 3-vector, drawn from default_rng(4) (magnitudes first)."""
+    import workloads as w
+    rng = np.random.default_rng(4)
+    mag = rng.uniform(0.05, 0.6, size=n) * (2 * np.pi / w.A_LAT)
+    d = rng.normal(size=(n, 3))
+    return mag[:, None] * d / np.linalg.norm(d, axis=1, keepdims=True)
+
+
+def _batch_bundles(n_small: int, n_cubic: int):
+    """Ground states of the first q of the pool on the two-atom cell (10 Ry, 18^3, 4^3 k) and
+    on the eight-atom cubic cell (20 Ry, 32^3, 4^3 k, 16 bands); a q whose sphere puts a plane
+    wave on the cut-off is skipped."""
+    import workloads as w
+    out = {"fcc2_10ry_18": [], "cubic8_20ry_32": []}
+    for cell, n, mk in (("fcc2_10ry_18", n_small, lambda q: _with_q(w.config_small(), q)),
+                        ("cubic8_20ry_32", n_cubic, w.config_cubic8)):
+        for q in q_pool():
+            if len(out[cell]) >= n:
+                break
+            try:
+                spec = mk(q)
+                spec.name = "%s_q%s" % (cell, "_".join("%+.4f" % c for c in q))
+                out[cell].append(w.get_bundle(spec))
+            except ValueError:
+                continue
+    return out
+
+
+def _with_q(spec, q):
+    spec.q_cart = np.asarray(q, dtype=np.float64)
+    return spec
+
+
+def _batch(n_small: int, n_cubic: int, steps: int = 1500):
+    """Many independent chains on one GPU at once: n_small momentum transfers of the pool on
+    the two-atom cell and n_cubic on the eight-atom cell, all submitted together to the request
+    loop (one stream per chain), steps FP32 pseudo-Hermitian steps each.  Returns the whole
+    batch's steps/s and the wall time to the last spectrum."""
+    from paper_2111_06623_gb300 import ll
+    pools = _batch_bundles(n_small, n_cubic)
+    jobs = [(cell, b) for cell, bs in pools.items() for b in bs]
+    wgrid = np.linspace(0.0, 40.0, 4001)
+    srv = ll.Server(hbm_budget_bytes=150 << 30, max_slots=len(jobs), chunk=32)
+    ids, t0 = [], time.perf_counter()
+    for cell, bb in jobs:
+        s = bb.spec
+        ids.append(srv.submit(steps, wgrid, 0.1, lattice=s.lattice, nfft=s.nfft, kcart=bb.kcart,
+                              miller_k=bb.miller_k, miller_kq=bb.miller_kq, u_k=bb.u_k, u_kq=bb.u_kq, eps_k=bb.eps_k,
+                              vloc_r=bb.vloc_r, rho_r=bb.rho_r, beta_kq=bb.beta_kq, dij=bb.dij, q_cart=s.q_cart,
+                              approx="tddft", flavour="ph", precision="fp32", max_steps=steps))
+    res = {}
+    while len(res) < len(ids):
+        for i, (cell, _) in zip(ids, jobs):
+            if i not in res:
+                st, r = srv.poll(i)
+                if st in (ll.JOB_DONE, ll.JOB_FAILED):
+                    res[i] = (cell, st, r)
+        time.sleep(0.002)
+    wall = time.perf_counter() - t0
+    peak = srv.stats()["peak"]
+    srv.close()
+    done = sum(r["steps_done"] for _, st, r in res.values() if st == ll.JOB_DONE)
+    per_cell = {}
+    for cell, st, r in res.values():
+        c = per_cell.setdefault(cell, {"chains": 0, "failed": 0, "mean_run_s": 0.0})
+        c["chains"] += 1
+        c["failed"] += st != ll.JOB_DONE
+        c["mean_run_s"] += r["run_s"]
+    for c in per_cell.values():
+        c["mean_run_s"] /= max(1, c["chains"])
+    # one eight-atom chain alone (CUDA events, FP32): the per-chain speed of the larger cell
+    single = None
+    if pools["cubic8_20ry_32"]:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+        ch, _, ms, _ = _time_chain(pools["cubic8_20ry_32"][0], "fp32", 300, 5, stream)
+        ch.close()
+        single = {"cell": "cubic8_20ry_32", "steps": 300, "steps_per_s": 300 / (ms / 1e3), "ms_per_step": ms / 300}
+    return {"chains": len(jobs), "steps_per_chain": steps, "steps_per_s": done / wall, "wall_s": wall,
+            "single_chain": single,
+            "peak_hbm_gb": peak / 2 ** 30, "cells": per_cell,
+            "q_pool": "64 q, |q| ~ U(0.05, 0.6) 2pi/a, Gaussian directions, default_rng(4); first q of the pool per cell"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -292,6 +378,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--serving-jobs", type=int, default=16)
+    ap.add_argument("--batch-small", type=int, default=16, help="chains of the two-atom cell in the many-Q batch")
+    ap.add_argument("--batch-cubic", type=int, default=2, help="chains of the eight-atom cell in the many-Q batch")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")
@@ -382,6 +470,7 @@ def main():
                     "frac": None, "traffic": None}
 
     serving = _serving(b, args.serving_jobs) if args.serving_jobs > 0 else None
+    batch = _batch(args.batch_small, args.batch_cubic) if args.batch_small + args.batch_cubic > 0 else None
 
     cpu = None
     if rank == 0:
@@ -406,7 +495,7 @@ def main():
             "spectrum_err_fp32_vs_fp64_all_steps": spec_err_full,
             "step_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))} if lat else None,
             "kernel_ms": ms_cls, "kernel_launches": launches,
-            "roofline": roofline, "serving": serving, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(total), "clocks": clocks,
+            "roofline": roofline, "serving": serving, "batch": batch, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(total), "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

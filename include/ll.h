@@ -106,6 +106,27 @@ int ll_spectrum(const double* beta, const double* gamma, const double* z, int m,
                 const double* q_cart, const double* omega_ev, int n_omega, double eta_ev, double* chi,
                 double* eps_inv, double* eps, void* stream);
 
+/* Extrapolation of the Lanczos coefficients (Sec. 2.5 end, Sec. 3.3, Appendix A): the
+ * tridiagonal matrix of the m computed coefficients is continued to m_total x m_total at no
+ * cost.  The off-diagonal coefficients of index i >= m (arrays as in ll_lanczos, index 0 being
+ * b_1) take constant values: LL_EXTRAP_CONSTANT one value, the mean of beta (and of gamma)
+ * over the indices max(1, m/2)..m-1; LL_EXTRAP_OSC (bi-constant) the means over the even and
+ * over the odd indices of that range, each continuing its own parity.  z is continued with
+ * zeros.  m >= 2 (>= 4 for LL_EXTRAP_OSC), m <= m_total <= LL_EXTRAP_MAX, else LL_EINVAL;
+ * LL_EXTRAP_NO ignores m_total.  The means and the continued fraction run on the device. */
+enum { LL_EXTRAP_NO = 0, LL_EXTRAP_CONSTANT = 1, LL_EXTRAP_OSC = 2 };
+#define LL_EXTRAP_MAX 1000000
+
+/* ll_lanczos_spectrum with the chain's first m coefficients (m <= 0: all) extrapolated to
+ * m_total. */
+int ll_lanczos_spectrum_x(ll_handle* h, int m, int kind, int m_total, const double* omega_ev, int n_omega,
+                          double eta_ev, double* chi, double* eps_inv, double* eps);
+
+/* ll_spectrum with the caller's m coefficients extrapolated to m_total. */
+int ll_spectrum_x(const double* beta, const double* gamma, const double* z, int m, int kind, int m_total,
+                  double omega_cell, const double* q_cart, const double* omega_ev, int n_omega, double eta_ev,
+                  double* chi, double* eps_inv, double* eps, void* stream);
+
 /* Allocation-free variant of ll_spectrum, for callers that cannot allocate device memory
  * while they run: services whose memory pool has already reserved the GPU's memory, and
  * latency-critical loops where a cudaMalloc/cudaFree (which may synchronise the device and

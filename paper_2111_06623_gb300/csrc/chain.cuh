@@ -24,8 +24,10 @@ struct ChainBase {
   virtual int enqueue(int n, std::string& err) = 0;
   virtual int collect(double* beta, double* gamma, double* z, int* done, std::string& err) = 0;
   virtual int steps_queued() const = 0;
-  virtual int spectrum(int m, const double* w_ev, int nw, double eta_ev, double* chi, double* ei, double* e,
-                       std::string& err) = 0;
+  // kind / m_total: LL_EXTRAP_* continuation of the m coefficients to m_total (Sec. 3.3)
+  virtual int spectrum(int m, int kind, int m_total, const double* w_ev, int nw, double eta_ev, double* chi,
+                       double* ei, double* e, std::string& err) = 0;
+  virtual int steps() const = 0;
   virtual int apply(int upper, const double* x, double* out, std::string& err) = 0;
   virtual int get_map(int* out, std::string& err) = 0;
   virtual int get_start(double* y, std::string& err) = 0;
@@ -279,6 +281,12 @@ class Chain : public ChainBase {
     if ((rc = upload_sphere(hk_, dk_, err)) || (rc = upload_sphere(hq_, dq_, err))) return rc;
     cb_ncol_ = std::max(hk_.ncol_max, hq_.ncol_max);
     const int norb = nvec_ * nks_ * nbnd_;
+    {
+      int dev = 0, sms = 0;
+      if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+        nsm_ = sms;
+      cudaGetLastError();
+    }
     ngroups_ = groups_for(norb);
     // per-k work: fused (one CTA holds a k block) when it fits in shared memory, else split
     // over chunks of plane waves (LL_SPLIT_PERK=1 in the environment forces the split path)
@@ -473,9 +481,12 @@ class Chain : public ChainBase {
     return status;
   }
 
-  int spectrum(int m, const double* w_ev, int nw, double eta_ev, double* chi, double* ei, double* e,
-               std::string& err) override {
+  int steps() const override { return steps_; }
+
+  int spectrum(int m, int kind, int m_total, const double* w_ev, int nw, double eta_ev, double* chi, double* ei,
+               double* e, std::string& err) override {
     if (m <= 0 || m > steps_) m = steps_;
+    if (kind == LL_EXTRAP_NO || m_total < m) m_total = m;
     if (m < 1 || nw < 1) { err = "no coefficients or no frequencies"; return LL_EINVAL; }
     int rc;
     if (nw > spec_cap_) {
@@ -489,7 +500,12 @@ class Chain : public ChainBase {
     for (int i = 0; i < nw; ++i) w[i] = w_ev[i] / ha;
     LL_CK(cudaMemcpyAsync(spec_w_, w.data(), nw * sizeof(double), cudaMemcpyHostToDevice, st_));
     const double q2 = q_[0] * q_[0] + q_[1] * q_[1] + q_[2] * q_[2];
-    k_spectrum<<<(nw + 127) / 128, 128, 0, st_>>>(m, beta_, gamma_, z_, nw, spec_w_, eta_ev / ha, 4.0 / omega_,
+    if (m_total > m) {
+      if (!tail_ && (rc = alloc(&tail_, 1))) return rc;
+      k_extrap_tail<<<1, 256, 0, st_>>>(m, kind, beta_, gamma_, tail_);
+    }
+    k_spectrum<<<(nw + 127) / 128, 128, 0, st_>>>(m, m_total, m_total > m ? tail_ : nullptr, beta_, gamma_, z_, nw,
+                                                  spec_w_, eta_ev / ha, 4.0 / omega_,
                                                   4.0 * 3.14159265358979323846 / q2, spec_out_, spec_out_ + nw,
                                                   spec_out_ + 2L * nw);
     LL_CK(cudaGetLastError());
@@ -696,20 +712,32 @@ class Chain : public ChainBase {
     return LL_EUNSUPPORTED;
   }
   int groups_for(int norb) const {
-    const int target = 4 * 152;
+    const int target = 4 * nsm_;
     int g = std::max(1, (target + N_ - 1) / N_);
     return std::min(g, norb);
+  }
+  // Orbital groups of one plane-pass launch (grid N x groups): as many CTAs as fit on the
+  // GPU at once for this mode's occupancy, so that the launch is a single wave.
+  template <typename K>
+  int groups_for_kernel(K kernel, size_t smem, int norb, int& cache) {
+    if (cache == 0) {
+      int occ = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, 128, smem) != cudaSuccess || occ < 1) {
+        cudaGetLastError();
+        occ = 1;
+      }
+      cache = std::max(1, (occ * nsm_) / N_);
+    }
+    return std::max(1, std::min(std::min(cache, ngroups_), norb));
   }
   template <int N, int MODE>
   int xy_nm(const SphereDev& s, int norb, int o_off, int dens_vec, std::string& err) {
     constexpr int B = BO<N, MODE>::v;
-    const int ng = std::min(ngroups_, norb);
     XYArgs a;
     a.s = s;
     a.nbnd = nbnd_;
     a.norb = norb;
     a.cb_ncol = cb_ncol_;
-    a.per_group = (norb + ng - 1) / ng;
     a.o_off = o_off;
     a.dens_vec = dens_vec;
     a.f_ncol = FastDiv((unsigned)cb_ncol_);
@@ -725,6 +753,8 @@ class Chain : public ChainBase {
     if (MODE == XY_PASS1 || MODE == XY_PASS1_DENS) smem += (size_t)N * N * sizeof(T);
     int rc;
     if ((rc = set_smem(k_xy<T, N, B, MODE>, smem, err))) return rc;
+    const int ng = groups_for_kernel(k_xy<T, N, B, MODE>, smem, norb, xy_groups_[MODE]);
+    a.per_group = (norb + ng - 1) / ng;
     k_xy<T, N, B, MODE><<<dim3(N, ng), 128, smem, st_>>>(a, cbuf_, vloc_, vpr_, ur_, nprt_, ur_);
     if (MODE == XY_PASS1_DENS) last_ng_ = ng;
     cudaError_t e = cudaGetLastError();
@@ -870,6 +900,8 @@ class Chain : public ChainBase {
 
   cudaStream_t st_ = nullptr;
   int N_ = 0, nks_ = 0, nbnd_ = 0, nproj_ = 0, approx_ = 0, flavour_ = 0, cap_ = 0, nvec_ = 1, ngroups_ = 1;
+  int nsm_ = 152;           // SMs of the device
+  int xy_groups_[4] = {0, 0, 0, 0};   // plane-pass groups per mode (one wave), 0 = not yet known
   int cb_ncol_ = 0, steps_ = 0, queued_ = 0, spec_cap_ = 0, last_ng_ = 1;
   bool stopped_ = false;
   Profiler prof_;
@@ -885,6 +917,7 @@ class Chain : public ChainBase {
   cplx<T> *nr_ = nullptr, *ng_ = nullptr, *vpr_ = nullptr, *y_ = nullptr, *vecs_ = nullptr;
   cplx<T>* scratch_ = nullptr;
   cplx<double> *spart_ = nullptr, *gamma_ = nullptr, *z_ = nullptr, *zpart_ = nullptr, *spec_out_ = nullptr;
+  ExtrapTail* tail_ = nullptr;   // continuation constants of the coefficients (spectrum)
   bool split_ = false;      // per-k work split over chunks of plane waves (split.cuh)
   int nchunk_ = 1;          // plane-wave chunks per k on the split path
   cplx<double> *sp_s_ = nullptr, *sp_c_ = nullptr, *ub_ = nullptr;   // chunk partials of U^H r, B^H x; U^H B

@@ -863,20 +863,68 @@ __device__ __forceinline__ cplx<double> cdiv(cplx<double> a, cplx<double> b) {
   return mk((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
 }
 
-static __global__ void k_spectrum(int m, const double* __restrict__ beta, const cplx<double>* __restrict__ gamma,
-                           const cplx<double>* __restrict__ z, int nw, const double* __restrict__ w_ha, double eta,
-                           double pref, double vq, cplx<double>* __restrict__ chi, cplx<double>* __restrict__ epsi,
-                           cplx<double>* __restrict__ eps) {
+// Continuation of the coefficients past the m computed ones (Sec. 2.5, Sec. 3.3): for an
+// index i >= m, beta_i = b[i % 2] and gamma_i = g[i % 2] ('constant': b[0] = b[1]); z_i = 0.
+struct ExtrapTail {
+  double b[2];
+  cplx<double> g[2];
+};
+
+// The tail constants: means over the positions max(1, m/2)..m-1, both parities together
+// (kind 1, constant) or each parity apart (kind 2, bi-constant), fixed summation order.
+// One block of 256 threads.
+static __global__ void __launch_bounds__(256) k_extrap_tail(int m, int kind, const double* __restrict__ beta,
+                                                            const cplx<double>* __restrict__ gamma,
+                                                            ExtrapTail* __restrict__ tail) {
+  __shared__ double red[8][6];
+  const int h = m / 2 > 1 ? m / 2 : 1;
+  double s[6] = {0, 0, 0, 0, 0, 0};   // per parity: beta, Re gamma, Im gamma
+  for (int i = h + threadIdx.x; i < m; i += blockDim.x) {
+    const int p = (kind == 2) ? (i & 1) : 0;
+    s[3 * p] += beta[i];
+    s[3 * p + 1] += gamma[i].x;
+    s[3 * p + 2] += gamma[i].y;
+  }
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    const double v = warp_sum(s[c]);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][c] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t[6] = {0, 0, 0, 0, 0, 0};
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+      for (int c = 0; c < 6; ++c) t[c] += red[w][c];
+    int n[2] = {0, 0};
+    for (int i = h; i < m; ++i) ++n[(kind == 2) ? (i & 1) : 0];
+    for (int p = 0; p < 2; ++p) {
+      const int q = (kind == 2) ? p : 0;
+      const double c = n[q] > 0 ? 1.0 / n[q] : 0.0;
+      tail->b[p] = t[3 * q] * c;
+      tail->g[p] = mk(t[3 * q + 1] * c, t[3 * q + 2] * c);
+    }
+  }
+}
+
+// m_total > m continues the chain with `tail` (T grows to m_total x m_total; z stays m long).
+static __global__ void k_spectrum(int m, int m_total, const ExtrapTail* __restrict__ tail,
+                                  const double* __restrict__ beta, const cplx<double>* __restrict__ gamma,
+                                  const cplx<double>* __restrict__ z, int nw, const double* __restrict__ w_ha,
+                                  double eta, double pref, double vq, cplx<double>* __restrict__ chi,
+                                  cplx<double>* __restrict__ epsi, cplx<double>* __restrict__ eps) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nw) return;
+  if (m_total < m || !tail) m_total = m;
   const cplx<double> w = mk(w_ha[i], eta);
-  cplx<double> d = w, r = z[m - 1];
-  for (int j = m - 2; j >= 0; --j) {
-    const cplx<double> bg = cmul(mk(beta[j + 1], 0.0), gamma[j + 1]);
-    const cplx<double> q = cdiv(bg, d);
-    const cplx<double> rr = cdiv(mk(beta[j + 1] * r.x, beta[j + 1] * r.y), d);
+  cplx<double> d = w, r = (m_total > m) ? mk(0.0, 0.0) : z[m - 1];
+  for (int j = m_total - 2; j >= 0; --j) {
+    const int c = j + 1;
+    const double b = c < m ? beta[c] : tail->b[c & 1];
+    const cplx<double> g = c < m ? gamma[c] : tail->g[c & 1];
+    const cplx<double> q = cdiv(cmul(mk(b, 0.0), g), d);
+    const cplx<double> rr = cdiv(mk(b * r.x, b * r.y), d);
     d = w - q;
-    r = z[j] + rr;
+    r = (j < m ? z[j] : mk(0.0, 0.0)) + rr;
   }
   const cplx<double> u1 = cdiv(r, d);
   const cplx<double> c = u1 * (pref * beta[0]);

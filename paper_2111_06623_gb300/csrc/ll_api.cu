@@ -64,19 +64,38 @@ int ll_lanczos(ll_handle* h, int n_steps, double* beta, double* gamma, double* z
   return rc == LL_OK ? LL_OK : fail(rc, "ll_lanczos: " + err);
 }
 
+static bool extrap_args_ok(int m, int kind, int m_total) {
+  if (kind == LL_EXTRAP_NO) return true;
+  if (kind != LL_EXTRAP_CONSTANT && kind != LL_EXTRAP_OSC) return false;
+  if (m_total < m || m_total > LL_EXTRAP_MAX) return false;
+  return m >= (kind == LL_EXTRAP_OSC ? 4 : 2);
+}
+
 int ll_lanczos_spectrum(ll_handle* h, int m, const double* omega_ev, int n_omega, double eta_ev, double* chi,
                         double* eps_inv, double* eps) {
   if (!h || !omega_ev || n_omega < 1) return fail(LL_EINVAL, "bad spectrum arguments");
   std::string err;
-  int rc = h->chain->spectrum(m, omega_ev, n_omega, eta_ev, chi, eps_inv, eps, err);
+  int rc = h->chain->spectrum(m, LL_EXTRAP_NO, 0, omega_ev, n_omega, eta_ev, chi, eps_inv, eps, err);
   return rc == LL_OK ? LL_OK : fail(rc, "ll_lanczos_spectrum: " + err);
 }
 
-int ll_spectrum(const double* beta, const double* gamma, const double* z, int m, double omega_cell, const double* q_cart,
-                const double* omega_ev, int n_omega, double eta_ev, double* chi, double* eps_inv, double* eps,
-                void* stream) {
+int ll_lanczos_spectrum_x(ll_handle* h, int m, int kind, int m_total, const double* omega_ev, int n_omega,
+                          double eta_ev, double* chi, double* eps_inv, double* eps) {
+  if (!h || !omega_ev || n_omega < 1) return fail(LL_EINVAL, "bad spectrum arguments");
+  const int mm = (m <= 0 || m > h->chain->steps()) ? h->chain->steps() : m;
+  if (!extrap_args_ok(mm, kind, m_total)) return fail(LL_EINVAL, "bad extrapolation arguments");
+  std::string err;
+  int rc = h->chain->spectrum(m, kind, m_total, omega_ev, n_omega, eta_ev, chi, eps_inv, eps, err);
+  return rc == LL_OK ? LL_OK : fail(rc, "ll_lanczos_spectrum_x: " + err);
+}
+
+static int spectrum_impl(const double* beta, const double* gamma, const double* z, int m, int kind, int m_total,
+                         double omega_cell, const double* q_cart, const double* omega_ev, int n_omega, double eta_ev,
+                         double* chi, double* eps_inv, double* eps, void* stream) {
   if (!beta || !gamma || !z || m < 1 || !q_cart || !omega_ev || n_omega < 1 || !(omega_cell > 0))
     return fail(LL_EINVAL, "bad spectrum arguments");
+  if (!extrap_args_ok(m, kind, m_total)) return fail(LL_EINVAL, "bad extrapolation arguments");
+  if (kind == LL_EXTRAP_NO) m_total = m;
   const double q2 = q_cart[0] * q_cart[0] + q_cart[1] * q_cart[1] + q_cart[2] * q_cart[2];
   if (!(q2 > 0)) return fail(LL_EINVAL, "Q = 0");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -85,10 +104,12 @@ int ll_spectrum(const double* beta, const double* gamma, const double* z, int m,
   for (int i = 0; i < n_omega; ++i) w[i] = omega_ev[i] / ha;
   double *db = nullptr, *dw = nullptr;
   ll::cplx<double> *dg = nullptr, *dz = nullptr, *dout = nullptr;
-  auto cleanup = [&]() { cudaFree(db); cudaFree(dw); cudaFree(dg); cudaFree(dz); cudaFree(dout); };
+  ll::ExtrapTail* dt = nullptr;
+  auto cleanup = [&]() { cudaFree(db); cudaFree(dw); cudaFree(dg); cudaFree(dz); cudaFree(dout); cudaFree(dt); };
   if (cudaMalloc(&db, m * sizeof(double)) != cudaSuccess || cudaMalloc(&dg, m * sizeof(ll::cplx<double>)) != cudaSuccess ||
       cudaMalloc(&dz, m * sizeof(ll::cplx<double>)) != cudaSuccess || cudaMalloc(&dw, n_omega * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&dout, 3L * n_omega * sizeof(ll::cplx<double>)) != cudaSuccess) {
+      cudaMalloc(&dout, 3L * n_omega * sizeof(ll::cplx<double>)) != cudaSuccess ||
+      cudaMalloc(&dt, sizeof(ll::ExtrapTail)) != cudaSuccess) {
     cleanup();
     return fail(LL_ENOMEM, "ll_spectrum: device allocation");
   }
@@ -96,7 +117,9 @@ int ll_spectrum(const double* beta, const double* gamma, const double* z, int m,
   cudaMemcpyAsync(dg, gamma, m * sizeof(ll::cplx<double>), cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(dz, z, m * sizeof(ll::cplx<double>), cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(dw, w.data(), n_omega * sizeof(double), cudaMemcpyHostToDevice, st);
-  ll::k_spectrum<<<(n_omega + 127) / 128, 128, 0, st>>>(m, db, dg, dz, n_omega, dw, eta_ev / ha, 4.0 / omega_cell,
+  if (m_total > m) ll::k_extrap_tail<<<1, 256, 0, st>>>(m, kind, db, dg, dt);
+  ll::k_spectrum<<<(n_omega + 127) / 128, 128, 0, st>>>(m, m_total, m_total > m ? dt : nullptr, db, dg, dz, n_omega,
+                                                         dw, eta_ev / ha, 4.0 / omega_cell,
                                                          4.0 * 3.14159265358979323846 / q2, dout, dout + n_omega,
                                                          dout + 2L * n_omega);
   cudaError_t e = cudaGetLastError();
@@ -109,6 +132,20 @@ int ll_spectrum(const double* beta, const double* gamma, const double* z, int m,
   cleanup();
   if (e != cudaSuccess) return fail(LL_ECUDA, std::string("ll_spectrum: ") + cudaGetErrorString(e));
   return LL_OK;
+}
+
+int ll_spectrum(const double* beta, const double* gamma, const double* z, int m, double omega_cell, const double* q_cart,
+                const double* omega_ev, int n_omega, double eta_ev, double* chi, double* eps_inv, double* eps,
+                void* stream) {
+  return spectrum_impl(beta, gamma, z, m, LL_EXTRAP_NO, m, omega_cell, q_cart, omega_ev, n_omega, eta_ev, chi, eps_inv,
+                       eps, stream);
+}
+
+int ll_spectrum_x(const double* beta, const double* gamma, const double* z, int m, int kind, int m_total,
+                  double omega_cell, const double* q_cart, const double* omega_ev, int n_omega, double eta_ev,
+                  double* chi, double* eps_inv, double* eps, void* stream) {
+  return spectrum_impl(beta, gamma, z, m, kind, m_total, omega_cell, q_cart, omega_ev, n_omega, eta_ev, chi, eps_inv,
+                       eps, stream);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -187,7 +224,7 @@ int ll_spectrum_static(const double* beta, const double* gamma, const double* z,
   if (e == cudaSuccess) e = cudaMemcpyAsync(dw, omega_ev, n_omega * sizeof(double), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) {
     k_ev_to_ha<<<(n_omega + 127) / 128, 128, 0, st>>>(n_omega, dw);
-    ll::k_spectrum<<<(n_omega + 127) / 128, 128, 0, st>>>(m, db, dg, dz, n_omega, dw, eta_ev / 27.211386245988,
+    ll::k_spectrum<<<(n_omega + 127) / 128, 128, 0, st>>>(m, m, nullptr, db, dg, dz, n_omega, dw, eta_ev / 27.211386245988,
                                                            4.0 / omega_cell, 4.0 * 3.14159265358979323846 / q2, dout,
                                                            dout + kStaticMaxOmega, dout + 2L * kStaticMaxOmega);
     e = cudaGetLastError();

@@ -133,7 +133,7 @@ void complete_job(ll_server* s, Job* j, int lanczos_rc, const std::string& lerr)
       j->chi.resize(2 * (size_t)nw);
       j->eps_inv.resize(2 * (size_t)nw);
       j->eps.resize(2 * (size_t)nw);
-      const int rc = j->chain->spectrum(m, j->omega.data(), nw, j->eta, j->chi.data(), j->eps_inv.data(),
+      const int rc = j->chain->spectrum(m, LL_EXTRAP_NO, 0, j->omega.data(), nw, j->eta, j->chi.data(), j->eps_inv.data(),
                                         j->eps.data(), err);
       if (rc != LL_OK && lanczos_rc == LL_OK) {
         finish(s, j, rc, "spectrum: " + err);

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libll.so")
 
 LL_OK, LL_EINVAL, LL_ENOMEM, LL_EBREAKDOWN, LL_ENOTPD, LL_ETIMEOUT, LL_ECUDA = 0, 1, 2, 3, 4, 5, 6
 LL_PENDING, LL_ENOTFOUND, LL_EUNSUPPORTED = 7, 8, 9
+LL_EXTRAP_NO, LL_EXTRAP_CONSTANT, LL_EXTRAP_OSC = 0, 1, 2
 APPROX = {"ipa": 0, "rpa": 1, "tddft": 2}
 FLAVOUR = {"ph": 0, "nh": 1}
 PRECISION = {"fp64": 0, "fp32": 1}
@@ -54,6 +55,9 @@ def _load():
         "ll_spectrum": (C.c_int, [_dp, _dp, _dp, C.c_int, C.c_double, _dp, _dp, C.c_int, C.c_double, _dp, _dp, _dp, vp]),
         "ll_spectrum_static": (C.c_int, [_dp, _dp, _dp, C.c_int, C.c_double, _dp, _dp, C.c_int, C.c_double, _dp,
                                          _dp, _dp, vp]),
+        "ll_lanczos_spectrum_x": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, _dp, C.c_int, C.c_double, _dp, _dp, _dp]),
+        "ll_spectrum_x": (C.c_int, [_dp, _dp, _dp, C.c_int, C.c_int, C.c_int, C.c_double, _dp, _dp, C.c_int,
+                                    C.c_double, _dp, _dp, _dp, vp]),
         "ll_apply": (C.c_int, [vp, C.c_int, _dp, _dp]),
         "ll_get_map": (C.c_int, [vp, _ip]),
         "ll_get_start": (C.c_int, [vp, _dp]),
@@ -79,6 +83,7 @@ def _load():
 
 _lib = _load()
 EXPORTS = ("ll_create", "ll_destroy", "ll_lanczos", "ll_lanczos_spectrum", "ll_spectrum", "ll_spectrum_static",
+           "ll_lanczos_spectrum_x", "ll_spectrum_x",
            "ll_apply", "ll_get_map", "ll_get_start", "ll_footprint", "ll_profile", "ll_profile_read", "ll_last_error",
            "ll_version", "ll_server_create",
            "ll_server_set_chunk", "ll_submit", "ll_poll", "ll_server_stats", "ll_server_last_error",
@@ -186,11 +191,17 @@ class Chain:
             raise err
         return beta[: done.value].copy(), gamma[: done.value].copy(), z[: done.value].copy()
 
-    def spectrum(self, omega_ev, eta_ev: float, m: int = 0):
+    def spectrum(self, omega_ev, eta_ev: float, m: int = 0, extrapolation: str = "no", m_total: int = 0):
+        """chi, eps^-1, eps from the chain's first m coefficients (0: all), optionally
+        extrapolated ('constant' or 'osc') to m_total (ll_lanczos_spectrum[_x])."""
         w = np.ascontiguousarray(omega_ev, dtype=np.float64)
         out = [np.zeros(len(w), dtype=np.complex128) for _ in range(3)]
-        _check(_lib.ll_lanczos_spectrum(self._h, int(m), _d(w), len(w), float(eta_ev),
-                                        *[_d(o.view(np.float64)) for o in out]))
+        if extrapolation == "no":
+            _check(_lib.ll_lanczos_spectrum(self._h, int(m), _d(w), len(w), float(eta_ev),
+                                            *[_d(o.view(np.float64)) for o in out]))
+        else:
+            _check(_lib.ll_lanczos_spectrum_x(self._h, int(m), EXTRAP[extrapolation], int(m_total), _d(w), len(w),
+                                              float(eta_ev), *[_d(o.view(np.float64)) for o in out]))
         return tuple(out)
 
     def _split(self, flat):
@@ -237,17 +248,27 @@ class Chain:
         return int(b.value)
 
 
-def spectrum(beta, gamma, z, omega_cell, q_cart, omega_ev, eta_ev, stream=None):
-    """chi, eps^-1, eps from caller-held coefficients (ll_spectrum)."""
+EXTRAP = {"no": LL_EXTRAP_NO, "constant": LL_EXTRAP_CONSTANT, "osc": LL_EXTRAP_OSC}
+
+
+def spectrum(beta, gamma, z, omega_cell, q_cart, omega_ev, eta_ev, stream=None, extrapolation: str = "no",
+             m_total: int = 0):
+    """chi, eps^-1, eps from caller-held coefficients (ll_spectrum), optionally extrapolated
+    ('constant' or 'osc') to m_total coefficients (ll_spectrum_x)."""
     b = np.ascontiguousarray(beta, dtype=np.float64)
     g = np.ascontiguousarray(gamma, dtype=np.complex128)
     zz = np.ascontiguousarray(z, dtype=np.complex128)
     q = np.ascontiguousarray(q_cart, dtype=np.float64)
     w = np.ascontiguousarray(omega_ev, dtype=np.float64)
     out = [np.zeros(len(w), dtype=np.complex128) for _ in range(3)]
-    _check(_lib.ll_spectrum(_d(b), _d(g.view(np.float64)), _d(zz.view(np.float64)), len(b), float(omega_cell),
-                            _d(q), _d(w), len(w), float(eta_ev), *[_d(o.view(np.float64)) for o in out],
-                            C.c_void_p(stream) if stream else None))
+    st = C.c_void_p(stream) if stream else None
+    if extrapolation == "no":
+        _check(_lib.ll_spectrum(_d(b), _d(g.view(np.float64)), _d(zz.view(np.float64)), len(b), float(omega_cell),
+                                _d(q), _d(w), len(w), float(eta_ev), *[_d(o.view(np.float64)) for o in out], st))
+    else:
+        _check(_lib.ll_spectrum_x(_d(b), _d(g.view(np.float64)), _d(zz.view(np.float64)), len(b),
+                                  EXTRAP[extrapolation], int(m_total), float(omega_cell), _d(q), _d(w), len(w),
+                                  float(eta_ev), *[_d(o.view(np.float64)) for o in out], st))
     return tuple(out)
 
 

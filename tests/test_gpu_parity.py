@@ -263,3 +263,25 @@ def test_cubic8_non_hermitian_unsupported(lib, cubic8):
     with pytest.raises(lib.LLError) as e:
         chain_from_bundle(cubic8, flavour="nh", max_steps=4)
     assert e.value.code == lib.LL_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("kind", ["constant", "osc"])
+def test_extrapolated_spectrum(lib, small, kind):
+    """Coefficients continued to 5000 (Sec. 3.3) on the device, from caller-held coefficients
+    (ll_spectrum_x) and from the chain's own (ll_lanczos_spectrum_x), against the oracle's
+    extrapolation and LAPACK solve on the same coefficients."""
+    from oracle.extrapolation import extrapolate
+    sys = System(small)
+    ref = lanczos.pseudo_hermitian(sys, 200)
+    s = small.spec
+    eb, eg, ez = extrapolate(ref.beta, ref.gamma, ref.z, kind, 5000)
+    rchi, _, _ = spectrum.spectrum(eb, eg, ez, s.omega, s.q_cart, WGRID, ETA)
+    chi, _, _ = lib.spectrum(ref.beta, ref.gamma, ref.z, s.omega, s.q_cart, WGRID, ETA, extrapolation=kind,
+                             m_total=5000)
+    assert np.max(np.abs(chi - rchi)) / np.max(np.abs(rchi)) < 1e-10
+    ch = chain_from_bundle(small, max_steps=200)
+    got = ch.lanczos(200)
+    chi2, _, _ = ch.spectrum(WGRID, ETA, extrapolation=kind, m_total=5000)
+    gb, gg, gz = extrapolate(got[0], got[1], got[2], kind, 5000)
+    rchi2, _, _ = spectrum.spectrum(gb, gg, gz, s.omega, s.q_cart, WGRID, ETA)
+    assert np.max(np.abs(chi2 - rchi2)) / np.max(np.abs(rchi2)) < 1e-10

@@ -76,3 +76,17 @@ def test_rejects_sphere_too_large_for_grid(ll):
     with pytest.raises(ll.LLError) as e:
         ll.Chain(**args)
     assert e.value.code == ll.LL_EINVAL
+
+
+def test_rejects_bad_extrapolation(ll):
+    """Argument checks of ll_spectrum_x run on the host before any device work."""
+    b = np.ones(10)
+    g = np.ones(10, dtype=complex)
+    w = np.linspace(0, 10, 5)
+    for kind, m_total, beta in (("osc", 100, b[:3]), ("constant", 5, b), ("constant", 100, b[:1])):
+        with pytest.raises(ll.LLError) as e:
+            ll.spectrum(beta, g[:len(beta)], g[:len(beta)], 270.0, [0.06, 0, 0], w, 0.1,
+                        extrapolation=kind, m_total=m_total)
+        assert e.value.code == ll.LL_EINVAL
+    with pytest.raises(KeyError):
+        ll.spectrum(b, g, g, 270.0, [0.06, 0, 0], w, 0.1, extrapolation="linear", m_total=100)
