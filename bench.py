@@ -60,12 +60,12 @@ def _bundle():
     return w.get_bundle(w.config_kb())
 
 
-def _chain(b, precision, max_steps, stream):
+def _chain(b, precision, max_steps, stream, flavour="ph"):
     from paper_2111_06623_gb300 import ll
     s = b.spec
     return ll.Chain(lattice=s.lattice, nfft=s.nfft, kcart=b.kcart, miller_k=b.miller_k, miller_kq=b.miller_kq,
                     u_k=b.u_k, u_kq=b.u_kq, eps_k=b.eps_k, vloc_r=b.vloc_r, rho_r=b.rho_r, beta_kq=b.beta_kq,
-                    dij=b.dij, q_cart=s.q_cart, approx="tddft", flavour="ph", precision=precision,
+                    dij=b.dij, q_cart=s.q_cart, approx="tddft", flavour=flavour, precision=precision,
                     max_steps=max_steps, stream=stream)
 
 
@@ -135,6 +135,22 @@ def _xy_flops_per_apply(b, with_k: bool) -> float:
     return tot
 
 
+def _small_cell(stream):
+    import torch
+    import workloads as w
+    bs = w.get_bundle(w.config_small())
+    ch, _, ms, _ = _time_chain(bs, "fp64", 300, 5, stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    ch.spectrum(np.linspace(0.0, 40.0, 4001), 0.1)
+    e1.record()
+    torch.cuda.synchronize()
+    ch.close()
+    return {"workload": "fcc2_10ry_18: 2-atom FCC, 10 Ry, 18^3, 4x4x4 k, 4 bands, RPA+ALDA, PH, FP64",
+            "steps": 300, "steps_per_s": 300 / (ms / 1e3), "ms_per_step": ms / 300,
+            "spectrum_ms": e0.elapsed_time(e1), "dtype": "f64"}
+
+
 def source_digest() -> str:
     """sha256 of the CUDA sources and the C header: names the code a profile was taken on."""
     import hashlib
@@ -167,9 +183,9 @@ def profiled_traffic():
         return None
 
 
-def _time_chain(b, precision, steps, warmup, stream, profile=False):
+def _time_chain(b, precision, steps, warmup, stream, profile=False, flavour="ph"):
     import torch
-    ch = _chain(b, precision, warmup + steps + 64, stream)
+    ch = _chain(b, precision, warmup + steps + 64, stream, flavour)
     ch.lanczos(warmup)
     torch.cuda.synchronize()
     if profile:
@@ -414,6 +430,13 @@ def main():
     clocks = clk.summary()
     # FP64 path on the same number of steps
     ch64, c64, ms64, _ = _time_chain(b, "fp64", K, W, stream)
+    # the non-Hermitian recursion (two applications per step), FP32, same steps
+    chnh, _, msnh, _ = _time_chain(b, "fp32", K, W, stream, flavour="nh")
+    chnh.close()
+    nh = {"value": world * K / (msnh / 1e3), "ms_per_step": msnh / K, "applies_per_step": 2, "dtype": "f32"}
+    # the small two-atom cell (10 Ry, 18^3, 4^3 k, 256 orbitals): 300 FP64 pseudo-Hermitian
+    # steps and the spectrum, on the device
+    small = _small_cell(stream)
     m = min(SPEC_WINDOW, len(c32[0]), len(c64[0]))
     l32, l64 = _loss(c32, b, m), _loss(c64, b, m)
     spec_err = float(np.max(np.abs(l32 - l64)) / np.max(np.abs(l64)))
@@ -490,6 +513,7 @@ def main():
             "config": {"workload": WORKLOAD, "orbitals": int(b.nks * b.spec.nbnd), "npw_avg": float(np.mean(b.npw_kq)),
                        "l2": "per-step working set ~0.6 GB > 129 MB L2 (no flush)", "parallelism": "replicas"},
             "fp64": {"value": world * K / (ms64 / 1e3), "ms_per_step": ms64 / K, "dtype": "f64"},
+            "nh_fp32": nh, "small_cell": small,
             "speedup_fp32_vs_fp64": ms64 / ms32,
             "spectrum_err_fp32_vs_fp64": spec_err, "spectrum_window_steps": m,
             "spectrum_err_fp32_vs_fp64_all_steps": spec_err_full,

@@ -191,7 +191,7 @@ static inline void recip(const double a[3][3], double b[3][3]) {
 // orbital-grid planes are staged (their shared memory is the limit), three rounds otherwise
 // so that the axis-2 passes (a sphere's rows, ~N/3 lines per orbital) also fill the block.
 template <int N, int MODE> struct BO {
-  static constexpr int v = MODE == XY_PASS1_DENS ? (128 / N < 1 ? 1 : 128 / N) : (MODE == XY_PASS2 ? 256 / N : 384 / N);
+  static constexpr int v = (MODE == XY_PASS1_DENS || MODE == XY_PASS2) ? 256 / N : 384 / N;
 };
 
 template <typename T>
@@ -748,7 +748,7 @@ class Chain : public ChainBase {
     const int NP = N + 1;
     size_t smem = (size_t)B * cb_ncol_ + (size_t)B * s.nrow_max * NP;
     if (MODE == XY_PASS2) smem += (size_t)N * N;
-    if (MODE == XY_PASS1_DENS) smem += (size_t)(B + 1) * N * N + 1;   // + alignment of the u planes
+    if (MODE == XY_PASS1_DENS) smem += (size_t)(128 / N) * N * N;   // per-slot density planes
     smem *= sizeof(cplx<T>);
     if (MODE == XY_PASS1 || MODE == XY_PASS1_DENS) smem += (size_t)N * N * sizeof(T);
     int rc;

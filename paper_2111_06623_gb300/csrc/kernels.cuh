@@ -59,32 +59,24 @@ __global__ void __launch_bounds__(128) k_zinv(SphereDev s, const cplx<T>* __rest
 }
 
 // ---------------------------------------------------------------------------------------
-// Asynchronous 16-byte global -> shared copies (cp.async, L2 only), their commit and wait.
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
-
-// ---------------------------------------------------------------------------------------
 // Per-plane pass of one operator application.  grid (N planes, groups), block 128.
 // The sphere's columns are ordered by (m2, m1) and grouped in rows of equal m2 (consecutive
 // m1).  For every orbital of the group (BO at a time), at plane j3 = blockIdx.x:
 //   rows     1D FFT along axis 1 (m1 <-> j1) of every sphere row, between the column buffer
 //            Cs and the row buffer Ys[row][j1];
 //   lines    one thread per (orbital, j1): 1D FFT along axis 2 (m2 <-> j2) of the line
-//            x(j2, j1), j2 = 0..N-1, held in registers.  Consecutive threads take consecutive
-//            j1, so every real-space plane (V, v', u, the density) is read and written with
-//            unit stride across a warp straight from HBM: no staging copies.
+//            x(j2, j1), j2 = 0..N-1, held in registers.  Thread t = s N + j1 (s < S = 128/N)
+//            always takes column j1, for the batch's orbitals b = s, s + S, ...; consecutive
+//            threads take consecutive j1, so every real-space plane (V, v', u, the density)
+//            is read and written with unit stride across a warp straight from HBM.
 // Modes:
 //   XY_PASS1       inverse 2D FFT of the plane's columns, t(r) = V(r) x(r), forward 2D FFT
 //                  back to the columns (in place);
 //   XY_PASS1_DENS  the same plus the response-density partial sum_o conj(u_o(r)) x_o(r) of the
-//                  orbitals of vector dens_vec, written per (group, plane) to nprt (orbitals
-//                  summed in a fixed order).  The batch's u planes are copied into the product
-//                  planes Pb with cp.async while the rows are transformed, and each line
-//                  replaces its u values there by conj(u) x;
+//                  orbitals of vector dens_vec, written per (group, plane) to nprt.  Each
+//                  thread adds its lines' products into its own column of its slot's plane
+//                  Pb[s] (no other thread touches it: no barrier, a fixed order); the S slots
+//                  are summed in order once, at the end;
 //   XY_PASS2       t(r) = v'(r) u(r) from the orbital grid, forward 2D FFT, added into the
 //                  columns (linearity: one axis-3 transform serves both passes);
 //   XY_STORE       inverse 2D FFT only, x(r) stored to grid_out (orbital grids at set-up).
@@ -113,13 +105,12 @@ __global__ void __launch_bounds__(128, MODE == XY_PASS1_DENS ? 3 : 4) k_xy(XYArg
   const SphereDev& s = a.s;
   cplx<T>* Cs = reinterpret_cast<cplx<T>*>(smem_raw);                 // [BO][cb_ncol]
   cplx<T>* Ys = Cs + BO * a.cb_ncol;                                    // [BO][nrow_max][NP]
+  constexpr int S = 128 / N;                                           // line slots
   cplx<T>* Pl = Ys + BO * s.nrow_max * NP;                              // [N][N] v' (pass 2)
-  // [BO][N][N] u, then conj(u) x; 16-byte aligned for the cp.async copies
-  cplx<T>* Pb = Pl + (MODE == XY_PASS2 ? NN : 0);
-  Pb += (16 - (reinterpret_cast<size_t>(Pb) & 15)) % 16 / sizeof(cplx<T>);
-  cplx<T>* Dacc = Pb + (MODE == XY_PASS1_DENS ? BO * NN : 0);           // [N][N] density
-  T* Pv = reinterpret_cast<T*>(Dacc + (MODE == XY_PASS1_DENS ? NN : 0));  // [N][N] V (real)
+  cplx<T>* Pb = Pl + (MODE == XY_PASS2 ? NN : 0);                       // [S][N][N] density
+  T* Pv = reinterpret_cast<T*>(Pb + (MODE == XY_PASS1_DENS ? S * NN : 0));  // [N][N] V (real)
   const long plane = (long)NN;
+  const int ls = threadIdx.x / N, lj1 = threadIdx.x - ls * N;           // line slot, column
 
   if (MODE == XY_PASS1 || MODE == XY_PASS1_DENS) {
     for (int i = threadIdx.x; i < NN; i += blockDim.x) Pv[i] = vloc[iz * plane + i];
@@ -127,23 +118,13 @@ __global__ void __launch_bounds__(128, MODE == XY_PASS1_DENS ? 3 : 4) k_xy(XYArg
     for (int i = threadIdx.x; i < NN; i += blockDim.x) Pl[i] = vpr[iz * plane + i];
   }
   if (MODE == XY_PASS1_DENS)
-    for (int i = threadIdx.x; i < NN; i += blockDim.x) Dacc[i] = czero<T>();
+    for (int i = threadIdx.x; i < S * NN; i += blockDim.x) Pb[i] = czero<T>();
 
   const int o_begin = a.o_off + g * a.per_group;
   const int o_end = a.o_off + min(a.norb, g * a.per_group + a.per_group);
   for (int ob = o_begin; ob < o_end; ob += BO) {
     const int nb = min(BO, o_end - ob);
     __syncthreads();
-    if (MODE == XY_PASS1_DENS) {  // u planes of the batch's density orbitals -> Pb
-      constexpr int E = 16 / (int)sizeof(cplx<T>);   // complex values per 16-byte copy
-      for (int e = threadIdx.x; e < nb * (NN / E); e += blockDim.x) {
-        const int b = e / (NN / E), q = (e - b * (NN / E)) * E;
-        const int o = ob + b;
-        if (a.f_pervec.div(o) == a.dens_vec)
-          cp_async16(Pb + b * NN + q, ur + (long)a.f_pervec.mod(o) * N * plane + iz * plane + q);
-      }
-      cp_async_commit();
-    }
     if (MODE != XY_PASS2) {
       for (int i = threadIdx.x; i < nb * a.cb_ncol; i += blockDim.x) {
         const int b = a.f_ncol.div(i), c = i - b * a.cb_ncol;
@@ -169,12 +150,12 @@ __global__ void __launch_bounds__(128, MODE == XY_PASS1_DENS ? 3 : 4) k_xy(XYArg
 #pragma unroll
         for (int p = 0; p < N; ++p) ys[p] = l[p];
       }
-      if (MODE == XY_PASS1_DENS) cp_async_wait_all();
       __syncthreads();
     }
     // axis 2: one line per (orbital, j1), element p of the line at grid point (j2 = p, j1)
-    for (int i = threadIdx.x; i < nb * N; i += blockDim.x) {
-      const int b = i / N, j1 = i - b * N;
+#pragma unroll 1
+    for (int b = ls; ls < S && b < nb; b += S) {
+      const int j1 = lj1;
       const int o = ob + b, k = a.f_nks.mod(a.f_nbnd.div(o));
       const int nr = s.nrow[k];
       const int m2min = s.row[k * s.nrow_max].x;
@@ -196,16 +177,12 @@ __global__ void __launch_bounds__(128, MODE == XY_PASS1_DENS ? 3 : 4) k_xy(XYArg
           for (int p = 0; p < N; ++p) dst[p * N] = l[p];
           continue;
         }
-        if (MODE == XY_PASS1_DENS) {
-          // conj(u) x of this line, summed over the batch's orbitals after the barrier
-          cplx<T>* pb = Pb + b * NN + j1;
-          if (a.f_pervec.div(o) == a.dens_vec) {
+        if (MODE == XY_PASS1_DENS && a.f_pervec.div(o) == a.dens_vec) {
+          // conj(u) x of this line into this thread's own column of its slot
+          const cplx<T>* u = ur + (long)a.f_pervec.mod(o) * N * plane + iz * plane + j1;
+          cplx<T>* pb = Pb + ls * NN + j1;
 #pragma unroll
-            for (int p = 0; p < N; ++p) pb[p * N] = cjmul(pb[p * N], l[p]);
-          } else {
-#pragma unroll
-            for (int p = 0; p < N; ++p) pb[p * N] = czero<T>();
-          }
+          for (int p = 0; p < N; ++p) pb[p * N] = pb[p * N] + cjmul(u[p * N], l[p]);
         }
 #pragma unroll
         for (int p = 0; p < N; ++p) l[p] = l[p] * Pv[p * N + j1];
@@ -219,13 +196,6 @@ __global__ void __launch_bounds__(128, MODE == XY_PASS1_DENS ? 3 : 4) k_xy(XYArg
     }
     __syncthreads();
     if (MODE == XY_STORE) continue;
-    if (MODE == XY_PASS1_DENS) {  // density of the batch, orbitals summed in a fixed order
-      for (int i = threadIdx.x; i < NN; i += blockDim.x) {
-        cplx<T> acc = Dacc[i];
-        for (int b = 0; b < nb; ++b) acc = acc + Pb[b * NN + i];
-        Dacc[i] = acc;
-      }
-    }
     // forward FFT along axis 1 of every row, keep the row's columns
     for (int i = threadIdx.x; i < nb * s.nrow_max; i += blockDim.x) {
       const int b = a.f_nrow.div(i), r = i - b * s.nrow_max;
@@ -253,9 +223,13 @@ __global__ void __launch_bounds__(128, MODE == XY_PASS1_DENS ? 3 : 4) k_xy(XYArg
       *dst = (MODE == XY_PASS2) ? *dst + Cs[i] : Cs[i];
     }
   }
-  if (MODE == XY_PASS1_DENS) {
+  if (MODE == XY_PASS1_DENS) {  // the slots summed in order
     __syncthreads();
-    for (int i = threadIdx.x; i < NN; i += blockDim.x) nprt[(long)g * N * plane + iz * plane + i] = Dacc[i];
+    for (int i = threadIdx.x; i < NN; i += blockDim.x) {
+      cplx<T> acc = Pb[i];
+      for (int q = 1; q < S; ++q) acc = acc + Pb[q * NN + i];
+      nprt[(long)g * N * plane + iz * plane + i] = acc;
+    }
   }
 }
 
