@@ -151,6 +151,25 @@ def _small_cell(stream):
             "spectrum_ms": e0.elapsed_time(e1), "dtype": "f64"}
 
 
+def _step_flops(b) -> tuple[float, float]:
+    """FFT flops of one pseudo-Hermitian step (the mean of a D+K and a D application):
+    (nominal, pruned).  Nominal: 5 N^3 log2 N^3 per full 3D FFT, 2P + 2 FFTs for D+K and 2P
+    for D (P orbitals).  Pruned (what the kernels compute): per orbital, the sphere's
+    columns along axis 3 both ways, the per-plane passes of _xy_flops_per_apply, pass 2's
+    (N + rows) forward lines per plane, and two full FFTs of the response density."""
+    n = b.spec.nfft
+    nb = b.spec.nbnd
+    p = b.nks * nb
+    full = 5.0 * n ** 3 * np.log2(n ** 3)
+    nominal = 0.5 * ((2 * p + 2) + 2 * p) * full
+    line = 5.0 * n * np.log2(n)
+    axis3 = sum(nb * 2 * len({(a, c) for a, c in m[:, :2].tolist()}) * line for m in b.miller_kq)
+    pass2 = sum(nb * n * ((n + len(np.unique(m[:, 1]))) * line + 6 * n * n) for m in b.miller_kq)
+    dk = _xy_flops_per_apply(b, True) + pass2 + axis3 + 2 * full
+    d = _xy_flops_per_apply(b, False) + axis3
+    return nominal, 0.5 * (dk + d)
+
+
 def source_digest() -> str:
     """sha256 of the CUDA sources and the C header: names the code a profile was taken on."""
     import hashlib
@@ -227,32 +246,26 @@ def _oracle_sample(b, nk_sample: int, nsteps: int):
 
 
 def _serving(b_kb, n_jobs: int, seed: int = 7):
-    """A Poisson stream (mean 20 jobs/s) of Lanczos jobs through the request loop: the small
-    two-atom workload at four momentum transfers and the KB workload, 500-1500 pseudo-Hermitian
-    FP32 steps each, admission under a 150 GB HBM budget.  Returns throughput and the p50/p99
-    time from submission to the finished spectrum."""
-    import workloads as w
+    """A Poisson stream (mean 20 jobs/s, arrivals from default_rng(seed)) of Lanczos jobs
+    through the request loop under a 150 GB HBM budget: each job picks a cell uniformly (the
+    two-atom cell at one of four q of the many-Q pool, the KB workload, the eight-atom cell at
+    one of two q of the pool) and U[500, 3000] pseudo-Hermitian FP32 steps.  Returns
+    throughput and the p50/p99 time from submission to the finished spectrum."""
     from paper_2111_06623_gb300 import ll
+    pools = _batch_bundles(4, 2)
+    cells = [pools["fcc2_10ry_18"], [b_kb], pools["cubic8_20ry_32"]]
     rng = np.random.default_rng(seed)
-    pool = []
-    qr = np.random.default_rng(5)
-    for _ in range(4):
-        spec = w.config_small()
-        d = qr.normal(size=3)
-        spec.q_cart = qr.uniform(0.05, 0.3) * (2 * np.pi / w.A_LAT) * d / np.linalg.norm(d)
-        spec.name = "fcc2_10ry_18_q%03d" % int(1000 * np.linalg.norm(spec.q_cart))
-        pool.append(w.get_bundle(spec))
-    pool.append(b_kb)
     wgrid = np.linspace(0.0, 40.0, 4001)
     srv = ll.Server(hbm_budget_bytes=150 << 30, max_slots=16, chunk=32)
     t_arr = np.cumsum(rng.exponential(1.0 / 20.0, size=n_jobs))
-    picks = rng.integers(0, len(pool), size=n_jobs)
-    steps = rng.integers(500, 1501, size=n_jobs)
+    picks = rng.integers(0, len(cells), size=n_jobs)
+    steps = rng.integers(500, 3001, size=n_jobs)
+    which = rng.integers(0, 1 << 30, size=n_jobs)
     ids, t0 = [], time.perf_counter()
-    for ta, pk, ns in zip(t_arr, picks, steps):
+    for ta, pk, ns, wq in zip(t_arr, picks, steps, which):
         while time.perf_counter() - t0 < ta:
             time.sleep(0.001)
-        bb = pool[pk]
+        bb = cells[pk][wq % len(cells[pk])]
         s = bb.spec
         ids.append(srv.submit(int(ns), wgrid, 0.1, lattice=s.lattice, nfft=s.nfft, kcart=bb.kcart,
                               miller_k=bb.miller_k, miller_kq=bb.miller_kq, u_k=bb.u_k, u_kq=bb.u_kq, eps_k=bb.eps_k,
@@ -274,7 +287,8 @@ def _serving(b_kb, n_jobs: int, seed: int = 7):
     return {"jobs": n_jobs, "steps_per_s": done / wall, "p50_s": float(np.percentile(v, 50)),
             "p99_s": float(np.percentile(v, 99)), "wall_s": wall, "peak_hbm_gb": peak / 2 ** 30,
             "budget_gb": 150, "slots": 16,
-            "stream": "Poisson 20 jobs/s (seed 7), small cell at 4 Q + KB workload, 500-1500 FP32 PH steps"}
+            "stream": ("Poisson 20 jobs/s (seed 7); cell U{2-atom at 4 q, KB workload, 8-atom at 2 q}; "
+                       "U[500, 3000] FP32 PH steps")}
 
 
 def q_pool(n: int = 64) -> np.ndarray:
@@ -393,7 +407,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--serving-jobs", type=int, default=16)
+    ap.add_argument("--serving-jobs", type=int, default=32)
     ap.add_argument("--batch-small", type=int, default=16, help="chains of the two-atom cell in the many-Q batch")
     ap.add_argument("--batch-cubic", type=int, default=2, help="chains of the eight-atom cell in the many-Q batch")
     args = ap.parse_args()
@@ -492,6 +506,12 @@ def main():
         roofline = {"bound": "alu", "kernel": dom, "achieved": None, "peak": peak, "unit": "TFLOP/s",
                     "frac": None, "traffic": None}
 
+    nom, pru = _step_flops(b)
+    step_roofline = {"fft_gflop_per_step_nominal": nom / 1e9, "fft_gflop_per_step_pruned": pru / 1e9,
+                     "achieved_tflops_nominal": nom * value / world / 1e12,
+                     "achieved_tflops_pruned": pru * value / world / 1e12,
+                     "frac_nominal": nom * value / world / 1e12 / peak, "frac_pruned": pru * value / world / 1e12 / peak,
+                     "peak_tflops": peak, "bound": "alu"}
     serving = _serving(b, args.serving_jobs) if args.serving_jobs > 0 else None
     batch = _batch(args.batch_small, args.batch_cubic) if args.batch_small + args.batch_cubic > 0 else None
 
@@ -519,7 +539,7 @@ def main():
             "spectrum_err_fp32_vs_fp64_all_steps": spec_err_full,
             "step_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))} if lat else None,
             "kernel_ms": ms_cls, "kernel_launches": launches,
-            "roofline": roofline, "serving": serving, "batch": batch, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(total), "clocks": clocks,
+            "roofline": roofline, "step_roofline": step_roofline, "serving": serving, "batch": batch, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(total), "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -428,7 +428,7 @@ class Chain : public ChainBase {
         // update of the Lanczos vectors fused with the axis-3 inverse FFT of r_{j+1}
         const int u0 = prof_.mark(st_);
         if ((rc = launch_zinv_ph(j, err))) return rc;
-        prof_.count(LL_PROF_ZINV, split_ ? 2 : 1);
+        prof_.count(LL_PROF_ZINV, 2);
         prof_.span(LL_PROF_ZINV, u0, prof_.mark(st_));
         // r_{j+1} is upper when j is odd; the upper half gets D + K
         const int dens = (j % 2 == 1 && approx_ != LL_APPROX_IPA) ? 0 : -1;
@@ -674,10 +674,12 @@ class Chain : public ChainBase {
     const size_t smem = (size_t)nbnd_ * hq_.npw_pad * sizeof(cplx<T>) + (size_t)nbnd_ * nbnd_ * sizeof(cplx<double>) +
                         red_bytes(256);
     int rc;
-    if ((rc = set_smem(k_zinv_ph<T, N>, smem, err))) return rc;
     Coef co{beta_, gamma_, zpart_, err_};
-    k_zinv_ph<T, N><<<nks_, 256, smem, st_>>>(j, (j % 2 == 0) ? 1 : 0, dq_, nbnd_, part_, R(), X(), Vp(), y_, ukq_,
-                                              co, tol_, cbuf_, cb_ncol_);
+    // the per-k update, then the axis-3 inverse FFTs, one thread per column line
+    if ((rc = set_smem(k_ph_update<T>, smem, err))) return rc;
+    k_ph_update<T><<<nks_, 256, smem, st_>>>(j, (j % 2 == 0) ? 1 : 0, dq_, nbnd_, part_, R(), X(), Vp(), y_, ukq_, co,
+                                             tol_);
+    k_zinv<T, N><<<dim3(nks_, 1), 128, 0, st_>>>(dq_, R(), nbnd_, cbuf_, cb_ncol_);
     LL_CK(cudaGetLastError());
     return LL_OK;
   }

@@ -494,17 +494,18 @@ __device__ __forceinline__ double block_mean(const double* p, int n, int stride 
   return t / n;
 }
 
-// Pseudo-Hermitian step j fused with the first stage of the operator: beta_j from the
-// partials of Re(r_j^H X_j) (every block re-reduces them in the same order), z_j partial,
-// r_{j+1} = P_c(X_j/beta_j - beta_j v_{j-1}), v_j = r_j/beta_j, then the sphere columns of
-// r_{j+1} inverse-FFT'd along axis 3 straight from shared memory.  grid nks, block 256.
-// smem: r [nbnd][npw_pad], S [nbnd*nbnd] (double complex), reduction scratch.
-template <typename T, int N>
-__global__ void __launch_bounds__(256) k_zinv_ph(int j, int r_upper, SphereDev s, int nbnd,
-                                                 const double* __restrict__ part, cplx<T>* __restrict__ R,
-                                                 const cplx<T>* __restrict__ X, cplx<T>* __restrict__ Vp,
-                                                 const cplx<T>* __restrict__ y, const cplx<T>* __restrict__ ukq,
-                                                 Coef co, double tol, cplx<T>* __restrict__ cbuf, int cb_ncol) {
+// Pseudo-Hermitian step j: beta_j from the partials of Re(r_j^H X_j) (every block
+// re-reduces them in the same order), z_j partial, r_{j+1} = P_c(X_j/beta_j - beta_j v_{j-1})
+// formed in shared memory and written to R, v_j = r_j/beta_j.  The sphere columns of r_{j+1}
+// are then inverse-FFT'd along axis 3 by k_zinv (one thread per column line): with the
+// transforms inside this kernel its registers allowed 3 CTAs per SM instead of 4.
+// grid nks, block 256.  smem: r [nbnd][npw_pad], S [nbnd*nbnd] (double complex), scratch.
+template <typename T>
+__global__ void __launch_bounds__(256) k_ph_update(int j, int r_upper, SphereDev s, int nbnd,
+                                                   const double* __restrict__ part, cplx<T>* __restrict__ R,
+                                                   const cplx<T>* __restrict__ X, cplx<T>* __restrict__ Vp,
+                                                   const cplx<T>* __restrict__ y, const cplx<T>* __restrict__ ukq,
+                                                   Coef co, double tol) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int npw_pad = s.npw_pad, nks = s.nks;
   cplx<T>* rs = reinterpret_cast<cplx<T>*>(smem_raw);
@@ -541,22 +542,6 @@ __global__ void __launch_bounds__(256) k_zinv_ph(int j, int r_upper, SphereDev s
   small_dots<T>(uk, npw_pad, rs, npw_pad, np, nbnd, nbnd, nullptr, cf, red);
   subtract_projection<T>(rs, uk, cf, nbnd, npw_pad);
   for (int i = threadIdx.x; i < nbnd * npw_pad; i += blockDim.x) R[base + i] = rs[i];
-  const int nc = s.ncol[k];
-  for (int it = threadIdx.x; it < nbnd * nc; it += blockDim.x) {
-    const int v = it / nc, c = it - v * nc;
-    const int4 cl = s.col[k * s.ncol_max + c];
-    const cplx<T>* src = rs + v * npw_pad + s.colstart[k * s.ncol_max + c];
-    cplx<T> a[N];
-#pragma unroll
-    for (int p = 0; p < N; ++p) {
-      const int i = wrapn<N>(p - cl.z);
-      a[p] = (i < cl.w) ? src[i] : czero<T>();
-    }
-    fft_line<T, N, +1>(a);
-    cplx<T>* dst = cbuf + ((long)k * nbnd + v) * N * cb_ncol + c;
-#pragma unroll
-    for (int p = 0; p < N; ++p) dst[(long)p * cb_ncol] = a[p];
-  }
 }
 
 // Last stage of the operator fused with the per-k projections: forward FFT of the columns

@@ -1,6 +1,6 @@
 // Per-k work of the pseudo-Hermitian step split over several CTAs per k-point (sm_103a).
 //
-// The fused per-k kernels (k_zinv_ph, k_zfwd_proj) hold a whole k block of two vectors,
+// The fused per-k kernels (k_ph_update, k_zfwd_proj) hold a whole k block of two vectors,
 // 2 nbnd npw complex values, in one CTA's shared memory.  Systems whose k blocks do not fit
 // (the eight-atom cell: 16 bands x 1632 plane waves, 420 KB in FP32) take this path: every
 // k block is cut into chunks of kChunk plane waves (for the projections) or of kLines column
