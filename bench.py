@@ -170,6 +170,20 @@ def _step_flops(b) -> tuple[float, float]:
     return nominal, 0.5 * (dk + d)
 
 
+def _sc16(stream, steps: int = 200):
+    """The sixteen-atom cell (32 bands, 48^3, 64 KB projectors, 2048 orbitals of ~6000 plane
+    waves; the split per-k path), FP32 pseudo-Hermitian steps, when its ground state is cached
+    (building it takes ~30 minutes of CPU)."""
+    import workloads as w
+    b = w.cached_bundle(w.config_sc16())
+    if b is None:
+        return {"skipped": "ground state not cached (workloads.get_bundle(config_sc16()) takes ~30 min of CPU)"}
+    ch, _, ms, _ = _time_chain(b, "fp32", steps, 3, stream)
+    ch.close()
+    return {"workload": "sc16kb_30ry_48: 16-atom 2x2x2 supercell + KB s/p, 30 Ry, 48^3, 4x4x4 k, 32 bands, PH",
+            "steps": steps, "steps_per_s": steps / (ms / 1e3), "ms_per_step": ms / steps, "dtype": "f32"}
+
+
 def source_digest() -> str:
     """sha256 of the CUDA sources and the C header: names the code a profile was taken on."""
     import hashlib
@@ -408,6 +422,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--serving-jobs", type=int, default=32)
+    ap.add_argument("--headline-only", action="store_true",
+                    help="time the FP32 chain on the KB workload only (no other legs): for profiling")
     ap.add_argument("--batch-small", type=int, default=16, help="chains of the two-atom cell in the many-Q batch")
     ap.add_argument("--batch-cubic", type=int, default=2, help="chains of the eight-atom cell in the many-Q batch")
     args = ap.parse_args()
@@ -442,15 +458,20 @@ def main():
         ch32, c32, ms32, prof = _time_chain(b, "fp32", K, W, stream, profile=True)
     barrier()
     clocks = clk.summary()
-    # FP64 path on the same number of steps
-    ch64, c64, ms64, _ = _time_chain(b, "fp64", K, W, stream)
-    # the non-Hermitian recursion (two applications per step), FP32, same steps
-    chnh, _, msnh, _ = _time_chain(b, "fp32", K, W, stream, flavour="nh")
-    chnh.close()
-    nh = {"value": world * K / (msnh / 1e3), "ms_per_step": msnh / K, "applies_per_step": 2, "dtype": "f32"}
-    # the small two-atom cell (10 Ry, 18^3, 4^3 k, 256 orbitals): 300 FP64 pseudo-Hermitian
-    # steps and the spectrum, on the device
-    small = _small_cell(stream)
+    if args.headline_only:   # the FP32 chain alone (for profiling the headline's kernels)
+        ch64, c64, ms64 = ch32, c32, ms32
+        nh = small = None
+    else:
+        # FP64 path on the same number of steps
+        ch64, c64, ms64, _ = _time_chain(b, "fp64", K, W, stream)
+        # the non-Hermitian recursion (two applications per step), FP32, same steps
+        chnh, _, msnh, _ = _time_chain(b, "fp32", K, W, stream, flavour="nh")
+        chnh.close()
+        nh = {"value": world * K / (msnh / 1e3), "ms_per_step": msnh / K, "applies_per_step": 2, "dtype": "f32"}
+        # the small two-atom cell (10 Ry, 18^3, 4^3 k, 256 orbitals): 300 FP64 pseudo-Hermitian
+        # steps and the spectrum, on the device
+        small = _small_cell(stream)
+    sc16 = None if args.headline_only else _sc16(stream)
     m = min(SPEC_WINDOW, len(c32[0]), len(c64[0]))
     l32, l64 = _loss(c32, b, m), _loss(c64, b, m)
     spec_err = float(np.max(np.abs(l32 - l64)) / np.max(np.abs(l64)))
@@ -458,7 +479,7 @@ def main():
     spec_err_full = float(np.max(np.abs(lf32 - lf64)) / np.max(np.abs(lf64)))
     # per-step latency (single-step calls, host sync included)
     lat = []
-    for _ in range(50):
+    for _ in range(0 if args.headline_only else 50):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         if ch32.steps >= ch32.max_steps:
             break
@@ -468,21 +489,24 @@ def main():
         torch.cuda.synchronize()
         lat.append(e0.elapsed_time(e1))
     ch32.close()
-    ch64.close()
+    if ch64 is not ch32:
+        ch64.close()
 
     # end to end through the C ABI with host buffers: create (H2D of the ground state and
     # set-up), K steps, spectrum, coefficients and spectrum back to the host
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    che = _chain(b, "fp32", K, stream)
-    ce = che.lanczos(K)
-    wgrid = np.linspace(0.0, 40.0, 4001)
-    chi, ei, eps = che.spectrum(wgrid, 0.1)
-    che.close()
-    torch.cuda.synchronize()
-    t_e2e = time.perf_counter() - t0
-    e2e = {"value": K / t_e2e, "unit": "steps/s", "h2d_bytes_per_step": _bundle_bytes(b) / K,
-           "d2h_bytes_per_step": (sum(c.nbytes for c in ce) + chi.nbytes + ei.nbytes + eps.nbytes) / K}
+    e2e = None
+    if not args.headline_only:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        che = _chain(b, "fp32", K, stream)
+        ce = che.lanczos(K)
+        wgrid = np.linspace(0.0, 40.0, 4001)
+        chi, ei, eps = che.spectrum(wgrid, 0.1)
+        che.close()
+        torch.cuda.synchronize()
+        t_e2e = time.perf_counter() - t0
+        e2e = {"value": K / t_e2e, "unit": "steps/s", "h2d_bytes_per_step": _bundle_bytes(b) / K,
+               "d2h_bytes_per_step": (sum(c.nbytes for c in ce) + chi.nbytes + ei.nbytes + eps.nbytes) / K}
 
     # max over ranks of the timed region; the whole job's steps over that time
     tmax = max_over_ranks(ms32, world)
@@ -512,11 +536,12 @@ def main():
                      "achieved_tflops_pruned": pru * value / world / 1e12,
                      "frac_nominal": nom * value / world / 1e12 / peak, "frac_pruned": pru * value / world / 1e12 / peak,
                      "peak_tflops": peak, "bound": "alu"}
-    serving = _serving(b, args.serving_jobs) if args.serving_jobs > 0 else None
-    batch = _batch(args.batch_small, args.batch_cubic) if args.batch_small + args.batch_cubic > 0 else None
+    serving = _serving(b, args.serving_jobs) if args.serving_jobs > 0 and not args.headline_only else None
+    batch = (_batch(args.batch_small, args.batch_cubic)
+             if args.batch_small + args.batch_cubic > 0 and not args.headline_only else None)
 
     cpu = None
-    if rank == 0:
+    if rank == 0 and not args.headline_only:
         nk = 8
         t1 = _oracle_sample(b, nk, 1)
         n = max(1, int(args.cpu_seconds / max(t1, 1e-3)))
@@ -532,8 +557,9 @@ def main():
             "dtype": "f32", "data": "synthetic (seeded LDA ground state, workloads/)",
             "config": {"workload": WORKLOAD, "orbitals": int(b.nks * b.spec.nbnd), "npw_avg": float(np.mean(b.npw_kq)),
                        "l2": "per-step working set ~0.6 GB > 129 MB L2 (no flush)", "parallelism": "replicas"},
-            "fp64": {"value": world * K / (ms64 / 1e3), "ms_per_step": ms64 / K, "dtype": "f64"},
-            "nh_fp32": nh, "small_cell": small,
+            "fp64": None if args.headline_only else {"value": world * K / (ms64 / 1e3), "ms_per_step": ms64 / K,
+                                                      "dtype": "f64"},
+            "nh_fp32": nh, "small_cell": small, "sc16": sc16,
             "speedup_fp32_vs_fp64": ms64 / ms32,
             "spectrum_err_fp32_vs_fp64": spec_err, "spectrum_window_steps": m,
             "spectrum_err_fp32_vs_fp64_all_steps": spec_err_full,

@@ -279,7 +279,7 @@ class Chain : public ChainBase {
     if ((rc = tw_tables_upload(st_)) != cudaSuccess) { err = "twiddle upload failed"; return LL_ECUDA; }
     // device buffers
     if ((rc = upload_sphere(hk_, dk_, err)) || (rc = upload_sphere(hq_, dq_, err))) return rc;
-    cb_ncol_ = std::max(hk_.ncol_max, hq_.ncol_max);
+    cb_ncol_ = round_up(std::max(hk_.ncol_max, hq_.ncol_max), 2);   // even: 16-byte rows in FP32
     const int norb = nvec_ * nks_ * nbnd_;
     {
       int dev = 0, sms = 0;
@@ -298,24 +298,22 @@ class Chain : public ChainBase {
       const char* env = getenv("LL_SPLIT_PERK");
       split_ = fused > 227 * 1024 || (env && env[0] == '1' && env[1] == 0);
       nchunk_ = split_ ? (pq + kChunk - 1) / kChunk : 1;
-      if (split_ && flavour_ == LL_FLAVOUR_NH) {
-        err = "the non-Hermitian recursion needs k blocks (2 nbnd npw values) that fit one CTA's shared memory";
-        return LL_EUNSUPPORTED;
-      }
     }
-    const long nzp = (long)nks_ * nchunk_;
+    const long nzp = (long)nks_ * nchunk_;            // partials per vector and step
+    const long nzv = nzp * nvec_;
     if ((rc = alloc(&whart_, n3)) || (rc = alloc(&kin_, (long)nks_ * pq)) || (rc = alloc(&uk_, (long)nks_ * nbnd_ * pk)) ||
         (rc = alloc(&ukq_, vq)) || (rc = alloc(&bkq_, (long)bkq.size())) || (rc = alloc(&eps_, (long)nks_ * nbnd_)) ||
         (rc = alloc(&dij_, std::max(1, nproj_))) || (rc = alloc(&vloc_, n3)) || (rc = alloc(&rho_, n3)) ||
         (rc = alloc(&fxc_, n3)) || (rc = alloc(&ur_, (long)nks_ * nbnd_ * n3)) ||
         (rc = alloc(&cbuf_, (long)norb * n * cb_ncol_)) || (rc = alloc(&nprt_, (long)ngroups_ * n3)) ||
         (rc = alloc(&nr_, n3)) || (rc = alloc(&ng_, n3)) || (rc = alloc(&vpr_, n3)) ||
-        (rc = alloc(&y_, vq)) || (rc = alloc(&map_, (long)nks_ * pq)) || (rc = alloc(&part_, std::max(2L * nks_, nzp))) ||
-        (rc = alloc(&spart_, (long)nks_)) || (rc = alloc(&vecs_, 3L * nvec_ * vq)) ||
+        (rc = alloc(&y_, vq)) || (rc = alloc(&map_, (long)nks_ * pq)) || (rc = alloc(&part_, std::max(2L * nks_, nzv))) ||
+        (rc = alloc(&spart_, nzp)) || (rc = alloc(&vecs_, 3L * nvec_ * vq)) ||
         (rc = alloc(&beta_, cap_ + 2)) || (rc = alloc(&gamma_, cap_ + 2)) || (rc = alloc(&z_, cap_ + 1)) ||
         (rc = alloc(&zpart_, (long)(cap_ + 1) * nzp)) || (rc = alloc(&err_, 2)))
       return rc;
-    if (split_ && ((rc = alloc(&sp_s_, nzp * nbnd_ * nbnd_)) || (rc = alloc(&sp_c_, nzp * std::max(1, nproj_ * nbnd_))) ||
+    // chunk partials: U^H x per vector (two per vector on the non-Hermitian update), B^H x
+    if (split_ && ((rc = alloc(&sp_s_, 2 * nzv * nbnd_ * nbnd_)) || (rc = alloc(&sp_c_, nzv * std::max(1, nproj_ * nbnd_))) ||
                    (rc = alloc(&ub_, (long)nks_ * nbnd_ * std::max(1, nproj_)))))
       return rc;
     (void)err;
@@ -438,12 +436,22 @@ class Chain : public ChainBase {
         // L v_j: D + K on an upper v; L^dag w_j: D + K on a lower w
         const int dens = (approx_ == LL_APPROX_IPA) ? -1 : (upper ? 0 : 1);
         if ((rc = op(2, Vc(), XV(), dens, err))) return rc;
-        if ((rc = set_smem(k_nh_update<T>, smem_nh, err))) return rc;
         const int u0 = prof_.mark(st_);
-        k_nh_update<T><<<nks_, 128, smem_nh, st_>>>(j, upper, nks_, nbnd_, pq, dq_.npw, XV(), XW(), VpNH(), Wp(), Vc(),
-                                                    y_, ukq_, co, spart_);
-        k_nh_normalize<T><<<nks_, 128, 0, st_>>>(j, nks_, nbnd_, pq, spart_, XV(), XW(), Vc(), VpNH(), Wc(), Wp(), co,
-                                                 tol_);
+        if (split_) {  // the update split over plane-wave chunks (split.cuh)
+          const size_t sm = (size_t)(2 * nbnd_) * kTileP * sizeof(cplx<T>);
+          if ((rc = set_smem(k_sp_nh_start<T>, sm, err))) return rc;
+          k_sp_nh_start<T><<<dim3(nks_, nchunk_), 256, sm, st_>>>(j, upper, nks_, nbnd_, pq, dq_.npw, nchunk_, XV(),
+                                                                  XW(), VpNH(), Wp(), Vc(), y_, ukq_, co, sp_s_);
+          k_sp_nh_proj<T><<<dim3(nks_, nchunk_), 256, 0, st_>>>(nks_, nbnd_, pq, dq_.npw, nchunk_, XV(), XW(), ukq_,
+                                                                sp_s_, spart_);
+          prof_.count(LL_PROF_UPDATE, 1);
+        } else {
+          if ((rc = set_smem(k_nh_update<T>, smem_nh, err))) return rc;
+          k_nh_update<T><<<nks_, 128, smem_nh, st_>>>(j, upper, nks_, nbnd_, pq, dq_.npw, XV(), XW(), VpNH(), Wp(),
+                                                      Vc(), y_, ukq_, co, spart_);
+        }
+        k_nh_normalize<T><<<nks_, 128, 0, st_>>>(j, nks_, nbnd_, pq, nchunk_, spart_, XV(), XW(), Vc(), VpNH(), Wc(),
+                                                 Wp(), co, tol_);
         prof_.count(LL_PROF_UPDATE, 2);
         prof_.span(LL_PROF_UPDATE, u0, prof_.mark(st_));
       }

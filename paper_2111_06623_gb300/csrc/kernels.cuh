@@ -59,6 +59,13 @@ __global__ void __launch_bounds__(128) k_zinv(SphereDev s, const cplx<T>* __rest
 }
 
 // ---------------------------------------------------------------------------------------
+// Bulk prefetch of a contiguous global range into L2 (no data returned to the SM): address
+// 16-byte aligned, size a multiple of 16.
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// ---------------------------------------------------------------------------------------
 // Per-plane pass of one operator application.  grid (N planes, groups), block 128.
 // The sphere's columns are ordered by (m2, m1) and grouped in rows of equal m2 (consecutive
 // m1).  For every orbital of the group (BO at a time), at plane j3 = blockIdx.x:
@@ -95,7 +102,7 @@ struct XYArgs {
 };
 
 template <typename T, int N, int BO, int MODE>
-__global__ void __launch_bounds__(128, MODE == XY_PASS1_DENS ? 3 : 4) k_xy(XYArgs a, cplx<T>* __restrict__ cbuf, const T* __restrict__ vloc,
+__global__ void __launch_bounds__(128, N > 36 ? 2 : (MODE == XY_PASS1_DENS ? 3 : 4)) k_xy(XYArgs a, cplx<T>* __restrict__ cbuf, const T* __restrict__ vloc,
                                                const cplx<T>* __restrict__ vpr, const cplx<T>* __restrict__ ur,
                                                cplx<T>* __restrict__ nprt, cplx<T>* __restrict__ grid_out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -122,9 +129,20 @@ __global__ void __launch_bounds__(128, MODE == XY_PASS1_DENS ? 3 : 4) k_xy(XYArg
 
   const int o_begin = a.o_off + g * a.per_group;
   const int o_end = a.o_off + min(a.norb, g * a.per_group + a.per_group);
+  // The next batch's column-buffer rows of this plane (cb_ncol is even: 16-byte multiples)
+  // are prefetched into L2 while this batch is transformed.  (Prefetching the orbital-grid
+  // planes too was measured: their lines were evicted before use and re-read, +20 % DRAM.)
+  auto prefetch_batch = [&](int obatch) {
+    const int t = threadIdx.x;
+    if (t < BO && obatch + t < o_end)
+      prefetch_l2(cbuf + (long)(obatch + t) * N * a.cb_ncol + (long)iz * a.cb_ncol,
+                  (unsigned)(a.cb_ncol * sizeof(cplx<T>)));
+  };
+  prefetch_batch(o_begin);
   for (int ob = o_begin; ob < o_end; ob += BO) {
     const int nb = min(BO, o_end - ob);
     __syncthreads();
+    if (ob + BO < o_end) prefetch_batch(ob + BO);
     if (MODE != XY_PASS2) {
       for (int i = threadIdx.x; i < nb * a.cb_ncol; i += blockDim.x) {
         const int b = a.f_ncol.div(i), c = i - b * a.cb_ncol;
@@ -663,7 +681,7 @@ __global__ void __launch_bounds__(128) k_nh_update(int j, int upper, int nks, in
 // Non-Hermitian normalisation at the end of step j: beta_{j+1} = sqrt|s|, gamma_{j+1} =
 // s/beta_{j+1}; v_{j-1} <- v_j, v_j <- v_hat/beta; w_{j-1} <- w_j, w_j <- w_hat/conj(gamma).
 template <typename T>
-__global__ void __launch_bounds__(128) k_nh_normalize(int j, int nks, int nbnd, int npw_pad,
+__global__ void __launch_bounds__(128) k_nh_normalize(int j, int nks, int nbnd, int npw_pad, int nchunk,
                                                       const cplx<double>* __restrict__ spart,
                                                       const cplx<T>* __restrict__ XV, const cplx<T>* __restrict__ XW,
                                                       cplx<T>* __restrict__ Vc, cplx<T>* __restrict__ Vp,
@@ -671,8 +689,9 @@ __global__ void __launch_bounds__(128) k_nh_normalize(int j, int nks, int nbnd, 
                                                       double tol) {
   __shared__ cplx<double> sc[2];
   const int k = blockIdx.x;
-  const double sr = block_mean(reinterpret_cast<const double*>(spart), nks, 2, 0);
-  const double si = block_mean(reinterpret_cast<const double*>(spart), nks, 2, 1);
+  // spart: nks nchunk partials (one per k, or per (k, chunk) on the split path)
+  const double sr = block_mean(reinterpret_cast<const double*>(spart), nks * nchunk, 2, 0) * nchunk;
+  const double si = block_mean(reinterpret_cast<const double*>(spart), nks * nchunk, 2, 1) * nchunk;
   if (threadIdx.x == 0) {
     const double a = sqrt(sr * sr + si * si);
     double b = sqrt(a);

@@ -356,4 +356,114 @@ static __global__ void k_sp_reduce(int nchunk, int np, const cplx<double>* __res
   }
 }
 
+// Non-Hermitian step j on the split path, first part (the fused k_nh_update cut in two):
+// z_j partial = (y, v_j) over the chunk, v_hat = XV - gamma_j v_{j-1} and w_hat = XW -
+// beta_j w_{j-1} in place, and the chunk's partials of U^H v_hat, U^H w_hat.
+// grid (nks, nchunk), block 256; dynamic smem 2 nbnd kTileP complex T.
+template <typename T>
+__global__ void __launch_bounds__(256) k_sp_nh_start(int j, int upper, int nks, int nbnd, int npw_pad,
+                                                     const int* __restrict__ npw, int nchunk, cplx<T>* __restrict__ XV,
+                                                     cplx<T>* __restrict__ XW, const cplx<T>* __restrict__ Vp,
+                                                     const cplx<T>* __restrict__ Wp, const cplx<T>* __restrict__ Vc,
+                                                     const cplx<T>* __restrict__ y, const cplx<T>* __restrict__ ukq,
+                                                     Coef co, cplx<double>* __restrict__ spart2) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T>* tile = reinterpret_cast<cplx<T>*>(smem_raw);
+  __shared__ double zred[2][8];
+  const int k = blockIdx.x, c = blockIdx.y;
+  const int g0 = c * kChunk, g1 = min(npw_pad, g0 + kChunk), n = g1 - g0;
+  const long base = (long)k * nbnd * npw_pad;
+  const int zi = (j - 1) * nks * nchunk + k * nchunk + c;
+  if (upper) {  // z_j partial = (y, v_j) over the chunk
+    double zr = 0.0, zim = 0.0;
+    for (int e = threadIdx.x; e < nbnd * n; e += blockDim.x) {
+      const int v = e / n;
+      const long i = base + (long)v * npw_pad + g0 + e - v * n;
+      const cplx<T> a = y[i], r = Vc[i];
+      zr += (double)(a.x * r.x + a.y * r.y);
+      zim += (double)(a.x * r.y - a.y * r.x);
+    }
+    zr = warp_sum(zr);
+    zim = warp_sum(zim);
+    if ((threadIdx.x & 31) == 0) { zred[0][threadIdx.x >> 5] = zr; zred[1][threadIdx.x >> 5] = zim; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sr = 0.0, si = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { sr += zred[0][w]; si += zred[1][w]; }
+      co.zpart[zi] = mk(sr, si);
+    }
+  } else if (threadIdx.x == 0) {
+    co.zpart[zi] = mk(0.0, 0.0);
+  }
+  const double bj = co.beta[j - 1];
+  const cplx<double> gj = co.gamma[j - 1];
+  const cplx<T> g = mk((T)gj.x, (T)gj.y), bc = mk((T)bj, (T)0);
+  for (int e = threadIdx.x; e < nbnd * n; e += blockDim.x) {
+    const int v = e / n;
+    const long i = base + (long)v * npw_pad + g0 + e - v * n;
+    XV[i] = XV[i] - cmul(g, Vp[i]);
+    XW[i] = XW[i] - cmul(bc, Wp[i]);
+  }
+  __syncthreads();
+  const int ge = max(g0, min(g1, npw[k]));
+  cplx<double>* out = spart2 + ((long)k * nchunk + c) * 2 * nbnd * nbnd;
+  chunk_dots<T>(ukq + base, npw_pad, XV + base, npw_pad, g0, ge, nbnd, nbnd, tile, out);
+  chunk_dots<T>(ukq + base, npw_pad, XW + base, npw_pad, g0, ge, nbnd, nbnd, tile, out + nbnd * nbnd);
+}
+
+// Second part: P_c on v_hat and w_hat with the coefficients reduced over the chunks (fixed
+// order), and the chunk's partial s = (w_hat, v_hat).  grid (nks, nchunk), block 256.
+template <typename T>
+__global__ void __launch_bounds__(256) k_sp_nh_proj(int nks, int nbnd, int npw_pad, const int* __restrict__ npw,
+                                                    int nchunk, cplx<T>* __restrict__ XV, cplx<T>* __restrict__ XW,
+                                                    const cplx<T>* __restrict__ ukq,
+                                                    const cplx<double>* __restrict__ spart2,
+                                                    cplx<double>* __restrict__ spart) {
+  __shared__ cplx<T> Sv[32 * 32], Sw[32 * 32];
+  __shared__ double sred[2][8];
+  const int k = blockIdx.x, c = blockIdx.y;
+  const int nn = nbnd * nbnd;
+  for (int p = threadIdx.x; p < nn; p += blockDim.x) {
+    double vr = 0.0, vi = 0.0, wr = 0.0, wi = 0.0;
+    for (int cc = 0; cc < nchunk; ++cc) {
+      const cplx<double>* q = spart2 + ((long)k * nchunk + cc) * 2 * nn;
+      vr += q[p].x; vi += q[p].y;
+      wr += q[nn + p].x; wi += q[nn + p].y;
+    }
+    Sv[p] = mk((T)vr, (T)vi);
+    Sw[p] = mk((T)wr, (T)wi);
+  }
+  __syncthreads();
+  const int g0 = c * kChunk, g1 = min(npw_pad, g0 + kChunk), n = g1 - g0;
+  const int np = npw[k];
+  const long base = (long)k * nbnd * npw_pad;
+  const cplx<T>* uk = ukq + base;
+  double sr = 0.0, si = 0.0;
+  for (int e = threadIdx.x; e < nbnd * n; e += blockDim.x) {
+    const int v = e / n, g = g0 + e - v * n;
+    const long i = base + (long)v * npw_pad + g;
+    cplx<T> a = XV[i], b = XW[i];
+    for (int w = 0; w < nbnd; ++w) {
+      const cplx<T> u = uk[(long)w * npw_pad + g];
+      a = a - cmul(u, Sv[w * nbnd + v]);
+      b = b - cmul(u, Sw[w * nbnd + v]);
+    }
+    XV[i] = a;
+    XW[i] = b;
+    if (g < np) {
+      sr += (double)(b.x * a.x + b.y * a.y);
+      si += (double)(b.x * a.y - b.y * a.x);
+    }
+  }
+  sr = warp_sum(sr);
+  si = warp_sum(si);
+  if ((threadIdx.x & 31) == 0) { sred[0][threadIdx.x >> 5] = sr; sred[1][threadIdx.x >> 5] = si; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += sred[0][w]; b += sred[1][w]; }
+    spart[(long)k * nchunk + c] = mk(a, b);
+  }
+}
+
 }  // namespace ll

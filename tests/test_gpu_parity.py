@@ -259,10 +259,21 @@ def test_cubic8_first_coefficients(lib, cubic8):
     assert _coef_rel(got32, ref, 8) < 1e-4
 
 
-def test_cubic8_non_hermitian_unsupported(lib, cubic8):
-    with pytest.raises(lib.LLError) as e:
-        chain_from_bundle(cubic8, flavour="nh", max_steps=4)
-    assert e.value.code == lib.LL_EUNSUPPORTED
+def test_cubic8_non_hermitian(lib, cubic8):
+    """The non-Hermitian recursion on the split path (update cut into two chunked kernels)."""
+    sys = System(cubic8)
+    ref = lanczos.non_hermitian(sys, 5)
+    got = chain_from_bundle(cubic8, flavour="nh", max_steps=5).lanczos(5)
+    assert _coef_rel(got, ref, 5) < 1e-10
+
+
+def test_split_path_non_hermitian_small(lib, small, monkeypatch):
+    """Forced split path, 120 non-Hermitian FP64 steps: the oracle's first 100 coefficients."""
+    sys = System(small)
+    ref = lanczos.non_hermitian(sys, 120)
+    monkeypatch.setenv("LL_SPLIT_PERK", "1")
+    got = chain_from_bundle(small, flavour="nh", max_steps=120).lanczos(120)
+    assert _coef_rel(got, ref, 100) < 1e-10
 
 
 @pytest.mark.parametrize("kind", ["constant", "osc"])
@@ -285,3 +296,30 @@ def test_extrapolated_spectrum(lib, small, kind):
     gb, gg, gz = extrapolate(got[0], got[1], got[2], kind, 5000)
     rchi2, _, _ = spectrum.spectrum(gb, gg, gz, s.omega, s.q_cart, WGRID, ETA)
     assert np.max(np.abs(chi2 - rchi2)) / np.max(np.abs(rchi2)) < 1e-10
+
+
+# ---- sixteen-atom cell (32 bands, 48^3, 64 KB projectors, ~6000 plane waves): its ground
+# state takes ~30 minutes of CPU, so these run where the bundle has been built and cached ----
+
+@pytest.fixture(scope="module")
+def sc16():
+    b = w.cached_bundle(w.config_sc16())
+    if b is None:
+        pytest.skip("sixteen-atom ground state not cached (workloads.get_bundle(config_sc16()))")
+    return b
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+def test_sc16_single_application(lib, sc16, precision, tol):
+    sys = System(sc16)
+    ch = chain_from_bundle(sc16, precision=precision, max_steps=4)
+    x = _rand(sys, 14)
+    for upper in (False, True):
+        assert rel_batch(ch.apply(x, upper), sys.apply_op(x, upper)) < tol
+
+
+def test_sc16_first_coefficients(lib, sc16):
+    sys = System(sc16)
+    ref = lanczos.pseudo_hermitian(sys, 3)
+    got = chain_from_bundle(sc16, max_steps=3).lanczos(3)
+    assert _coef_rel(got, ref, 3) < 1e-10

@@ -125,6 +125,25 @@ def config_cubic8(q_cart: np.ndarray | None = None) -> SystemSpec:
                       approx="tddft", scf_kmesh=(2, 2, 2), steps=1500, flavour="ph")
 
 
+def config_sc16(q_cart: np.ndarray | None = None) -> SystemSpec:
+    """Sixteen-atom cell: the 2x2x2 supercell of the two-atom primitive cell (Omega = 2160
+    bohr^3, all sides 14.51 bohr), atoms displaced by N(0, 0.05 bohr) from default_rng(20211112)
+    (shape (16, 3), atom-major), KB s/p projectors on every atom (64), 30 Ry, 48^3 grid,
+    4x4x4 mesh, 32 bands, Q = 0.15 (2 pi/a)(1,1,0)/sqrt(2) unless given.  The self-consistent
+    density is converged at Gamma (the supercell's Gamma folds the primitive 2x2x2 mesh), to
+    1e-8 in the L1 density residual."""
+    lat0, tau0 = _diamond(A_LAT)
+    lat = 2.0 * lat0
+    shifts = [i * lat0[0] + j * lat0[1] + k * lat0[2] for i in range(2) for j in range(2) for k in range(2)]
+    tau = np.array([t + sh for sh in shifts for t in tau0])
+    tau = tau + np.random.default_rng(20211112).normal(0.0, 0.05, size=(16, 3))
+    q = (0.15 * (2 * np.pi / A_LAT) * np.array([1.0, 1.0, 0.0]) / np.sqrt(2.0) if q_cart is None
+         else np.asarray(q_cart, float))
+    return SystemSpec("sc16kb_30ry_48", lat, tau, 4.0, 1.0, 30.0, 48, (4, 4, 4), 32, q,
+                      approx="tddft", kb=True, scf_kmesh=(1, 1, 1), steps=2000, flavour="ph",
+                      extra={"scf_tol": 1e-8})
+
+
 def config_tiny(kb: bool = False, approx: str = "tddft") -> SystemSpec:
     """A cell small enough for brute-force Casida diagonalisation: 4 Ry, 12^3, 2x2x2 k."""
     lat, tau = _diamond(A_LAT)
@@ -152,7 +171,7 @@ def config_free_electron(nk: int = 6, ecut: float = 3.0, nfft: int = 12,
     return s
 
 
-CONFIGS = {"small": config_small, "kb": config_kb, "tiny": config_tiny, "cubic8": config_cubic8}
+CONFIGS = {"small": config_small, "kb": config_kb, "tiny": config_tiny, "cubic8": config_cubic8, "sc16": config_sc16}
 
 
 def sphere(kcart: np.ndarray, bvec: np.ndarray, ecut_ry: float, guard: float = 1e-9) -> np.ndarray:

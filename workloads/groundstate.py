@@ -261,7 +261,10 @@ def scf(spec: SystemSpec, tol: float = 1e-11, maxiter: int = 80, verbose: bool =
     rho = np.full((n, n, n), spec.nelec / spec.omega)
     if spec.free_electron:
         return vion + lda_vxc(rho), rho, 0
-    runner = runner or _Runner(0)
+    tol = spec.extra.get("scf_tol", tol)
+    # a pool of single-threaded workers only pays with several k-points; one or two large
+    # eigenproblems run here with threaded LAPACK
+    runner = runner if (runner is not None and len(kc) >= 4) else _Runner(0)
     hist_in, hist_res = [], []
     err = np.inf
     for it in range(1, maxiter + 1):
@@ -390,6 +393,12 @@ def load_bundle(spec: SystemSpec, path: str) -> Bundle:
                   eps_k=z["eps_k"], eps_kq=z["eps_kq"], vloc_r=z["vloc_r"], rho_r=z["rho_r"],
                   beta_kq=[np.ascontiguousarray(sl(z["beta_kq"], sq, i).T) for i in range(nks)],
                   dij=z["dij"], scf_iters=int(z["scf_iters"]), gap_min=float(z["gap_min"]))
+
+
+def cached_bundle(spec: SystemSpec) -> Bundle | None:
+    """The cached bundle of spec, or None when it has not been built here."""
+    path = os.path.join(cache_dir(), f"{spec.name}_{_spec_key(spec)}.npz")
+    return load_bundle(spec, path) if os.path.exists(path) else None
 
 
 def get_bundle(spec: SystemSpec, verbose: bool = False) -> Bundle:
