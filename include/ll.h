@@ -87,11 +87,13 @@ int ll_destroy(ll_handle* h);
 /* Runs n_steps more Lanczos steps (Sec. 2.5), continuing from the resident state
  * (restart semantics of Sec. 3.2).  On return the arrays hold every coefficient so far
  * (`*steps_done` of them; capacity max_steps):
+ *   alpha[i] = T_{i,i} = 0: every Lanczos vector has one non-zero half of the SBR pair and L
+ *              maps one half to the other, so the diagonal of T vanishes in both recursions;
  *   beta[i]  = b_1 (i = 0) or T_{i+1,i};   gamma[i] (complex) = b_1 or T_{i,i+1};
  *   z[i] (complex) = z_{i+1} = ((y, 0), v_{i+1}) (Eq. 31).
- * Any of beta, gamma, z may be NULL.  LL_ENOTPD / LL_EBREAKDOWN stop the chain; steps_done
- * then counts the steps whose coefficients are valid. */
-int ll_lanczos(ll_handle* h, int n_steps, double* beta, double* gamma, double* z, int* steps_done);
+ * Any of alpha, beta, gamma, z may be NULL.  LL_ENOTPD / LL_EBREAKDOWN stop the chain;
+ * steps_done then counts the steps whose coefficients are valid. */
+int ll_lanczos(ll_handle* h, int n_steps, double* alpha, double* beta, double* gamma, double* z, int* steps_done);
 
 /* Spectrum of a handle's own coefficients on the device (Eqs. 32-33, 5):
  * chi(Q, w) = (4/Omega) b_1 sum_j z_j x_j with ((w + i eta) - T_M) x = e_1, using the first
@@ -187,6 +189,12 @@ int ll_footprint(const ll_system_desc* desc, size_t* bytes);
 
 const char* ll_last_error(void);
 const char* ll_version(void);
+
+/* Measured FMA throughput of the current device in TFLOP/s (precision LL_PREC_FP32 or
+ * LL_PREC_FP64): a kernel of independent FMA chains on every SM, the fastest of three timed
+ * launches on `stream` (CUDA events).  The roofline denominator of the FFT kernels.  Allocates
+ * and frees a small device buffer; returns after the measurement. */
+int ll_fma_peak(int precision, double* tflops, void* stream);
 
 /* ---- Request loop: continuous batching of chains (an engineering addition; the paper runs
  * one recursion per momentum transfer, Sec. 3.2).  A scheduler thread admits queued jobs in

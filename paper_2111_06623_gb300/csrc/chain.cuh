@@ -291,15 +291,25 @@ class Chain : public ChainBase {
     // per-k work: fused (one CTA holds a k block) when it fits in shared memory, else split
     // over chunks of plane waves (LL_SPLIT_PERK=1 in the environment forces the split path)
     {
-      // dynamic part of k_zfwd_proj, plus its static arrays (projection coefficients, eps)
-      const size_t fused = 2 * (size_t)nbnd_ * pq * sizeof(cplx<T>) +
-                           (size_t)std::max(nproj_, nbnd_) * nbnd_ * sizeof(cplx<double>) + red_bytes(256) +
-                           32 * 32 * sizeof(cplx<T>) + 4096;
+      // one CTA per (k, group of bpc bands): the largest band group whose two vectors, dot
+      // coefficients, scratch and static arrays fit one CTA's shared memory (all bands of a
+      // k-point when they fit: the Lanczos partials are then one per k)
+      auto fused = [&](int b) {
+        bpc_ = b;
+        return 2 * (size_t)b * pq * sizeof(cplx<T>) + (size_t)std::max(nproj_, nbnd_) * b * sizeof(cplx<double>) +
+               red_bytes(256) + 32 * 32 * sizeof(cplx<T>) + 4096;
+      };
+      int best = 0;
+      for (int b = nbnd_; b >= 1 && !best; --b)
+        if (nbnd_ % b == 0 && fused(b) <= 227 * 1024) best = b;
+      bpc_ = best > 0 ? best : nbnd_;
+      ngrp_ = nbnd_ / bpc_;
       const char* env = getenv("LL_SPLIT_PERK");
-      split_ = fused > 227 * 1024 || (env && env[0] == '1' && env[1] == 0);
+      split_ = best == 0 || (env && env[0] == '1' && env[1] == 0);
       nchunk_ = split_ ? (pq + kChunk - 1) / kChunk : 1;
+      npk_ = split_ ? nchunk_ : ngrp_;
     }
-    const long nzp = (long)nks_ * nchunk_;            // partials per vector and step
+    const long nzp = (long)nks_ * npk_;               // partials per vector and step
     const long nzv = nzp * nvec_;
     if ((rc = alloc(&whart_, n3)) || (rc = alloc(&kin_, (long)nks_ * pq)) || (rc = alloc(&uk_, (long)nks_ * nbnd_ * pk)) ||
         (rc = alloc(&ukq_, vq)) || (rc = alloc(&bkq_, (long)bkq.size())) || (rc = alloc(&eps_, (long)nks_ * nbnd_)) ||
@@ -417,7 +427,7 @@ class Chain : public ChainBase {
     if (stopped_) { err = "the chain stopped at a breakdown"; return LL_EBREAKDOWN; }
     int rc;
     const int pq = hq_.npw_pad;
-    const size_t smem_nh = 2 * (size_t)nbnd_ * pq * sizeof(cplx<T>) + (size_t)nbnd_ * nbnd_ * sizeof(cplx<double>) +
+    const size_t smem_nh = 2 * (size_t)bpc_ * pq * sizeof(cplx<T>) + (size_t)nbnd_ * bpc_ * sizeof(cplx<double>) +
                            16 * 4 * sizeof(double);
     Coef co{beta_, gamma_, zpart_, err_};
     for (int s = 0; s < n; ++s) {
@@ -447,10 +457,11 @@ class Chain : public ChainBase {
           prof_.count(LL_PROF_UPDATE, 1);
         } else {
           if ((rc = set_smem(k_nh_update<T>, smem_nh, err))) return rc;
-          k_nh_update<T><<<nks_, 128, smem_nh, st_>>>(j, upper, nks_, nbnd_, pq, dq_.npw, XV(), XW(), VpNH(), Wp(),
+          k_nh_update<T><<<dim3(nks_, ngrp_), 128, smem_nh, st_>>>(j, upper, nks_, nbnd_, bpc_, pq, dq_.npw, XV(),
+                                                                   XW(), VpNH(), Wp(),
                                                       Vc(), y_, ukq_, co, spart_);
         }
-        k_nh_normalize<T><<<nks_, 128, 0, st_>>>(j, nks_, nbnd_, pq, nchunk_, spart_, XV(), XW(), Vc(), VpNH(), Wc(),
+        k_nh_normalize<T><<<nks_, 128, 0, st_>>>(j, nks_, nbnd_, pq, npk_, spart_, XV(), XW(), Vc(), VpNH(), Wc(),
                                                  Wp(), co, tol_);
         prof_.count(LL_PROF_UPDATE, 2);
         prof_.span(LL_PROF_UPDATE, u0, prof_.mark(st_));
@@ -458,7 +469,7 @@ class Chain : public ChainBase {
       LL_CK(cudaGetLastError());
     }
     if (n > 0) {
-      k_reduce_z<<<(n + 127) / 128, 128, 0, st_>>>(zpart_, nks_ * nchunk_, nks_, queued_, queued_ + n, z_);
+      k_reduce_z<<<(n + 127) / 128, 128, 0, st_>>>(zpart_, nks_ * npk_, nks_, queued_, queued_ + n, z_);
       LL_CK(cudaGetLastError());
       prof_.count(LL_PROF_UPDATE);
     }
@@ -616,18 +627,18 @@ class Chain : public ChainBase {
 
   // reduction scratch of the per-k dot routines: max(16, 2*ni*nj) doubles per warp
   size_t red_bytes(int threads) const {
-    const int pairs = std::max(std::max(nproj_, nbnd_) * nbnd_, 8);
+    const int pairs = std::max(std::max(nproj_, nbnd_) * std::max(bpc_, 1), 8);
     return (size_t)(threads / 32) * 2 * pairs * sizeof(double);
   }
   template <int N>
   int zfwd_proj_n(int nvec, const cplx<T>* in, cplx<T>* out, std::string& err) {
     if (split_) return zfwd_split_n<N>(nvec, in, out, err);
-    const size_t smem = 2 * (size_t)nbnd_ * hq_.npw_pad * sizeof(cplx<T>) +
-                        (size_t)std::max(nproj_, nbnd_) * nbnd_ * sizeof(cplx<double>) + red_bytes(256);
+    const size_t smem = 2 * (size_t)bpc_ * hq_.npw_pad * sizeof(cplx<T>) +
+                        (size_t)std::max(nproj_, nbnd_) * bpc_ * sizeof(cplx<double>) + red_bytes(256);
     int rc;
     if ((rc = set_smem(k_zfwd_proj<T, N>, smem, err))) return rc;
-    k_zfwd_proj<T, N><<<dim3(nks_, nvec), 256, smem, st_>>>(dq_, nbnd_, cbuf_, cb_ncol_, in, kin_, eps_, ukq_, bkq_,
-                                                             dij_, nproj_, out, part_);
+    k_zfwd_proj<T, N><<<dim3(nks_, nvec, ngrp_), 256, smem, st_>>>(dq_, nbnd_, bpc_, cbuf_, cb_ncol_, in, kin_, eps_,
+                                                                    ukq_, bkq_, dij_, nproj_, out, part_);
     LL_CK(cudaGetLastError());
     return LL_OK;
   }
@@ -679,14 +690,14 @@ class Chain : public ChainBase {
   template <int N>
   int zinv_ph_n(int j, std::string& err) {
     if (split_) return zinv_split_n<N>(j, err);
-    const size_t smem = (size_t)nbnd_ * hq_.npw_pad * sizeof(cplx<T>) + (size_t)nbnd_ * nbnd_ * sizeof(cplx<double>) +
+    const size_t smem = (size_t)bpc_ * hq_.npw_pad * sizeof(cplx<T>) + (size_t)nbnd_ * bpc_ * sizeof(cplx<double>) +
                         red_bytes(256);
     int rc;
     Coef co{beta_, gamma_, zpart_, err_};
-    // the per-k update, then the axis-3 inverse FFTs, one thread per column line
+    // the per-(k, band group) update, then the axis-3 inverse FFTs, one thread per column line
     if ((rc = set_smem(k_ph_update<T>, smem, err))) return rc;
-    k_ph_update<T><<<nks_, 256, smem, st_>>>(j, (j % 2 == 0) ? 1 : 0, dq_, nbnd_, part_, R(), X(), Vp(), y_, ukq_, co,
-                                             tol_);
+    k_ph_update<T><<<dim3(nks_, ngrp_), 256, smem, st_>>>(j, (j % 2 == 0) ? 1 : 0, dq_, nbnd_, bpc_, part_, R(), X(),
+                                                          Vp(), y_, ukq_, co, tol_);
     k_zinv<T, N><<<dim3(nks_, 1), 128, 0, st_>>>(dq_, R(), nbnd_, cbuf_, cb_ncol_);
     LL_CK(cudaGetLastError());
     return LL_OK;
@@ -742,7 +753,7 @@ class Chain : public ChainBase {
   }
   template <int N, int MODE>
   int xy_nm(const SphereDev& s, int norb, int o_off, int dens_vec, std::string& err) {
-    constexpr int B = BO<N, MODE>::v;
+    int B = BO<N, MODE>::v;
     XYArgs a;
     a.s = s;
     a.nbnd = nbnd_;
@@ -756,16 +767,24 @@ class Chain : public ChainBase {
     a.f_nks = FastDiv((unsigned)s.nks);
     a.f_pervec = FastDiv((unsigned)(s.nks * nbnd_));
     const int NP = N + 1;
-    size_t smem = (size_t)B * cb_ncol_ + (size_t)B * s.nrow_max * NP;
-    if (MODE == XY_PASS2) smem += (size_t)N * N;
-    if (MODE == XY_PASS1_DENS) smem += (size_t)(128 / N) * N * N;   // per-slot density planes
-    smem *= sizeof(cplx<T>);
-    if (MODE == XY_PASS1 || MODE == XY_PASS1_DENS) smem += (size_t)N * N * sizeof(T);
+    auto smem_for = [&](int b) {
+      size_t m = (size_t)b * cb_ncol_ + (size_t)b * s.nrow_max * NP;
+      if (MODE == XY_PASS2) m += (size_t)N * N;
+      if (MODE == XY_PASS1_DENS) m += (size_t)(128 / N) * N * N;   // per-slot density planes
+      m *= sizeof(cplx<T>);
+      if (MODE == XY_PASS1 || MODE == XY_PASS1_DENS) m += (size_t)N * N * sizeof(T);
+      return m;
+    };
+    // fewer orbitals per batch where the default batch's tiles exceed shared memory (FP64 at
+    // N = 48 on the 16-atom cell)
+    while (B > 1 && smem_for(B) > 200 * 1024) --B;
+    const size_t smem = smem_for(B);
+    a.bo = B;
     int rc;
-    if ((rc = set_smem(k_xy<T, N, B, MODE>, smem, err))) return rc;
-    const int ng = groups_for_kernel(k_xy<T, N, B, MODE>, smem, norb, xy_groups_[MODE]);
+    if ((rc = set_smem(k_xy<T, N, MODE>, smem, err))) return rc;
+    const int ng = groups_for_kernel(k_xy<T, N, MODE>, smem, norb, xy_groups_[MODE]);
     a.per_group = (norb + ng - 1) / ng;
-    k_xy<T, N, B, MODE><<<dim3(N, ng), 128, smem, st_>>>(a, cbuf_, vloc_, vpr_, ur_, nprt_, ur_);
+    k_xy<T, N, MODE><<<dim3(N, ng), 128, smem, st_>>>(a, cbuf_, vloc_, vpr_, ur_, nprt_, ur_);
     if (MODE == XY_PASS1_DENS) last_ng_ = ng;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) { err = std::string("k_xy: ") + cudaGetErrorString(e); return LL_ECUDA; }
@@ -930,6 +949,8 @@ class Chain : public ChainBase {
   ExtrapTail* tail_ = nullptr;   // continuation constants of the coefficients (spectrum)
   bool split_ = false;      // per-k work split over chunks of plane waves (split.cuh)
   int nchunk_ = 1;          // plane-wave chunks per k on the split path
+  int bpc_ = 1, ngrp_ = 1;  // bands per CTA of the per-k kernels, band groups per k
+  int npk_ = 1;             // partial sums per k of the Lanczos scalars (ngrp_, or nchunk_ split)
   cplx<double> *sp_s_ = nullptr, *sp_c_ = nullptr, *ub_ = nullptr;   // chunk partials of U^H r, B^H x; U^H B
   double* spec_w_ = nullptr;
   int *map_ = nullptr, *err_ = nullptr;

@@ -96,12 +96,13 @@ struct XYArgs {
   int per_group;               // orbitals per group
   int o_off;                   // first orbital of this launch (orbital o = o_off + local index)
   int dens_vec;                // vector whose orbitals feed the density (XY_PASS1_DENS)
+  int bo;                      // orbitals per batch (as many as shared memory allows, <= the mode's default)
   FastDiv f_ncol, f_nrow;      // divisions by cb_ncol and by the sphere table's nrow_max
   FastDiv f_nbnd, f_nks;       // orbital -> k: (o / nbnd) mod nks
   FastDiv f_pervec;            // orbital -> vector: o / (nks nbnd)
 };
 
-template <typename T, int N, int BO, int MODE>
+template <typename T, int N, int MODE>
 __global__ void __launch_bounds__(128, N > 36 ? 2 : (MODE == XY_PASS1_DENS ? 3 : 4)) k_xy(XYArgs a, cplx<T>* __restrict__ cbuf, const T* __restrict__ vloc,
                                                const cplx<T>* __restrict__ vpr, const cplx<T>* __restrict__ ur,
                                                cplx<T>* __restrict__ nprt, cplx<T>* __restrict__ grid_out) {
@@ -109,6 +110,7 @@ __global__ void __launch_bounds__(128, N > 36 ? 2 : (MODE == XY_PASS1_DENS ? 3 :
   constexpr int NP = N + 1;
   constexpr int NN = N * N;
   const int iz = blockIdx.x, g = blockIdx.y;
+  const int BO = a.bo;
   const SphereDev& s = a.s;
   cplx<T>* Cs = reinterpret_cast<cplx<T>*>(smem_raw);                 // [BO][cb_ncol]
   cplx<T>* Ys = Cs + BO * a.cb_ncol;                                    // [BO][nrow_max][NP]
@@ -130,8 +132,10 @@ __global__ void __launch_bounds__(128, N > 36 ? 2 : (MODE == XY_PASS1_DENS ? 3 :
   const int o_begin = a.o_off + g * a.per_group;
   const int o_end = a.o_off + min(a.norb, g * a.per_group + a.per_group);
   // The next batch's column-buffer rows of this plane (cb_ncol is even: 16-byte multiples)
-  // are prefetched into L2 while this batch is transformed.  (Prefetching the orbital-grid
-  // planes too was measured: their lines were evicted before use and re-read, +20 % DRAM.)
+  // are prefetched into L2 while this batch is transformed; the density pass also prefetches
+  // the current batch's orbital-grid planes before its row transforms, which then hide the
+  // HBM latency.  (Prefetching the next batch's grid planes a whole batch ahead was
+  // measured: their lines were evicted before use and re-read, +20 % DRAM.)
   auto prefetch_batch = [&](int obatch) {
     const int t = threadIdx.x;
     if (t < BO && obatch + t < o_end)
@@ -143,6 +147,11 @@ __global__ void __launch_bounds__(128, N > 36 ? 2 : (MODE == XY_PASS1_DENS ? 3 :
     const int nb = min(BO, o_end - ob);
     __syncthreads();
     if (ob + BO < o_end) prefetch_batch(ob + BO);
+    if (MODE == XY_PASS1_DENS && threadIdx.x < nb) {
+      const int o = ob + threadIdx.x;
+      if (a.f_pervec.div(o) == a.dens_vec)
+        prefetch_l2(ur + (long)a.f_pervec.mod(o) * N * plane + iz * plane, (unsigned)(NN * sizeof(cplx<T>)));
+    }
     if (MODE != XY_PASS2) {
       for (int i = threadIdx.x; i < nb * a.cb_ncol; i += blockDim.x) {
         const int b = a.f_ncol.div(i), c = i - b * a.cb_ncol;
@@ -454,18 +463,29 @@ __device__ __forceinline__ void small_dots(const cplx<T>* A, long lda, const cpl
   else block_dots<T>(A, lda, B, ldb, npw, ni, nj, mult, out, red);
 }
 
-// x[v][g] -= sum_w U[w][g] S[w][v] for the nbnd orbitals of one k (S = U^H x).  The
-// coefficients are rounded to T once: conversions from double run on the slow FP64 pipe.
+// The P_c dot block S = U^H x (nbnd x nv): the 4 x 4 shape in registers, others chunked.
+// (A separate dispatcher from small_dots keeps the 8 x 4 KB shape's registers out of the
+// kernels that only project.)
+template <typename T>
+__device__ __forceinline__ void proj_dots(const cplx<T>* A, long lda, const cplx<T>* B, long ldb, int npw, int ni,
+                                          int nj, cplx<double>* out, double* red) {
+  if (ni == 4 && nj == 4) block_dots_fixed<T, 4, 4>(A, lda, B, ldb, npw, nullptr, out, red);
+  else block_dots<T>(A, lda, B, ldb, npw, ni, nj, nullptr, out, red);
+}
+
+// x[v][g] -= sum_w U[w][g] S[w][v] for nv orbitals x of one k against its nbnd occupied
+// states U (S = U^H x, nbnd x nv).  The coefficients are rounded to T once: conversions from
+// double run on the slow FP64 pipe.
 template <typename T>
 __device__ __forceinline__ void subtract_projection(cplx<T>* x, const cplx<T>* uk, const cplx<double>* S, int nbnd,
-                                                    int npw_pad) {
+                                                    int nv, int npw_pad) {
   __shared__ cplx<T> St[32 * 32];
-  for (int i = threadIdx.x; i < nbnd * nbnd; i += blockDim.x) St[i] = mk((T)S[i].x, (T)S[i].y);
+  for (int i = threadIdx.x; i < nbnd * nv; i += blockDim.x) St[i] = mk((T)S[i].x, (T)S[i].y);
   __syncthreads();
-  for (int i = threadIdx.x; i < nbnd * npw_pad; i += blockDim.x) {
+  for (int i = threadIdx.x; i < nv * npw_pad; i += blockDim.x) {
     const int v = i / npw_pad, gi = i - v * npw_pad;
     cplx<T> t = x[i];
-    for (int w = 0; w < nbnd; ++w) t = t - cmul(uk[(long)w * npw_pad + gi], St[w * nbnd + v]);
+    for (int w = 0; w < nbnd; ++w) t = t - cmul(uk[(long)w * npw_pad + gi], St[w * nv + v]);
     x[i] = t;
   }
   __syncthreads();
@@ -481,7 +501,7 @@ __global__ void __launch_bounds__(128) k_project(int nks, int nbnd, int npw_pad,
   const long base = ((long)vec * nks + k) * nbnd * npw_pad;
   const cplx<T>* uk = ukq + (long)k * nbnd * npw_pad;
   block_dots<T>(uk, npw_pad, x + base, npw_pad, npw[k], nbnd, nbnd, nullptr, cf, red);
-  subtract_projection<T>(x + base, uk, cf, nbnd, npw_pad);
+  subtract_projection<T>(x + base, uk, cf, nbnd, nbnd, npw_pad);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -512,62 +532,65 @@ __device__ __forceinline__ double block_mean(const double* p, int n, int stride 
   return t / n;
 }
 
-// Pseudo-Hermitian step j: beta_j from the partials of Re(r_j^H X_j) (every block
-// re-reduces them in the same order), z_j partial, r_{j+1} = P_c(X_j/beta_j - beta_j v_{j-1})
-// formed in shared memory and written to R, v_j = r_j/beta_j.  The sphere columns of r_{j+1}
-// are then inverse-FFT'd along axis 3 by k_zinv (one thread per column line): with the
-// transforms inside this kernel its registers allowed 3 CTAs per SM instead of 4.
-// grid nks, block 256.  smem: r [nbnd][npw_pad], S [nbnd*nbnd] (double complex), scratch.
+// Pseudo-Hermitian step j for one band group of one k-point (P_c, the norm and z act band by
+// band, so groups of bpc bands are independent): beta_j from the ngrp partials per k of
+// Re(r_j^H X_j) (every block re-reduces them in the same order), the group's z_j partial,
+// r_{j+1} = P_c(X_j/beta_j - beta_j v_{j-1}) formed in shared memory and written to R,
+// v_j = r_j/beta_j.  The sphere columns of r_{j+1} are then inverse-FFT'd along axis 3 by
+// k_zinv.  grid (nks, ngrp), block 256.  smem: r [bpc][npw_pad], S [nbnd*bpc] (double
+// complex), reduction scratch.
 template <typename T>
-__global__ void __launch_bounds__(256) k_ph_update(int j, int r_upper, SphereDev s, int nbnd,
+__global__ void __launch_bounds__(256) k_ph_update(int j, int r_upper, SphereDev s, int nbnd, int bpc,
                                                    const double* __restrict__ part, cplx<T>* __restrict__ R,
                                                    const cplx<T>* __restrict__ X, cplx<T>* __restrict__ Vp,
                                                    const cplx<T>* __restrict__ y, const cplx<T>* __restrict__ ukq,
                                                    Coef co, double tol) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int npw_pad = s.npw_pad, nks = s.nks;
+  const int k = blockIdx.x, grp = blockIdx.y, ngrp = gridDim.y;
   cplx<T>* rs = reinterpret_cast<cplx<T>*>(smem_raw);
-  cplx<double>* cf = reinterpret_cast<cplx<double>*>(rs + nbnd * npw_pad);
-  double* red = reinterpret_cast<double*>(cf + nbnd * nbnd);
+  cplx<double>* cf = reinterpret_cast<cplx<double>*>(rs + bpc * npw_pad);
+  double* red = reinterpret_cast<double*>(cf + nbnd * bpc);
   __shared__ double sbeta;
-  const int k = blockIdx.x;
-  const double b2 = block_mean(part, nks);
+  const double b2 = block_mean(part, nks * ngrp) * ngrp;
   if (threadIdx.x == 0) {
     double b = 1.0;
     if (!(b2 > tol)) flag_error(co.err, b2 <= 0.0 ? DEV_NOTPD : DEV_BREAKDOWN, j);
     else b = sqrt(b2);
     sbeta = b;
-    if (k == 0) { co.beta[j - 1] = b; co.gamma[j - 1] = mk(b, 0.0); }
+    if (k == 0 && grp == 0) { co.beta[j - 1] = b; co.gamma[j - 1] = mk(b, 0.0); }
   }
   __syncthreads();
   const double b = sbeta;
-  const long base = (long)k * nbnd * npw_pad;
+  const long base = ((long)k * nbnd + grp * bpc) * npw_pad;
   const int np = s.npw[k];
-  if (r_upper) {  // z_j = (y, r_j)/beta_j, the whole k block as one vector
-    small_dots<T>(y + base, 0, R + base, 0, nbnd * npw_pad, 1, 1, nullptr, cf, red);
-    if (threadIdx.x == 0) co.zpart[(long)(j - 1) * nks + k] = mk(cf[0].x / b, cf[0].y / b);
+  const long zi = (long)(j - 1) * nks * ngrp + (long)k * ngrp + grp;
+  if (r_upper) {  // z_j partial = (y, r_j)/beta_j over the group's bands
+    block_dots_fixed<T, 1, 1>(y + base, 0, R + base, 0, bpc * npw_pad, nullptr, cf, red);
+    if (threadIdx.x == 0) co.zpart[zi] = mk(cf[0].x / b, cf[0].y / b);
   } else if (threadIdx.x == 0) {
-    co.zpart[(long)(j - 1) * nks + k] = mk(0.0, 0.0);
+    co.zpart[zi] = mk(0.0, 0.0);
   }
   const T ib = (T)(1.0 / b), bb = (T)b;
-  for (int i = threadIdx.x; i < nbnd * npw_pad; i += blockDim.x) {
+  for (int i = threadIdx.x; i < bpc * npw_pad; i += blockDim.x) {
     const cplx<T> r = R[base + i];
     rs[i] = X[base + i] * ib - Vp[base + i] * bb;
     Vp[base + i] = r * ib;
   }
   __syncthreads();
-  const cplx<T>* uk = ukq + base;
-  small_dots<T>(uk, npw_pad, rs, npw_pad, np, nbnd, nbnd, nullptr, cf, red);
-  subtract_projection<T>(rs, uk, cf, nbnd, npw_pad);
-  for (int i = threadIdx.x; i < nbnd * npw_pad; i += blockDim.x) R[base + i] = rs[i];
+  const cplx<T>* uk = ukq + (long)k * nbnd * npw_pad;
+  proj_dots<T>(uk, npw_pad, rs, npw_pad, np, nbnd, bpc, cf, red);
+  subtract_projection<T>(rs, uk, cf, nbnd, bpc, npw_pad);
+  for (int i = threadIdx.x; i < bpc * npw_pad; i += blockDim.x) R[base + i] = rs[i];
 }
 
-// Last stage of the operator fused with the per-k projections: forward FFT of the columns
-// along axis 3 and gather of the sphere (1/N^3), + (1/2|k+Q+G|^2 - eps_vk) x, + KB
-// sum_p beta_p D_p <beta_p|x>, then P_c, the output X and the partial Re(x^H X).
-// grid (nks, nvec), block 256.  smem: x, t [nbnd][npw_pad]; coefficients; reduction scratch.
+// Last stage of the operator fused with the per-k projections, for one group of bpc bands of
+// one k-point (the kinetic, KB and P_c terms act band by band): forward FFT of the group's
+// columns along axis 3 and gather of the sphere (1/N^3), + (1/2|k+Q+G|^2 - eps_vk) x, + KB
+// sum_p beta_p D_p <beta_p|x>, then P_c, the output X and the group's partial Re(x^H X).
+// grid (nks, nvec, ngrp), block 256.  smem: x, t [bpc][npw_pad]; coefficients; scratch.
 template <typename T, int N>
-__global__ void __launch_bounds__(256) k_zfwd_proj(SphereDev s, int nbnd, const cplx<T>* __restrict__ cbuf,
+__global__ void __launch_bounds__(256, 2) k_zfwd_proj(SphereDev s, int nbnd, int bpc, const cplx<T>* __restrict__ cbuf,
                                                    int cb_ncol, const cplx<T>* __restrict__ xin,
                                                    const T* __restrict__ kin, const double* __restrict__ eps,
                                                    const cplx<T>* __restrict__ ukq, const cplx<T>* __restrict__ bkq,
@@ -575,19 +598,21 @@ __global__ void __launch_bounds__(256) k_zfwd_proj(SphereDev s, int nbnd, const 
                                                    cplx<T>* __restrict__ xout, double* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int npw_pad = s.npw_pad, nks = s.nks;
-  const int k = blockIdx.x, vec = blockIdx.y;
+  const int k = blockIdx.x, vec = blockIdx.y, grp = blockIdx.z, ngrp = gridDim.z;
+  const int v0 = grp * bpc;
   cplx<T>* xs = reinterpret_cast<cplx<T>*>(smem_raw);
-  cplx<T>* ts = xs + nbnd * npw_pad;
-  cplx<double>* cf = reinterpret_cast<cplx<double>*>(ts + nbnd * npw_pad);   // [max(nproj, nbnd) * nbnd]
-  double* red = reinterpret_cast<double*>(cf + (nproj > nbnd ? nproj : nbnd) * nbnd);
+  cplx<T>* ts = xs + bpc * npw_pad;
+  cplx<double>* cf = reinterpret_cast<cplx<double>*>(ts + bpc * npw_pad);   // [max(nproj, nbnd) * bpc]
+  double* red = reinterpret_cast<double*>(cf + (nproj > nbnd ? nproj : nbnd) * bpc);
   __shared__ T epsk[32];
-  const long base = ((long)vec * nks + k) * nbnd * npw_pad;
+  const long o0 = ((long)vec * nks + k) * nbnd + v0;      // first orbital of the group
+  const long base = o0 * npw_pad;
   const int np = s.npw[k];
   const cplx<T>* bk = bkq + (long)k * nproj * npw_pad;
   const cplx<T>* uk = ukq + (long)k * nbnd * npw_pad;
-  if (threadIdx.x < nbnd) epsk[threadIdx.x] = (T)eps[k * nbnd + threadIdx.x];
+  if (threadIdx.x < bpc) epsk[threadIdx.x] = (T)eps[k * nbnd + v0 + threadIdx.x];
   __syncthreads();
-  for (int i = threadIdx.x; i < nbnd * npw_pad; i += blockDim.x) {
+  for (int i = threadIdx.x; i < bpc * npw_pad; i += blockDim.x) {
     const int v = i / npw_pad, gi = i - v * npw_pad;
     const cplx<T> xv = xin[base + i];
     xs[i] = xv;
@@ -596,11 +621,10 @@ __global__ void __launch_bounds__(256) k_zfwd_proj(SphereDev s, int nbnd, const 
   __syncthreads();
   const int nc = s.ncol[k];
   const T scale = T(1) / T(N * N * N);
-  for (int it = threadIdx.x; it < nbnd * nc; it += blockDim.x) {
+  for (int it = threadIdx.x; it < bpc * nc; it += blockDim.x) {
     const int v = it / nc, c = it - v * nc;
-    const long o = ((long)vec * nks + k) * nbnd + v;
     const int4 cl = s.col[k * s.ncol_max + c];
-    const cplx<T>* src = cbuf + o * (long)N * cb_ncol + c;
+    const cplx<T>* src = cbuf + (o0 + v) * (long)N * cb_ncol + c;
     cplx<T> a[N];
 #pragma unroll
     for (int p = 0; p < N; ++p) a[p] = src[(long)p * cb_ncol];
@@ -614,68 +638,70 @@ __global__ void __launch_bounds__(256) k_zfwd_proj(SphereDev s, int nbnd, const 
   }
   __syncthreads();
   if (nproj > 0) {
-    small_dots<T>(bk, npw_pad, xs, npw_pad, np, nproj, nbnd, dij, cf, red);   // D_p <beta_p|x_v>
+    small_dots<T>(bk, npw_pad, xs, npw_pad, np, nproj, bpc, dij, cf, red);   // D_p <beta_p|x_v>
     cplx<T>* ct = reinterpret_cast<cplx<T>*>(red);    // the coefficients in T (red is free now)
-    for (int i = threadIdx.x; i < nproj * nbnd; i += blockDim.x) ct[i] = mk((T)cf[i].x, (T)cf[i].y);
+    for (int i = threadIdx.x; i < nproj * bpc; i += blockDim.x) ct[i] = mk((T)cf[i].x, (T)cf[i].y);
     __syncthreads();
-    for (int i = threadIdx.x; i < nbnd * npw_pad; i += blockDim.x) {
+    for (int i = threadIdx.x; i < bpc * npw_pad; i += blockDim.x) {
       const int v = i / npw_pad, gi = i - v * npw_pad;
       cplx<T> acc = ts[i];
-      for (int p = 0; p < nproj; ++p) acc = acc + cmul(bk[(long)p * npw_pad + gi], ct[p * nbnd + v]);
+      for (int p = 0; p < nproj; ++p) acc = acc + cmul(bk[(long)p * npw_pad + gi], ct[p * bpc + v]);
       ts[i] = acc;
     }
     __syncthreads();
   }
-  small_dots<T>(uk, npw_pad, ts, npw_pad, np, nbnd, nbnd, nullptr, cf, red);
-  subtract_projection<T>(ts, uk, cf, nbnd, npw_pad);
-  for (int i = threadIdx.x; i < nbnd * npw_pad; i += blockDim.x) xout[base + i] = ts[i];
-  small_dots<T>(xs, 0, ts, 0, nbnd * npw_pad, 1, 1, nullptr, cf, red);
-  if (threadIdx.x == 0) part[vec * nks + k] = cf[0].x;
+  small_dots<T>(uk, npw_pad, ts, npw_pad, np, nbnd, bpc, nullptr, cf, red);
+  subtract_projection<T>(ts, uk, cf, nbnd, bpc, npw_pad);
+  for (int i = threadIdx.x; i < bpc * npw_pad; i += blockDim.x) xout[base + i] = ts[i];
+  small_dots<T>(xs, 0, ts, 0, bpc * npw_pad, 1, 1, nullptr, cf, red);
+  if (threadIdx.x == 0) part[((long)vec * nks + k) * ngrp + grp] = cf[0].x;
 }
 
-// Non-Hermitian step j after the two operator applications XV = L v_j, XW = L^dag w_j:
-// v_hat = P_c(XV - gamma_j v_{j-1}), w_hat = P_c(XW - conj(beta_j) w_{j-1}) (stored in
-// XV, XW), per-k partials of s = (w_hat, v_hat) and of z_j = (y, v_j).  grid nks, block 128.
+// Non-Hermitian step j after the two operator applications XV = L v_j, XW = L^dag w_j, for
+// one group of bpc bands of one k-point: v_hat = P_c(XV - gamma_j v_{j-1}), w_hat =
+// P_c(XW - conj(beta_j) w_{j-1}) (stored in XV, XW), the group's partials of s = (w_hat,
+// v_hat) and of z_j = (y, v_j).  grid (nks, ngrp), block 128.
 template <typename T>
-__global__ void __launch_bounds__(128) k_nh_update(int j, int upper, int nks, int nbnd, int npw_pad,
+__global__ void __launch_bounds__(128) k_nh_update(int j, int upper, int nks, int nbnd, int bpc, int npw_pad,
                                                    const int* __restrict__ npw, cplx<T>* __restrict__ XV,
                                                    cplx<T>* __restrict__ XW, const cplx<T>* __restrict__ Vp,
                                                    const cplx<T>* __restrict__ Wp, const cplx<T>* __restrict__ Vc,
                                                    const cplx<T>* __restrict__ y, const cplx<T>* __restrict__ ukq,
                                                    Coef co, cplx<double>* __restrict__ spart) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cplx<T>* vs = reinterpret_cast<cplx<T>*>(smem_raw);          // [nbnd][npw_pad]
-  cplx<T>* ws = vs + nbnd * npw_pad;
-  cplx<double>* cf = reinterpret_cast<cplx<double>*>(ws + nbnd * npw_pad);   // [nbnd * nbnd]
-  double* red = reinterpret_cast<double*>(cf + nbnd * nbnd);
-  const int k = blockIdx.x;
-  const long base = (long)k * nbnd * npw_pad;
+  cplx<T>* vs = reinterpret_cast<cplx<T>*>(smem_raw);          // [bpc][npw_pad]
+  cplx<T>* ws = vs + bpc * npw_pad;
+  cplx<double>* cf = reinterpret_cast<cplx<double>*>(ws + bpc * npw_pad);   // [nbnd * bpc]
+  double* red = reinterpret_cast<double*>(cf + nbnd * bpc);
+  const int k = blockIdx.x, grp = blockIdx.y, ngrp = gridDim.y;
+  const long base = ((long)k * nbnd + grp * bpc) * npw_pad;
+  const long zi = (long)(j - 1) * nks * ngrp + (long)k * ngrp + grp;
   const int np = npw[k];
   const double bj = co.beta[j - 1];
   const cplx<double> gj = co.gamma[j - 1];
   const cplx<T> g = mk((T)gj.x, (T)gj.y), bc = mk((T)bj, (T)0);
-  if (upper) {  // z_j = (y, v_j), the whole k block as one vector
-    block_dots<T>(y + base, 0, Vc + base, 0, nbnd * npw_pad, 1, 1, nullptr, cf, red);
-    if (threadIdx.x == 0) co.zpart[(long)(j - 1) * nks + k] = cf[0];
+  if (upper) {  // z_j partial = (y, v_j) over the group's bands
+    block_dots<T>(y + base, 0, Vc + base, 0, bpc * npw_pad, 1, 1, nullptr, cf, red);
+    if (threadIdx.x == 0) co.zpart[zi] = cf[0];
   } else if (threadIdx.x == 0) {
-    co.zpart[(long)(j - 1) * nks + k] = mk(0.0, 0.0);
+    co.zpart[zi] = mk(0.0, 0.0);
   }
-  for (int i = threadIdx.x; i < nbnd * npw_pad; i += blockDim.x) {
+  for (int i = threadIdx.x; i < bpc * npw_pad; i += blockDim.x) {
     vs[i] = XV[base + i] - cmul(g, Vp[base + i]);
     ws[i] = XW[base + i] - cmul(bc, Wp[base + i]);
   }
   __syncthreads();
-  const cplx<T>* uk = ukq + base;
-  block_dots<T>(uk, npw_pad, vs, npw_pad, np, nbnd, nbnd, nullptr, cf, red);
-  subtract_projection<T>(vs, uk, cf, nbnd, npw_pad);
-  block_dots<T>(uk, npw_pad, ws, npw_pad, np, nbnd, nbnd, nullptr, cf, red);
-  subtract_projection<T>(ws, uk, cf, nbnd, npw_pad);
-  for (int i = threadIdx.x; i < nbnd * npw_pad; i += blockDim.x) {
+  const cplx<T>* uk = ukq + (long)k * nbnd * npw_pad;
+  block_dots<T>(uk, npw_pad, vs, npw_pad, np, nbnd, bpc, nullptr, cf, red);
+  subtract_projection<T>(vs, uk, cf, nbnd, bpc, npw_pad);
+  block_dots<T>(uk, npw_pad, ws, npw_pad, np, nbnd, bpc, nullptr, cf, red);
+  subtract_projection<T>(ws, uk, cf, nbnd, bpc, npw_pad);
+  for (int i = threadIdx.x; i < bpc * npw_pad; i += blockDim.x) {
     XV[base + i] = vs[i];
     XW[base + i] = ws[i];
   }
-  block_dots<T>(ws, 0, vs, 0, nbnd * npw_pad, 1, 1, nullptr, cf, red);
-  if (threadIdx.x == 0) spart[k] = cf[0];
+  block_dots<T>(ws, 0, vs, 0, bpc * npw_pad, 1, 1, nullptr, cf, red);
+  if (threadIdx.x == 0) spart[(long)k * ngrp + grp] = cf[0];
 }
 
 // Non-Hermitian normalisation at the end of step j: beta_{j+1} = sqrt|s|, gamma_{j+1} =

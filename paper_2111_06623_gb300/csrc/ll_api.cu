@@ -24,10 +24,73 @@ int fail(int code, const std::string& msg) {
 }
 }  // namespace
 
+// ---------------------------------------------------------------------------------------
+// FMA throughput of the device: every thread runs 8 independent chains x <- x*m + c for
+// `iters` iterations (8 * iters FMAs, 2 flops each).  The multiplier is 1 - 2^-20 and the
+// addend small, so the chains stay finite; one store per thread, predicated on a value that
+// never occurs, keeps the work from being removed.
+namespace {
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_peak(int iters, T m, T c, T* sink) {
+  T x[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) x[q] = T(threadIdx.x + q);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) x[q] = fma(x[q], m, c);
+  }
+  T t = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) t += x[q];
+  if (t == T(-1.25)) sink[blockIdx.x * blockDim.x + threadIdx.x] = t;
+}
+
+template <typename T>
+int fma_peak(double* tflops, cudaStream_t st) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return fail(LL_ECUDA, "ll_fma_peak: device query");
+  const int blocks = sms * 8, threads = 256, iters = sizeof(T) == 4 ? 16384 : 1024;
+  T* sink = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaMalloc(&sink, sizeof(T) * blocks * threads) != cudaSuccess) return fail(LL_ENOMEM, "ll_fma_peak: allocation");
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const T m = T(1) - T(1) / T(1 << 20), c = T(1) / T(1 << 10);
+  k_fma_peak<T><<<blocks, threads, 0, st>>>(iters / 8, m, c, sink);   // warm-up
+  float best = 1e30f;
+  for (int rep = 0; rep < 3; ++rep) {
+    cudaEventRecord(e0, st);
+    k_fma_peak<T><<<blocks, threads, 0, st>>>(iters, m, c, sink);
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    best = ms < best ? ms : best;
+  }
+  cudaError_t e = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(sink);
+  if (e != cudaSuccess) return fail(LL_ECUDA, std::string("ll_fma_peak: ") + cudaGetErrorString(e));
+  *tflops = 2.0 * 8.0 * iters * (double)blocks * threads / (best * 1e-3) / 1e12;
+  return LL_OK;
+}
+}  // namespace
+
+
 extern "C" {
 
 const char* ll_last_error(void) { return g_err.c_str(); }
 const char* ll_version(void) { return "ll-gb300 1.0 (sm_103a)"; }
+
+int ll_fma_peak(int precision, double* tflops, void* stream) {
+  if (!tflops) return fail(LL_EINVAL, "null output");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (precision == LL_PREC_FP32) return fma_peak<float>(tflops, st);
+  if (precision == LL_PREC_FP64) return fma_peak<double>(tflops, st);
+  return fail(LL_EINVAL, "bad precision");
+}
 
 int ll_create(const ll_system_desc* desc, void* stream, ll_handle** out) {
   if (!desc || !out) return fail(LL_EINVAL, "null descriptor or output");
@@ -57,10 +120,14 @@ int ll_destroy(ll_handle* h) {
   return LL_OK;
 }
 
-int ll_lanczos(ll_handle* h, int n_steps, double* beta, double* gamma, double* z, int* steps_done) {
+int ll_lanczos(ll_handle* h, int n_steps, double* alpha, double* beta, double* gamma, double* z, int* steps_done) {
   if (!h) return fail(LL_EINVAL, "null handle");
   std::string err;
-  int rc = h->chain->lanczos(n_steps, beta, gamma, z, steps_done, err);
+  int done = 0;
+  int rc = h->chain->lanczos(n_steps, beta, gamma, z, &done, err);
+  if (steps_done) *steps_done = done;
+  if (alpha)
+    for (int i = 0; i < done; ++i) alpha[i] = 0.0;
   return rc == LL_OK ? LL_OK : fail(rc, "ll_lanczos: " + err);
 }
 

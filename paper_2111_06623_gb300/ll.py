@@ -50,7 +50,7 @@ def _load():
     sig = {
         "ll_create": (C.c_int, [C.POINTER(SystemDesc), vp, C.POINTER(vp)]),
         "ll_destroy": (C.c_int, [vp]),
-        "ll_lanczos": (C.c_int, [vp, C.c_int, _dp, _dp, _dp, _ip]),
+        "ll_lanczos": (C.c_int, [vp, C.c_int, _dp, _dp, _dp, _dp, _ip]),
         "ll_lanczos_spectrum": (C.c_int, [vp, C.c_int, _dp, C.c_int, C.c_double, _dp, _dp, _dp]),
         "ll_spectrum": (C.c_int, [_dp, _dp, _dp, C.c_int, C.c_double, _dp, _dp, C.c_int, C.c_double, _dp, _dp, _dp, vp]),
         "ll_spectrum_static": (C.c_int, [_dp, _dp, _dp, C.c_int, C.c_double, _dp, _dp, C.c_int, C.c_double, _dp,
@@ -74,6 +74,7 @@ def _load():
         "ll_server_destroy": (C.c_int, [vp]),
         "ll_last_error": (C.c_char_p, []),
         "ll_version": (C.c_char_p, []),
+        "ll_fma_peak": (C.c_int, [C.c_int, _dp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -85,7 +86,7 @@ _lib = _load()
 EXPORTS = ("ll_create", "ll_destroy", "ll_lanczos", "ll_lanczos_spectrum", "ll_spectrum", "ll_spectrum_static",
            "ll_lanczos_spectrum_x", "ll_spectrum_x",
            "ll_apply", "ll_get_map", "ll_get_start", "ll_footprint", "ll_profile", "ll_profile_read", "ll_last_error",
-           "ll_version", "ll_server_create",
+           "ll_version", "ll_fma_peak", "ll_server_create",
            "ll_server_set_chunk", "ll_submit", "ll_poll", "ll_server_stats", "ll_server_last_error",
            "ll_server_destroy")
 PROF_CLASSES = ("zinv", "xy1", "hxc", "xy2", "zfwd", "update")
@@ -93,6 +94,13 @@ PROF_CLASSES = ("zinv", "xy1", "hxc", "xy2", "zfwd", "update")
 
 def version() -> str:
     return _lib.ll_version().decode()
+
+
+def fma_peak(precision: str = "fp32", stream=None) -> float:
+    """Measured FMA throughput of the device, TFLOP/s (ll_fma_peak)."""
+    out = C.c_double(0.0)
+    _check(_lib.ll_fma_peak(PRECISION[precision], C.byref(out), C.c_void_p(stream) if stream else None))
+    return float(out.value)
 
 
 def _check(rc: int):
@@ -176,15 +184,18 @@ class Chain:
             pass
 
     def lanczos(self, n_steps: int):
-        """Runs n_steps more steps; returns (beta, gamma, z) of every step so far."""
+        """Runs n_steps more steps; returns (beta, gamma, z) of every step so far (the
+        vanishing diagonal alpha of every step so far is kept in self.alpha)."""
         cap = self.max_steps
+        alpha = np.full(cap, np.nan)
         beta = np.zeros(cap)
         gamma = np.zeros(cap, dtype=np.complex128)
         z = np.zeros(cap, dtype=np.complex128)
         done = C.c_int(0)
-        rc = _lib.ll_lanczos(self._h, int(n_steps), _d(beta), _d(gamma.view(np.float64)), _d(z.view(np.float64)),
-                             C.byref(done))
+        rc = _lib.ll_lanczos(self._h, int(n_steps), _d(alpha), _d(beta), _d(gamma.view(np.float64)),
+                             _d(z.view(np.float64)), C.byref(done))
         self.steps = done.value
+        self.alpha = alpha[: done.value].copy()
         if rc != LL_OK:
             err = LLError(rc, _lib.ll_last_error().decode())
             err.partial = (beta[: done.value], gamma[: done.value], z[: done.value])

@@ -119,6 +119,7 @@ def test_ph_coefficients_small_fp64(lib, small):
     ch = chain_from_bundle(small, max_steps=300)
     got = ch.lanczos(300)
     assert _coef_rel(got, ref, 100) < 1e-10
+    assert np.array_equal(ch.alpha, np.zeros(300))   # T has a zero diagonal (one SBR half per vector)
     assert _loss_err(got, (ref.beta, ref.gamma, ref.z), small.spec.omega, small.spec.q_cart) < 1e-3
 
 
@@ -241,8 +242,7 @@ def cubic8():
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
 def test_cubic8_single_application(lib, cubic8, precision, tol):
-    """Eight-atom cell (16 bands, ~1630 plane waves, 1024 orbitals): its k blocks exceed one
-    CTA's shared memory, so the chain takes the split path by itself."""
+    """Eight-atom cell (16 bands, ~1630 plane waves, 1024 orbitals): 16 per-k CTAs per k-point."""
     sys = System(cubic8)
     ch = chain_from_bundle(cubic8, precision=precision, max_steps=4)
     x = _rand(sys, 13)
@@ -260,7 +260,7 @@ def test_cubic8_first_coefficients(lib, cubic8):
 
 
 def test_cubic8_non_hermitian(lib, cubic8):
-    """The non-Hermitian recursion on the split path (update cut into two chunked kernels)."""
+    """The non-Hermitian recursion on the eight-atom cell."""
     sys = System(cubic8)
     ref = lanczos.non_hermitian(sys, 5)
     got = chain_from_bundle(cubic8, flavour="nh", max_steps=5).lanczos(5)

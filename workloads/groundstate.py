@@ -370,12 +370,13 @@ def cache_dir() -> str:
 
 
 def save_bundle(b: Bundle, path: str) -> None:
+    """The projectors beta_kq are not stored: they are a closed form of the spec and the
+    spheres, rebuilt on load (half the file for the cells with many projectors)."""
     arrs = dict(kfrac=b.kfrac, kcart=b.kcart, eps_k=b.eps_k, eps_kq=b.eps_kq, vloc_r=b.vloc_r,
                 rho_r=b.rho_r, dij=b.dij, scf_iters=b.scf_iters, gap_min=b.gap_min,
                 npw_k=b.npw_k, npw_kq=b.npw_kq,
                 miller_k=np.concatenate(b.miller_k), miller_kq=np.concatenate(b.miller_kq),
-                u_k=np.concatenate([u.T for u in b.u_k]), u_kq=np.concatenate([u.T for u in b.u_kq]),
-                beta_kq=np.concatenate([x.T for x in b.beta_kq]))
+                u_k=np.concatenate([u.T for u in b.u_k]), u_kq=np.concatenate([u.T for u in b.u_kq]))
     np.savez(path, **arrs)
 
 
@@ -385,14 +386,18 @@ def load_bundle(spec: SystemSpec, path: str) -> Bundle:
     sk, sq = np.concatenate([[0], np.cumsum(npk)]), np.concatenate([[0], np.cumsum(npq)])
     sl = lambda a, s, i: a[s[i]:s[i + 1]]
     nks = len(npk)
+    if "beta_kq" in z.files:          # files written before the projectors were rebuilt on load
+        beta = [np.ascontiguousarray(sl(z["beta_kq"], sq, i).T) for i in range(nks)]
+    else:
+        kq = z["kcart"] + spec.q_cart[None, :]
+        beta = [kb_projectors(spec, kq[i], sl(z["miller_kq"], sq, i))[0] for i in range(nks)]
     return Bundle(spec=spec, kfrac=z["kfrac"], kcart=z["kcart"],
                   miller_k=[sl(z["miller_k"], sk, i) for i in range(nks)],
                   miller_kq=[sl(z["miller_kq"], sq, i) for i in range(nks)],
                   u_k=[np.ascontiguousarray(sl(z["u_k"], sk, i).T) for i in range(nks)],
                   u_kq=[np.ascontiguousarray(sl(z["u_kq"], sq, i).T) for i in range(nks)],
                   eps_k=z["eps_k"], eps_kq=z["eps_kq"], vloc_r=z["vloc_r"], rho_r=z["rho_r"],
-                  beta_kq=[np.ascontiguousarray(sl(z["beta_kq"], sq, i).T) for i in range(nks)],
-                  dij=z["dij"], scf_iters=int(z["scf_iters"]), gap_min=float(z["gap_min"]))
+                  beta_kq=beta, dij=z["dij"], scf_iters=int(z["scf_iters"]), gap_min=float(z["gap_min"]))
 
 
 def cached_bundle(spec: SystemSpec) -> Bundle | None:
