@@ -305,7 +305,9 @@ class Chain : public ChainBase {
       bpc_ = best > 0 ? best : nbnd_;
       ngrp_ = nbnd_ / bpc_;
       const char* env = getenv("LL_SPLIT_PERK");
-      split_ = best == 0 || (env && env[0] == '1' && env[1] == 0);
+      // the chunked path also where the band groups are small: per-group CTAs would read the
+      // projectors and U_{k+Q} once per group (32 times per k on the 16-atom cell)
+      split_ = best == 0 || 4 * best < nbnd_ || (env && env[0] == '1' && env[1] == 0);
       nchunk_ = split_ ? (pq + kChunk - 1) / kChunk : 1;
       npk_ = split_ ? nchunk_ : ngrp_;
     }
@@ -324,7 +326,8 @@ class Chain : public ChainBase {
       return rc;
     // chunk partials: U^H x per vector (two per vector on the non-Hermitian update), B^H x
     if (split_ && ((rc = alloc(&sp_s_, 2 * nzv * nbnd_ * nbnd_)) || (rc = alloc(&sp_c_, nzv * std::max(1, nproj_ * nbnd_))) ||
-                   (rc = alloc(&ub_, (long)nks_ * nbnd_ * std::max(1, nproj_)))))
+                   (rc = alloc(&ub_, (long)nks_ * nbnd_ * std::max(1, nproj_))) ||
+                   (rc = alloc(&sp_coef_, nvec_ * (long)nks_ * (nproj_ + nbnd_) * nbnd_))))
       return rc;
     (void)err;
     LL_CK(cudaMemcpyAsync(whart_, wh.data(), n3 * sizeof(T), cudaMemcpyHostToDevice, st_));
@@ -436,7 +439,7 @@ class Chain : public ChainBase {
         // update of the Lanczos vectors fused with the axis-3 inverse FFT of r_{j+1}
         const int u0 = prof_.mark(st_);
         if ((rc = launch_zinv_ph(j, err))) return rc;
-        prof_.count(LL_PROF_ZINV, 2);
+        prof_.count(LL_PROF_ZINV, split_ ? 4 : 2);
         prof_.span(LL_PROF_ZINV, u0, prof_.mark(st_));
         // r_{j+1} is upper when j is odd; the upper half gets D + K
         const int dens = (j % 2 == 1 && approx_ != LL_APPROX_IPA) ? 0 : -1;
@@ -620,7 +623,7 @@ class Chain : public ChainBase {
       prof_.span(LL_PROF_XY2, e3, e2);
     }
     if ((rc = launch_zfwd_proj(nvec, in, out, err))) return rc;
-    prof_.count(LL_PROF_ZFWD, split_ ? 3 : 1);
+    prof_.count(LL_PROF_ZFWD, split_ ? 4 : 1);
     prof_.span(LL_PROF_ZFWD, e2, prof_.mark(st_));
     return LL_OK;
   }
@@ -661,14 +664,17 @@ class Chain : public ChainBase {
     const int lines = (nbnd_ * hq_.ncol_max + kLines - 1) / kLines;
     k_sp_zfwd<T, N><<<dim3(nks_, nvec, lines), kLines, 0, st_>>>(dq_, nbnd_, cbuf_, cb_ncol_, in, kin_, eps_, out);
     const size_t sm_d = (size_t)(std::max(nproj_, nbnd_) + nbnd_) * kTileP * sizeof(cplx<T>);
-    const size_t sm_a = (size_t)nproj_ * nbnd_ * (sizeof(cplx<double>) + sizeof(cplx<T>)) +
-                        (size_t)nbnd_ * nbnd_ * sizeof(cplx<T>);
+    const size_t sm_a = (size_t)(nproj_ + nbnd_) * (nbnd_ + kSub) * sizeof(cplx<T>);
     int rc;
-    if ((rc = set_smem(k_sp_dots<T>, sm_d, err)) || (rc = set_smem(k_sp_apply<T>, sm_a, err))) return rc;
+    const size_t sm_c = (size_t)nproj_ * nbnd_ * sizeof(cplx<double>);
+    if ((rc = set_smem(k_sp_dots<T>, sm_d, err)) || (rc = set_smem(k_sp_coef<T>, sm_c, err)) ||
+        (rc = set_smem(k_sp_apply<T>, sm_a, err)))
+      return rc;
     k_sp_dots<T><<<dim3(nks_, nvec, nchunk_), 256, sm_d, st_>>>(nks_, nbnd_, pq, dq_.npw, nchunk_, nproj_, in, out,
                                                                 ukq_, bkq_, sp_c_, sp_s_);
+    k_sp_coef<T><<<nks_ * nvec, 256, sm_c, st_>>>(nks_, nbnd_, nchunk_, nproj_, dij_, ub_, sp_c_, sp_s_, sp_coef_);
     k_sp_apply<T><<<dim3(nks_, nvec, nchunk_), 256, sm_a, st_>>>(nks_, nbnd_, pq, dq_.npw, nchunk_, nproj_, in, out,
-                                                                 ukq_, bkq_, dij_, ub_, sp_c_, sp_s_, part_);
+                                                                 ukq_, bkq_, sp_coef_, part_);
     LL_CK(cudaGetLastError());
     return LL_OK;
   }
@@ -681,9 +687,14 @@ class Chain : public ChainBase {
     Coef co{beta_, gamma_, zpart_, err_};
     k_sp_start<T><<<dim3(nks_, nchunk_), 256, sm, st_>>>(j, (j % 2 == 0) ? 1 : 0, nks_, nbnd_, pq, dq_.npw, nchunk_,
                                                          part_, R(), X(), Vp(), y_, ukq_, co, tol_, sp_s_);
-    const int lines = (nbnd_ * hq_.ncol_max + kLines - 1) / kLines;
-    k_sp_proj_cols<T, N><<<dim3(nks_, lines), kLines, 0, st_>>>(dq_, nbnd_, nchunk_, sp_s_, R(), ukq_, cbuf_,
-                                                                cb_ncol_);
+    // P_c with the chunk-reduced coefficients, tiled (U read once per chunk for all bands),
+    // then the axis-3 inverse FFTs over many CTAs per k
+    const size_t sm_a = (size_t)nbnd_ * (nbnd_ + kSub) * sizeof(cplx<T>);
+    if ((rc = set_smem(k_sp_apply<T>, sm_a, err))) return rc;
+    k_sp_coef<T><<<nks_, 256, 0, st_>>>(nks_, nbnd_, nchunk_, 0, dij_, ub_, sp_c_, sp_s_, sp_coef_);
+    k_sp_apply<T><<<dim3(nks_, 1, nchunk_), 256, sm_a, st_>>>(nks_, nbnd_, pq, dq_.npw, nchunk_, 0, nullptr, R(), ukq_,
+                                                              bkq_, sp_coef_, nullptr);
+    k_zinv<T, N><<<dim3(nks_, 1, zsplit()), 128, 0, st_>>>(dq_, R(), nbnd_, cbuf_, cb_ncol_);
     LL_CK(cudaGetLastError());
     return LL_OK;
   }
@@ -698,7 +709,7 @@ class Chain : public ChainBase {
     if ((rc = set_smem(k_ph_update<T>, smem, err))) return rc;
     k_ph_update<T><<<dim3(nks_, ngrp_), 256, smem, st_>>>(j, (j % 2 == 0) ? 1 : 0, dq_, nbnd_, bpc_, part_, R(), X(),
                                                           Vp(), y_, ukq_, co, tol_);
-    k_zinv<T, N><<<dim3(nks_, 1), 128, 0, st_>>>(dq_, R(), nbnd_, cbuf_, cb_ncol_);
+    k_zinv<T, N><<<dim3(nks_, 1, zsplit()), 128, 0, st_>>>(dq_, R(), nbnd_, cbuf_, cb_ncol_);
     LL_CK(cudaGetLastError());
     return LL_OK;
   }
@@ -715,9 +726,11 @@ class Chain : public ChainBase {
     return LL_EUNSUPPORTED;
   }
 
+  // CTAs per k-block of the axis-3 inverse FFTs: one per 1024 column lines
+  int zsplit() const { return std::max(1, nbnd_ * std::max(hk_.ncol_max, hq_.ncol_max) / 1024); }
   template <int N>
   int zinv_n(const SphereDev& s, const cplx<T>* in, int nvec) {
-    k_zinv<T, N><<<dim3(nks_, nvec), 128, 0, st_>>>(s, in, nbnd_, cbuf_, cb_ncol_);
+    k_zinv<T, N><<<dim3(nks_, nvec, zsplit()), 128, 0, st_>>>(s, in, nbnd_, cbuf_, cb_ncol_);
     return cudaGetLastError() == cudaSuccess ? LL_OK : LL_ECUDA;
   }
   int launch_zinv(const SphereDev& s, const cplx<T>* in, int nvec) {
@@ -952,6 +965,7 @@ class Chain : public ChainBase {
   int bpc_ = 1, ngrp_ = 1;  // bands per CTA of the per-k kernels, band groups per k
   int npk_ = 1;             // partial sums per k of the Lanczos scalars (ngrp_, or nchunk_ split)
   cplx<double> *sp_s_ = nullptr, *sp_c_ = nullptr, *ub_ = nullptr;   // chunk partials of U^H r, B^H x; U^H B
+  cplx<T>* sp_coef_ = nullptr;   // reduced KB and P_c coefficients per (vector, k) of the split apply
   double* spec_w_ = nullptr;
   int *map_ = nullptr, *err_ = nullptr;
 };

@@ -33,13 +33,14 @@ __device__ __forceinline__ int wrapn(int m) { return (int)((unsigned)(m + N) % (
 
 // ---------------------------------------------------------------------------------------
 // Sphere -> columns: scatter each column's points and inverse-FFT along axis 3.
-// grid (nks, nvec), block 128; item = (v, column).
+// grid (nks, nvec, split), block 128; item = (v, column), the k block's items spread over
+// the split CTAs.
 template <typename T, int N>
 __global__ void __launch_bounds__(128) k_zinv(SphereDev s, const cplx<T>* __restrict__ x, int nbnd,
                                               cplx<T>* __restrict__ cbuf, int cb_ncol) {
   const int k = blockIdx.x, vec = blockIdx.y;
   const int nc = s.ncol[k];
-  for (int it = threadIdx.x; it < nbnd * nc; it += blockDim.x) {
+  for (int it = blockIdx.z * blockDim.x + threadIdx.x; it < nbnd * nc; it += blockDim.x * gridDim.z) {
     const int v = it / nc, c = it - v * nc;
     const long o = ((long)vec * s.nks + k) * nbnd + v;
     const int4 cl = s.col[k * s.ncol_max + c];

@@ -9,9 +9,11 @@
 // the chunks in a fixed order (deterministic, no atomics).
 //
 // One pseudo-Hermitian step here: k_sp_start (beta_j, z_j partial, r_{j+1} before P_c,
-// partial U^H r) -> k_sp_proj_cols (P_c, axis-3 inverse FFT) -> planes and response
+// partial U^H r) -> k_sp_coef, k_sp_apply (P_c) -> k_zinv (axis-3 inverse FFT over several
+// CTAs per k) -> planes and response
 // potential as in the fused path -> k_sp_zfwd (axis-3 forward FFT, gather, kinetic - eps)
-// -> k_sp_dots (partial B^H x, U^H t) -> k_sp_apply (KB, P_c, output, norm partial).
+// -> k_sp_dots (partial B^H x, U^H t) -> k_sp_coef (coefficients) -> k_sp_apply (KB, P_c,
+// output, norm partial).
 #pragma once
 #include "kernels.cuh"
 
@@ -147,59 +149,6 @@ __global__ void __launch_bounds__(256) k_sp_start(int j, int r_upper, int nks, i
                 spart + ((long)k * nchunk + c) * nbnd * nbnd);
 }
 
-// S = sum over chunks of the partials (fixed order), rounded to T into St[w*nbnd + v].
-template <typename T>
-__device__ __forceinline__ void reduce_coef(const cplx<double>* part, int nchunk, int np, cplx<T>* St,
-                                            const double* mult = nullptr, int nj = 1) {
-  for (int p = threadIdx.x; p < np; p += blockDim.x) {
-    double re = 0.0, im = 0.0;
-    for (int c = 0; c < nchunk; ++c) {
-      re += part[(long)c * np + p].x;
-      im += part[(long)c * np + p].y;
-    }
-    const double m = mult ? mult[p / nj] : 1.0;
-    St[p] = mk((T)(re * m), (T)(im * m));
-  }
-}
-
-// Step j, second part: R <- P_c R (coefficients from the chunk partials), then the sphere
-// columns of R inverse-FFT'd along axis 3 into the column buffer.  One thread per column line
-// (band v, column c); grid (nks, ceil(nbnd ncol_max / kLines)), block kLines.
-template <typename T, int N>
-__global__ void __launch_bounds__(kLines) k_sp_proj_cols(SphereDev s, int nbnd, int nchunk,
-                                                         const cplx<double>* __restrict__ spart,
-                                                         cplx<T>* __restrict__ R, const cplx<T>* __restrict__ ukq,
-                                                         cplx<T>* __restrict__ cbuf, int cb_ncol) {
-  __shared__ cplx<T> St[32 * 32];
-  const int k = blockIdx.x, npw_pad = s.npw_pad;
-  reduce_coef<T>(spart + (long)k * nchunk * nbnd * nbnd, nchunk, nbnd * nbnd, St);
-  __syncthreads();
-  const int nc = s.ncol[k];
-  const int it = blockIdx.y * kLines + threadIdx.x;
-  if (it >= nbnd * nc) return;
-  const int v = it / nc, c = it - v * nc;
-  const int4 cl = s.col[k * s.ncol_max + c];
-  const long base = (long)k * nbnd * npw_pad;
-  cplx<T>* r = R + base + (long)v * npw_pad + s.colstart[k * s.ncol_max + c];
-  const cplx<T>* u = ukq + base + s.colstart[k * s.ncol_max + c];
-  cplx<T> a[N];
-#pragma unroll
-  for (int p = 0; p < N; ++p) {
-    const int i = wrapn<N>(p - cl.z);
-    cplx<T> val = czero<T>();
-    if (i < cl.w) {
-      val = r[i];
-      for (int w = 0; w < nbnd; ++w) val = val - cmul(u[(long)w * npw_pad + i], St[w * nbnd + v]);
-      r[i] = val;
-    }
-    a[p] = val;
-  }
-  fft_line<T, N, +1>(a);
-  cplx<T>* dst = cbuf + ((long)k * nbnd + v) * N * cb_ncol + c;
-#pragma unroll
-  for (int p = 0; p < N; ++p) dst[(long)p * cb_ncol] = a[p];
-}
-
 // Operator, last stage, first part: forward FFT of the columns along axis 3, gather of the
 // sphere (1/N^3) plus (1/2|k+Q+G|^2 - eps_vk) x into t = out.  grid (nks, nvec, lines).
 template <typename T, int N>
@@ -253,40 +202,30 @@ __global__ void __launch_bounds__(256) k_sp_dots(int nks, int nbnd, int npw_pad,
                 spart + (kv * nchunk + c) * nbnd * nbnd);
 }
 
-// Operator, last stage, second part: c = D o (B^H x), S = U^H t + (U^H B) c, then
-// t <- t + B c - U S (= P_c (t + B c)), zero on the padding, and the chunk's partial
-// Re(x^H t).  ub: U^H B per k, [nbnd][nproj] (double).  grid (nks, nvec, nchunk), block 256;
-// dynamic shared memory nproj nbnd (16 + sizeof(cplx<T>)) + nbnd^2 sizeof(cplx<T>) bytes.
+// Operator, last stage: the coefficients of one (vector, k), reduced over the chunks in a fixed
+// order: c = D o (B^H x) (nproj x nbnd) and S = U^H t + (U^H B) c (nbnd x nbnd), rounded to T
+// into coef[kv] = [c | S].  ub: U^H B per k, [nbnd][nproj] (double).  grid nks * nvec, block 256.
 template <typename T>
-__global__ void __launch_bounds__(256) k_sp_apply(int nks, int nbnd, int npw_pad, const int* __restrict__ npw,
-                                                  int nchunk, int nproj, const cplx<T>* __restrict__ xin,
-                                                  cplx<T>* __restrict__ t, const cplx<T>* __restrict__ ukq,
-                                                  const cplx<T>* __restrict__ bkq, const double* __restrict__ dij,
-                                                  const cplx<double>* __restrict__ ub,
-                                                  const cplx<double>* __restrict__ cpart,
-                                                  const cplx<double>* __restrict__ spart, double* __restrict__ part) {
+__global__ void __launch_bounds__(256) k_sp_coef(int nks, int nbnd, int nchunk, int nproj,
+                                                 const double* __restrict__ dij, const cplx<double>* __restrict__ ub,
+                                                 const cplx<double>* __restrict__ cpart,
+                                                 const cplx<double>* __restrict__ spart, cplx<T>* __restrict__ coef) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cplx<double>* cd = reinterpret_cast<cplx<double>*>(smem_raw);     // [nproj * nbnd]
-  cplx<T>* ct = reinterpret_cast<cplx<T>*>(cd + nproj * nbnd);       // [nproj * nbnd]
-  cplx<T>* St = ct + nproj * nbnd;                                    // [nbnd * nbnd]
-  __shared__ double wred[8];
-  const int k = blockIdx.x, vec = blockIdx.y, c = blockIdx.z;
-  const long kv = (long)vec * nks + k;
-  const int np = npw[k];
-  const int g0 = c * kChunk, g1 = min(npw_pad, g0 + kChunk);
-  if (nproj > 0) {
-    for (int p = threadIdx.x; p < nproj * nbnd; p += blockDim.x) {
-      double re = 0.0, im = 0.0;
-      for (int cc = 0; cc < nchunk; ++cc) {
-        re += cpart[(kv * nchunk + cc) * nproj * nbnd + p].x;
-        im += cpart[(kv * nchunk + cc) * nproj * nbnd + p].y;
-      }
-      const double m = dij[p / nbnd];
-      cd[p] = mk(re * m, im * m);
-      ct[p] = mk((T)(re * m), (T)(im * m));
+  cplx<double>* cd = reinterpret_cast<cplx<double>*>(smem_raw);   // [nproj * nbnd]
+  const long kv = blockIdx.x;
+  const int k = (int)(kv % nks);
+  cplx<T>* out = coef + kv * (long)(nproj + nbnd) * nbnd;
+  for (int p = threadIdx.x; p < nproj * nbnd; p += blockDim.x) {
+    double re = 0.0, im = 0.0;
+    for (int cc = 0; cc < nchunk; ++cc) {
+      re += cpart[(kv * nchunk + cc) * nproj * nbnd + p].x;
+      im += cpart[(kv * nchunk + cc) * nproj * nbnd + p].y;
     }
-    __syncthreads();
+    const double m = dij[p / nbnd];
+    cd[p] = mk(re * m, im * m);
+    out[p] = mk((T)(re * m), (T)(im * m));
   }
+  __syncthreads();
   for (int p = threadIdx.x; p < nbnd * nbnd; p += blockDim.x) {
     double re = 0.0, im = 0.0;
     for (int cc = 0; cc < nchunk; ++cc) {
@@ -299,33 +238,76 @@ __global__ void __launch_bounds__(256) k_sp_apply(int nks, int nbnd, int npw_pad
       re += a.x * d.x - a.y * d.y;
       im += a.x * d.y + a.y * d.x;
     }
-    St[p] = mk((T)re, (T)im);
+    out[nproj * nbnd + p] = mk((T)re, (T)im);
   }
-  __syncthreads();
+}
+
+// Operator, last stage, applied: t <- t + B c - U S (= P_c (t + B c)) on one chunk of plane
+// waves of one (vector, k), zero on the padding, and the chunk's partial Re(x^H t).  The chunk
+// is walked in sub-tiles of kSub plane waves: the sub-tile's projector and occupied-state
+// values (nproj + nbnd rows) are staged in shared memory once and serve every band, so each
+// is read from L2 once per chunk instead of once per band.  Thread t takes plane wave
+// t % kSub of the sub-tile and bands t / kSub, t / kSub + 256 / kSub, ...
+// grid (nks, nvec, nchunk), block 256; dynamic smem (nproj + nbnd) (kSub + nbnd) complex T.
+constexpr int kSub = 64;
+template <typename T>
+__global__ void __launch_bounds__(256) k_sp_apply(int nks, int nbnd, int npw_pad, const int* __restrict__ npw,
+                                                  int nchunk, int nproj, const cplx<T>* __restrict__ xin,
+                                                  cplx<T>* __restrict__ t, const cplx<T>* __restrict__ ukq,
+                                                  const cplx<T>* __restrict__ bkq, const cplx<T>* __restrict__ coef,
+                                                  double* __restrict__ part) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int VS = 256 / kSub;                                   // band strides per sub-tile
+  cplx<T>* Ct = reinterpret_cast<cplx<T>*>(smem_raw);             // [nproj][nbnd] then [nbnd][nbnd]
+  cplx<T>* Bt = Ct + (nproj + nbnd) * nbnd;                        // [nproj][kSub] then [nbnd][kSub]
+  __shared__ double wred[8];
+  const int k = blockIdx.x, vec = blockIdx.y, c = blockIdx.z;
+  const long kv = (long)vec * nks + k;
+  const int np = npw[k];
+  const int g0 = c * kChunk, g1 = min(npw_pad, g0 + kChunk);
+  const int nrow = nproj + nbnd;
+  const cplx<T>* cf = coef + kv * (long)nrow * nbnd;
+  for (int i = threadIdx.x; i < nrow * nbnd; i += blockDim.x) Ct[i] = cf[i];
   const long base = kv * nbnd * npw_pad;
   const cplx<T>* uk = ukq + (long)k * nbnd * npw_pad;
   const cplx<T>* bk = bkq + (long)k * nproj * npw_pad;
+  const int gl = threadIdx.x % kSub, vb = threadIdx.x / kSub;
   double nr = 0.0;
-  for (int e = threadIdx.x; e < nbnd * (g1 - g0); e += blockDim.x) {
-    const int v = e / (g1 - g0), g = g0 + e - v * (g1 - g0);
-    const long i = base + (long)v * npw_pad + g;
-    cplx<T> acc = czero<T>();
-    if (g < np) {
-      acc = t[i];
-      for (int q = 0; q < nproj; ++q) acc = acc + cmul(bk[(long)q * npw_pad + g], ct[q * nbnd + v]);
-      for (int w = 0; w < nbnd; ++w) acc = acc - cmul(uk[(long)w * npw_pad + g], St[w * nbnd + v]);
-      const cplx<T> x = xin[i];
-      nr += (double)(x.x * acc.x + x.y * acc.y);
+  for (int s0 = g0; s0 < g1; s0 += kSub) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < nrow * kSub; e += blockDim.x) {
+      const int row = e / kSub, g = s0 + e - row * kSub;
+      cplx<T> v = czero<T>();
+      if (g < g1) v = row < nproj ? bk[(long)row * npw_pad + g] : uk[(long)(row - nproj) * npw_pad + g];
+      Bt[e] = v;
     }
-    t[i] = acc;
+    __syncthreads();
+    const int g = s0 + gl;
+    if (g < g1) {
+      for (int v = vb; v < nbnd; v += VS) {
+        const long i = base + (long)v * npw_pad + g;
+        cplx<T> acc = czero<T>();
+        if (g < np) {
+          acc = t[i];
+          for (int q = 0; q < nproj; ++q) acc = acc + cmul(Bt[q * kSub + gl], Ct[q * nbnd + v]);
+          for (int w = 0; w < nbnd; ++w) acc = acc - cmul(Bt[(nproj + w) * kSub + gl], Ct[(nproj + w) * nbnd + v]);
+          if (part) {
+            const cplx<T> x = xin[i];
+            nr += (double)(x.x * acc.x + x.y * acc.y);
+          }
+        }
+        t[i] = acc;
+      }
+    }
   }
+  if (!part) return;   // the projection of the update step: no norm
   nr = warp_sum(nr);
   if ((threadIdx.x & 31) == 0) wred[threadIdx.x >> 5] = nr;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += wred[w];
-    part[kv * nchunk + c] = s;
+    double sum = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += wred[w];
+    part[kv * nchunk + c] = sum;
   }
 }
 
