@@ -28,6 +28,8 @@ struct ChainBase {
   virtual int spectrum(int m, int kind, int m_total, const double* w_ev, int nw, double eta_ev, double* chi,
                        double* ei, double* e, std::string& err) = 0;
   virtual int steps() const = 0;
+  // replay of captured steps on/off (on by default where the stream allows it)
+  virtual void set_graphs(bool on) = 0;
   virtual int apply(int upper, const double* x, double* out, std::string& err) = 0;
   virtual int get_map(int* out, std::string& err) = 0;
   virtual int get_start(double* y, std::string& err) = 0;
@@ -198,6 +200,8 @@ template <typename T>
 class Chain : public ChainBase {
  public:
   ~Chain() override {
+    for (cudaGraphExec_t& g : graph_)
+      if (g) cudaGraphExecDestroy(g);
     for (void* p : ptrs_) cudaFree(p);
   }
   size_t bytes() const override { return bytes_; }
@@ -322,8 +326,12 @@ class Chain : public ChainBase {
         (rc = alloc(&y_, vq)) || (rc = alloc(&map_, (long)nks_ * pq)) || (rc = alloc(&part_, std::max(2L * nks_, nzv))) ||
         (rc = alloc(&spart_, nzp)) || (rc = alloc(&vecs_, 3L * nvec_ * vq)) ||
         (rc = alloc(&beta_, cap_ + 2)) || (rc = alloc(&gamma_, cap_ + 2)) || (rc = alloc(&z_, cap_ + 1)) ||
-        (rc = alloc(&zpart_, (long)(cap_ + 1) * nzp)) || (rc = alloc(&err_, 2)))
+        (rc = alloc(&zpart_, (long)(cap_ + 1) * nzp)) || (rc = alloc(&err_, 2)) || (rc = alloc(&jdev_, 1)))
       return rc;
+    {
+      const char* g = getenv("LL_GRAPHS");
+      use_graphs_ = use_graphs_ && !(g && g[0] == '0' && g[1] == 0);
+    }
     // chunk partials: U^H x per vector (two per vector on the non-Hermitian update), B^H x
     if (split_ && ((rc = alloc(&sp_s_, 2 * nzv * nbnd_ * nbnd_)) || (rc = alloc(&sp_c_, nzv * std::max(1, nproj_ * nbnd_))) ||
                    (rc = alloc(&ub_, (long)nks_ * nbnd_ * std::max(1, nproj_))) ||
@@ -433,17 +441,28 @@ class Chain : public ChainBase {
     const size_t smem_nh = 2 * (size_t)bpc_ * pq * sizeof(cplx<T>) + (size_t)nbnd_ * bpc_ * sizeof(cplx<double>) +
                            16 * 4 * sizeof(double);
     Coef co{beta_, gamma_, zpart_, err_};
+    if (flavour_ == LL_FLAVOUR_PH && n > 0) {
+      k_step_set<<<1, 1, 0, st_>>>(jdev_, queued_ + 1);
+      LL_CK(cudaGetLastError());
+      prof_.count(LL_PROF_UPDATE);
+    }
     for (int s = 0; s < n; ++s) {
       const int j = queued_ + s + 1;
       if (flavour_ == LL_FLAVOUR_PH) {
-        // update of the Lanczos vectors fused with the axis-3 inverse FFT of r_{j+1}
-        const int u0 = prof_.mark(st_);
-        if ((rc = launch_zinv_ph(j, err))) return rc;
-        prof_.count(LL_PROF_ZINV, split_ ? 4 : 2);
-        prof_.span(LL_PROF_ZINV, u0, prof_.mark(st_));
-        // r_{j+1} is upper when j is odd; the upper half gets D + K
-        const int dens = (j % 2 == 1 && approx_ != LL_APPROX_IPA) ? 0 : -1;
-        if ((rc = op_rest(1, R(), X(), dens, err))) return rc;
+        const int par = j % 2;
+        // a step of each parity is captured into a CUDA graph once one has run eagerly (every
+        // lazily set kernel attribute and launch shape is then fixed) and replayed after that;
+        // not while profiling, and not on the legacy default stream, which cannot be captured
+        if (use_graphs_ && !prof_.on && st_ != nullptr && eager_done_[par] && !graph_[par]) {
+          if ((rc = capture_step(j, err))) return rc;
+        }
+        if (graph_[par] && !prof_.on) {
+          LL_CK(cudaGraphLaunch(graph_[par], st_));
+          count_step(j);
+        } else {
+          if ((rc = ph_step(j, err))) return rc;
+          eager_done_[par] = true;
+        }
       } else {
         const int upper = (j % 2 == 0) ? 1 : 0;
         // L v_j: D + K on an upper v; L^dag w_j: D + K on a lower w
@@ -480,6 +499,59 @@ class Chain : public ChainBase {
     return LL_OK;
   }
 
+  // One pseudo-Hermitian step (the step index comes from the device counter jdev_, which the
+  // step advances at its end): update of the Lanczos vectors and the axis-3 inverse FFT of
+  // r_{j+1}, then the rest of the operator (D + K when j is odd: r_{j+1} is then upper).
+  int ph_step(int j, std::string& err) {
+    int rc;
+    const int u0 = prof_.mark(st_);
+    if ((rc = launch_zinv_ph(j, err))) return rc;
+    prof_.span(LL_PROF_ZINV, u0, prof_.mark(st_));
+    const int dens = (j % 2 == 1 && approx_ != LL_APPROX_IPA) ? 0 : -1;
+    if ((rc = op_rest(1, R(), X(), dens, err))) return rc;
+    k_step_next<<<1, 1, 0, st_>>>(jdev_);
+    prof_.count(LL_PROF_ZINV, split_ ? 4 : 2);
+    prof_.count(LL_PROF_UPDATE);
+    LL_CK(cudaGetLastError());
+    return LL_OK;
+  }
+  // launch counts of a replayed step (the same kernels as ph_step)
+  void count_step(int j) {
+    prof_.count(LL_PROF_ZINV, split_ ? 4 : 2);
+    prof_.count(LL_PROF_UPDATE);
+    prof_.count(LL_PROF_XY1);
+    if (j % 2 == 1 && approx_ != LL_APPROX_IPA) {
+      prof_.count(LL_PROF_HXC, 3);
+      prof_.count(LL_PROF_XY2);
+    }
+    prof_.count(LL_PROF_ZFWD, split_ ? 4 : 1);
+  }
+  int capture_step(int j, std::string& err) {
+    cudaGraph_t g = nullptr;
+    LL_CK(cudaStreamBeginCapture(st_, cudaStreamCaptureModeThreadLocal));
+    // the captured launches are counted when the graph is replayed, not here (profiling is
+    // off during a capture, so only the launch counters move)
+    long long saved[LL_NPROF], saved_total = prof_.total;
+    for (int c = 0; c < LL_NPROF; ++c) saved[c] = prof_.launches[c];
+    int rc = ph_step(j, err);
+    for (int c = 0; c < LL_NPROF; ++c) prof_.launches[c] = saved[c];
+    prof_.total = saved_total;
+    cudaError_t e = cudaStreamEndCapture(st_, &g);
+    if (rc != LL_OK) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (e != cudaSuccess) { err = std::string("step capture: ") + cudaGetErrorString(e); return LL_ECUDA; }
+    e = cudaGraphInstantiate(&graph_[j % 2], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      graph_[j % 2] = nullptr;
+      err = std::string("step graph: ") + cudaGetErrorString(e);
+      return LL_ECUDA;
+    }
+    return LL_OK;
+  }
+
   int collect(double* beta, double* gamma, double* z, int* done, std::string& err) override {
     int herr[2];
     LL_CK(cudaMemcpyAsync(herr, err_, sizeof(herr), cudaMemcpyDeviceToHost, st_));
@@ -504,6 +576,7 @@ class Chain : public ChainBase {
   }
 
   int steps() const override { return steps_; }
+  void set_graphs(bool on) override { use_graphs_ = use_graphs_ && on; }
 
   int spectrum(int m, int kind, int m_total, const double* w_ev, int nw, double eta_ev, double* chi, double* ei,
                double* e, std::string& err) override {
@@ -685,8 +758,8 @@ class Chain : public ChainBase {
     int rc;
     if ((rc = set_smem(k_sp_start<T>, sm, err))) return rc;
     Coef co{beta_, gamma_, zpart_, err_};
-    k_sp_start<T><<<dim3(nks_, nchunk_), 256, sm, st_>>>(j, (j % 2 == 0) ? 1 : 0, nks_, nbnd_, pq, dq_.npw, nchunk_,
-                                                         part_, R(), X(), Vp(), y_, ukq_, co, tol_, sp_s_);
+    k_sp_start<T><<<dim3(nks_, nchunk_), 256, sm, st_>>>(jdev_, nks_, nbnd_, pq, dq_.npw, nchunk_, part_, R(), X(), Vp(),
+                                                         y_, ukq_, co, tol_, sp_s_);
     // P_c with the chunk-reduced coefficients, tiled (U read once per chunk for all bands),
     // then the axis-3 inverse FFTs over many CTAs per k
     const size_t sm_a = (size_t)nbnd_ * (nbnd_ + kSub) * sizeof(cplx<T>);
@@ -707,8 +780,8 @@ class Chain : public ChainBase {
     Coef co{beta_, gamma_, zpart_, err_};
     // the per-(k, band group) update, then the axis-3 inverse FFTs, one thread per column line
     if ((rc = set_smem(k_ph_update<T>, smem, err))) return rc;
-    k_ph_update<T><<<dim3(nks_, ngrp_), 256, smem, st_>>>(j, (j % 2 == 0) ? 1 : 0, dq_, nbnd_, bpc_, part_, R(), X(),
-                                                          Vp(), y_, ukq_, co, tol_);
+    k_ph_update<T><<<dim3(nks_, ngrp_), 256, smem, st_>>>(jdev_, dq_, nbnd_, bpc_, part_, R(), X(), Vp(), y_, ukq_, co,
+                                                          tol_);
     k_zinv<T, N><<<dim3(nks_, 1, zsplit()), 128, 0, st_>>>(dq_, R(), nbnd_, cbuf_, cb_ncol_);
     LL_CK(cudaGetLastError());
     return LL_OK;
@@ -960,6 +1033,10 @@ class Chain : public ChainBase {
   cplx<T>* scratch_ = nullptr;
   cplx<double> *spart_ = nullptr, *gamma_ = nullptr, *z_ = nullptr, *zpart_ = nullptr, *spec_out_ = nullptr;
   ExtrapTail* tail_ = nullptr;   // continuation constants of the coefficients (spectrum)
+  int* jdev_ = nullptr;          // device step counter of the pseudo-Hermitian recursion
+  bool use_graphs_ = true;       // replay captured steps (LL_GRAPHS=0 in the environment: eager)
+  bool eager_done_[2] = {false, false};
+  cudaGraphExec_t graph_[2] = {nullptr, nullptr};   // one captured step per parity of j
   bool split_ = false;      // per-k work split over chunks of plane waves (split.cuh)
   int nchunk_ = 1;          // plane-wave chunks per k on the split path
   int bpc_ = 1, ngrp_ = 1;  // bands per CTA of the per-k kernels, band groups per k

@@ -533,7 +533,8 @@ __device__ __forceinline__ double block_mean(const double* p, int n, int stride 
   return t / n;
 }
 
-// Pseudo-Hermitian step j for one band group of one k-point (P_c, the norm and z act band by
+// Pseudo-Hermitian step j (read from the device step counter, so that a captured step can be
+// replayed) for one band group of one k-point (P_c, the norm and z act band by
 // band, so groups of bpc bands are independent): beta_j from the ngrp partials per k of
 // Re(r_j^H X_j) (every block re-reduces them in the same order), the group's z_j partial,
 // r_{j+1} = P_c(X_j/beta_j - beta_j v_{j-1}) formed in shared memory and written to R,
@@ -541,12 +542,13 @@ __device__ __forceinline__ double block_mean(const double* p, int n, int stride 
 // k_zinv.  grid (nks, ngrp), block 256.  smem: r [bpc][npw_pad], S [nbnd*bpc] (double
 // complex), reduction scratch.
 template <typename T>
-__global__ void __launch_bounds__(256) k_ph_update(int j, int r_upper, SphereDev s, int nbnd, int bpc,
+__global__ void __launch_bounds__(256) k_ph_update(const int* __restrict__ jdev, SphereDev s, int nbnd, int bpc,
                                                    const double* __restrict__ part, cplx<T>* __restrict__ R,
                                                    const cplx<T>* __restrict__ X, cplx<T>* __restrict__ Vp,
                                                    const cplx<T>* __restrict__ y, const cplx<T>* __restrict__ ukq,
                                                    Coef co, double tol) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int j = *jdev, r_upper = (j % 2 == 0) ? 1 : 0;   // step index from the device counter
   const int npw_pad = s.npw_pad, nks = s.nks;
   const int k = blockIdx.x, grp = blockIdx.y, ngrp = gridDim.y;
   cplx<T>* rs = reinterpret_cast<cplx<T>*>(smem_raw);
@@ -745,6 +747,11 @@ __global__ void __launch_bounds__(128) k_nh_normalize(int j, int nks, int nbnd, 
 }
 
 // z_j = (1/nks) sum_k zpart[j][k] for j in [j0, j1)
+// Device step counter of the pseudo-Hermitian recursion: set before a run of steps, advanced
+// at the end of every step (one thread).
+static __global__ void k_step_set(int* jdev, int j) { *jdev = j; }
+static __global__ void k_step_next(int* jdev) { *jdev += 1; }
+
 // (nzp partials per step: one per k, or one per (k, chunk) on the split path)
 static __global__ void k_reduce_z(const cplx<double>* __restrict__ zpart, int nzp, int nks, int j0, int j1,
                                   cplx<double>* __restrict__ z) {

@@ -105,6 +105,10 @@ void start_job(ll_server* s, Job* j) {
     return;
   }
   j->chain = (j->desc.precision == LL_PREC_FP64) ? ll::make_chain_f64() : ll::make_chain_f32();
+  // the request loop's chains launch eagerly: with many chains sharing the GPU, replayed step
+  // graphs measured slower on the Poisson stream (2655 vs 3584 steps/s, p50 14.8 vs 5.3 s)
+  // and no faster on the many-Q batch
+  j->chain->set_graphs(false);
   const int rc = j->chain->create(&j->desc, j->stream, err);
   if (rc != LL_OK) {
     finish(s, j, rc, "create: " + err);

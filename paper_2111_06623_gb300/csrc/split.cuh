@@ -91,13 +91,14 @@ __device__ void chunk_dots(const cplx<T>* A, long lda, const cplx<T>* B, long ld
 // the chunk, r_{j+1} = X_j/beta_j - beta_j v_{j-1} into R, v_j = r_j/beta_j into Vp, and the
 // chunk's partial U^H r_{j+1}.  grid (nks, nchunk), block 256.
 template <typename T>
-__global__ void __launch_bounds__(256) k_sp_start(int j, int r_upper, int nks, int nbnd, int npw_pad,
+__global__ void __launch_bounds__(256) k_sp_start(const int* __restrict__ jdev, int nks, int nbnd, int npw_pad,
                                                   const int* __restrict__ npw, int nchunk,
                                                   const double* __restrict__ part, cplx<T>* __restrict__ R,
                                                   const cplx<T>* __restrict__ X, cplx<T>* __restrict__ Vp,
                                                   const cplx<T>* __restrict__ y, const cplx<T>* __restrict__ ukq,
                                                   Coef co, double tol, cplx<double>* __restrict__ spart) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int j = *jdev, r_upper = (j % 2 == 0) ? 1 : 0;   // step index from the device counter
   cplx<T>* tile = reinterpret_cast<cplx<T>*>(smem_raw);
   __shared__ double sbeta;
   __shared__ double zred[2][8];

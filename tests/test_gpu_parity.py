@@ -323,3 +323,20 @@ def test_sc16_first_coefficients(lib, sc16):
     ref = lanczos.pseudo_hermitian(sys, 3)
     got = chain_from_bundle(sc16, max_steps=3).lanczos(3)
     assert _coef_rel(got, ref, 3) < 1e-10
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_graph_replayed_steps_match_eager(lib, small, precision):
+    """On a stream other than the legacy default, the chain captures one pseudo-Hermitian step
+    of each parity into a CUDA graph and replays it; the coefficients are those of the eager
+    launches (default stream) bit for bit, over several calls (resume)."""
+    torch = pytest.importorskip("torch")
+    eager = chain_from_bundle(small, precision=precision, max_steps=80).lanczos(80)
+    st = torch.cuda.Stream()
+    ch = chain_from_bundle(small, precision=precision, max_steps=80, stream=st.cuda_stream)
+    ch.lanczos(7)
+    ch.lanczos(30)
+    got = ch.lanczos(43)
+    st.synchronize()
+    for a, b in zip(eager, got):
+        assert np.array_equal(a, b)
