@@ -78,7 +78,10 @@ typedef struct {
  * intersection, column/plane tables), u_{vk}(r) grids, f_xc(n0), the Hartree kernel
  * 4 pi/|Q+G|^2, the starting vector y = P_c u (Eq. 28) and, for the pseudo-Hermitian
  * flavour, its first operator application D y.  Work is queued on `stream`; the call
- * returns once the set-up has finished.  LL_EINVAL on malformed input (unsorted spheres,
+ * returns once the set-up has finished.  On a stream other than the legacy default (NULL),
+ * pseudo-Hermitian steps are captured into CUDA graphs (one per parity of the step index)
+ * after their first eager run and replayed; results are bitwise those of eager launches
+ * (LL_GRAPHS=0 in the environment keeps every launch eager).  LL_EINVAL on malformed input (unsorted spheres,
  * Miller indices that do not fit the grid, Q on the reciprocal lattice ...).
  * *out receives a handle to release with ll_destroy. */
 int ll_create(const ll_system_desc* desc, void* stream, ll_handle** out);
