@@ -799,8 +799,8 @@ class Chain : public ChainBase {
     return LL_EUNSUPPORTED;
   }
 
-  // CTAs per k-block of the axis-3 inverse FFTs: one per 1024 column lines
-  int zsplit() const { return std::max(1, nbnd_ * std::max(hk_.ncol_max, hq_.ncol_max) / 1024); }
+  // CTAs per k-block of the axis-3 inverse FFTs: one column line per thread
+  int zsplit() const { return std::max(1, (nbnd_ * std::max(hk_.ncol_max, hq_.ncol_max) + 127) / 128); }
   template <int N>
   int zinv_n(const SphereDev& s, const cplx<T>* in, int nvec) {
     k_zinv<T, N><<<dim3(nks_, nvec, zsplit()), 128, 0, st_>>>(s, in, nbnd_, cbuf_, cb_ncol_);
