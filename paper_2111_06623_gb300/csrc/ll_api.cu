@@ -361,7 +361,12 @@ int ll_footprint(const ll_system_desc* d, size_t* bytes) {
   const size_t ngroups = (4 * 152 + d->nfft - 1) / d->nfft;
   size_t b = elem * (vq * (3 * nvec + nvec + 2) + orb * pk + orb * n3 + cb + ngroups * n3 + 3 * n3 +
                      (size_t)d->nks * d->nproj * pq);
-  b += (elem / 2) * (2 * n3 + (size_t)d->nks * pq) + 8 * n3 + 40 * (size_t)(d->max_steps + 2) * (d->nks + 2);
+  // Lanczos partials: up to max(bands, plane-wave chunks) per k and step (band groups or the
+  // split path), and the split path's chunk partials and coefficient blocks
+  const size_t npk = (size_t)std::max(d->nbnd, (int)((pq + 511) / 512));
+  const size_t pairs = (size_t)(d->nproj + d->nbnd) * d->nbnd;
+  b += (elem / 2) * (2 * n3 + (size_t)d->nks * pq) + 8 * n3 +
+       40 * (size_t)(d->max_steps + 2) * (d->nks * npk + 2) + 48 * nvec * (size_t)d->nks * npk * pairs;
   *bytes = b;
   return LL_OK;
 }
