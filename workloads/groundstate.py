@@ -260,7 +260,9 @@ def scf(spec: SystemSpec, tol: float = 1e-11, maxiter: int = 80, verbose: bool =
     kw = np.full(len(kf), 1.0 / len(kf))
     rho = np.full((n, n, n), spec.nelec / spec.omega)
     if spec.free_electron:
-        return vion + lda_vxc(rho), rho, 0
+        # V = 0: the free-electron limit; the uniform gas's constant v_xc would shift every
+        # level alike, and the plane-wave levels below are the bare kinetic energies
+        return vion, rho, 0
     tol = spec.extra.get("scf_tol", tol)
     # a pool of single-threaded workers only pays with several k-points; one or two large
     # eigenproblems run here with threaded LAPACK
