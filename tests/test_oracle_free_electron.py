@@ -130,3 +130,22 @@ def test_plasma_frequency_from_first_moment():
     m1 = 4.0 / spec.omega * sys.inner(y, sys.apply_d(y)).real
     wp2 = 4 * np.pi / float(spec.q_cart @ spec.q_cart) * m1
     assert abs(wp2 / (4 * np.pi * spec.nelec / spec.omega) - 1.0) < 1e-12
+
+
+@pytest.mark.parametrize("flavour", ["ph", "nh"])
+@pytest.mark.parametrize("approx", ["rpa", "tddft"])
+def test_fsum_integral_of_loss_function(approx, flavour):
+    """The f-sum rule on the broadened loss function (Sec. 2.1): the integral of
+    omega (-Im eps^-1) over 0..60 eV is (pi/2) omega_p^2.  Each pole pair +-Omega adds two
+    Lorentzians whose logarithmic tails cancel, leaving an O(eta/Omega) error (~0.1 %)."""
+    b = _gas(K_SET, approx)
+    spec = b.spec
+    sys = System(b, approx)
+    co = lanczos.run(sys, 2 * len(K_SET), flavour)
+    wev = np.linspace(0.0, 60.0, 30001)
+    _, eps_inv, _ = spectrum.spectrum(co.beta, co.gamma, co.z, spec.omega, spec.q_cart, wev, 0.02)
+    wha = wev / w.HA_EV
+    f = wha * spectrum.loss(eps_inv)
+    moment = float(np.sum(0.5 * (f[1:] + f[:-1]) * np.diff(wha)))
+    wp2 = 4 * np.pi * spec.nelec / spec.omega
+    assert abs(moment / (0.5 * np.pi * wp2) - 1.0) < 5e-3
