@@ -82,7 +82,8 @@ typedef struct {
  * pseudo-Hermitian steps are captured into CUDA graphs (one per parity of the step index)
  * after their first eager run and replayed; results are bitwise those of eager launches
  * (LL_GRAPHS=0 in the environment keeps every launch eager).  LL_EINVAL on malformed input (unsorted spheres,
- * Miller indices that do not fit the grid, Q on the reciprocal lattice ...).
+ * Miller indices that do not fit the grid, Q on the reciprocal lattice, a NaN or infinity in any
+ * floating-point array, named in ll_last_error ...), checked on the host before any device work.
  * *out receives a handle to release with ll_destroy. */
 int ll_create(const ll_system_desc* desc, void* stream, ll_handle** out);
 int ll_destroy(ll_handle* h);

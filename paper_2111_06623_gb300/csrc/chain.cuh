@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -230,6 +231,25 @@ class Chain : public ChainBase {
     if (!build_sphere(nks_, d->npw_kq, d->miller_kq, n, hq_, err)) return LL_EINVAL;
     for (int k = 0; k < nks_; ++k)
       if (d->npw_kq[k] < nbnd_ + 1) { err = "sphere smaller than the occupied manifold"; return LL_EINVAL; }
+    {
+      // every floating-point input finite: a NaN or an infinity would pass into every
+      // coefficient of the chain without tripping the breakdown checks
+      long sk = 0, sq = 0;
+      for (int k = 0; k < nks_; ++k) sk += d->npw_k[k], sq += d->npw_kq[k];
+      const long n3 = (long)n * n * n;
+      const struct { const double* p; long len; const char* what; } in[] = {
+          {&d->lattice[0][0], 9, "lattice"},       {d->q_cart, 3, "q_cart"},
+          {d->kcart, 3L * nks_, "kcart"},          {d->u_k, 2L * nbnd_ * sk, "u_k"},
+          {d->u_kq, 2L * nbnd_ * sq, "u_kq"},      {d->eps_k, (long)nks_ * nbnd_, "eps_k"},
+          {d->vloc_r, n3, "vloc_r"},               {d->rho_r, n3, "rho_r"},
+          {d->beta_kq, 2L * nproj_ * sq, "beta_kq"}, {d->dij, (long)nproj_, "dij"}};
+      for (const auto& a : in)
+        for (long i = 0; i < a.len; ++i)
+          if (!std::isfinite(a.p[i])) {
+            err = std::string("non-finite value in ") + a.what + " at index " + std::to_string(i);
+            return LL_EINVAL;
+          }
+    }
     double b[3][3];
     recip(d->lattice, b);
     omega_ = fabs(d->lattice[0][0] * (d->lattice[1][1] * d->lattice[2][2] - d->lattice[1][2] * d->lattice[2][1]) -

@@ -90,3 +90,24 @@ def test_rejects_bad_extrapolation(ll):
         assert e.value.code == ll.LL_EINVAL
     with pytest.raises(KeyError):
         ll.spectrum(b, g, g, 270.0, [0.06, 0, 0], w, 0.1, extrapolation="linear", m_total=100)
+
+
+@pytest.mark.parametrize("name,bad", [("u_k", np.nan), ("u_kq", np.inf), ("eps_k", np.nan), ("vloc_r", -np.inf),
+                                      ("rho_r", np.nan), ("kcart", np.nan), ("q_cart", np.nan),
+                                      ("beta_kq", np.nan), ("dij", np.inf)])
+def test_rejects_non_finite_input(ll, name, bad):
+    b = w.get_bundle(w.config_tiny())
+    args = _desc_args(b)
+    if name in ("beta_kq", "dij") and len(b.dij) == 0:
+        pytest.skip("the cell has no KB projectors")
+    v = args[name]
+    if isinstance(v, list):                       # per-k arrays: spoil the last k-point's last entry
+        v = [x.copy() for x in v]
+        v[-1].flat[-1] = bad
+    else:
+        v = np.array(v, copy=True)
+        v.flat[v.size // 2] = bad
+    args[name] = v
+    with pytest.raises(ll.LLError) as e:
+        ll.Chain(**args)
+    assert e.value.code == ll.LL_EINVAL and f"non-finite value in {name}" in str(e.value)
