@@ -37,7 +37,8 @@ typedef enum {
   LL_ECUDA = 6,         /* a CUDA runtime call failed                                    */
   LL_PENDING = 7,
   LL_ENOTFOUND = 8,
-  LL_EUNSUPPORTED = 9   /* valid input outside what this build implements                */
+  LL_EUNSUPPORTED = 9,  /* valid input outside what this build implements                */
+  LL_ECANCELED = 10     /* the job was cancelled (ll_cancel)                             */
 } ll_status;
 
 enum { LL_APPROX_IPA = 0, LL_APPROX_RPA = 1, LL_APPROX_TDDFT = 2 };   /* Sec. 3.2 */
@@ -241,6 +242,13 @@ int ll_server_set_chunk(ll_server* s, int steps);
 int ll_submit(ll_server* s, const ll_job_desc* job, uint64_t* job_id);
 /* *state = LL_JOB_*; when res is given, fills it (results once the job has ended). */
 int ll_poll(ll_server* s, uint64_t job_id, int* state, ll_job_result* res);
+/* Cancels a job.  A queued job leaves the queue at once.  A running chain stops at the end of
+ * the scheduler's current round, when none of its kernels is in flight; it keeps the
+ * coefficients (and the spectrum, when a grid was given) of the steps it finished, and its
+ * memory goes back to the budget.  Either way the job ends FAILED with status LL_ECANCELED.
+ * A job that reaches its last step in that round, or that has already ended, keeps its
+ * outcome (LL_OK).  LL_ENOTFOUND for an unknown id. */
+int ll_cancel(ll_server* s, uint64_t job_id);
 /* Device bytes held by running chains now and at most so far; running and queued jobs. */
 int ll_server_stats(ll_server* s, size_t* used, size_t* peak, int* running, int* queued);
 const char* ll_server_last_error(void);

@@ -10,6 +10,8 @@
 // on what runs beside it (deterministic kernels, no shared state).
 #include <string.h>
 
+#include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -40,6 +42,7 @@ struct Job {
   double eta = 0.0;
   size_t footprint = 0;
   ll::ChainBase* chain = nullptr;
+  std::atomic<bool> cancel{false};  // set by ll_cancel, read by the scheduler between rounds
   cudaStream_t stream = nullptr;
   int steps_done = 0;
   std::vector<double> beta;
@@ -75,6 +78,13 @@ void copy_in(std::vector<V>& dst, const V* src, size_t n) {
   dst.assign(src, src + n);
 }
 
+// The job's copies of the ground state are not needed once it has ended.
+void drop_inputs(Job* j) {
+  for (auto* v : {&j->u_k, &j->u_kq, &j->beta_kq, &j->vloc, &j->rho}) std::vector<double>().swap(*v);
+  std::vector<int>().swap(j->miller_k);
+  std::vector<int>().swap(j->miller_kq);
+}
+
 void finish(ll_server* s, Job* j, int status, const std::string& err) {
   if (j->chain) {
     delete j->chain;
@@ -90,9 +100,7 @@ void finish(ll_server* s, Job* j, int status, const std::string& err) {
   j->err = err;
   j->state = (status == LL_OK) ? LL_JOB_DONE : LL_JOB_FAILED;
   j->t_done = now_s();
-  for (auto* v : {&j->u_k, &j->u_kq, &j->beta_kq, &j->vloc, &j->rho}) std::vector<double>().swap(*v);
-  std::vector<int>().swap(j->miller_k);
-  std::vector<int>().swap(j->miller_kq);
+  drop_inputs(j);
   s->cv.notify_all();
 }
 
@@ -186,7 +194,7 @@ void scheduler(ll_server* s) {
     std::vector<std::string> errs(run.size());
     for (size_t i = 0; i < run.size(); ++i) {
       const int n = std::min(chunk, run[i]->n_steps - run[i]->chain->steps_queued());
-      if (n > 0) rcs[i] = run[i]->chain->enqueue(n, errs[i]);
+      if (n > 0 && !run[i]->cancel.load()) rcs[i] = run[i]->chain->enqueue(n, errs[i]);
     }
     std::vector<Job*> still;
     for (size_t i = 0; i < run.size(); ++i) {
@@ -196,6 +204,11 @@ void scheduler(ll_server* s) {
       int rc = rcs[i];
       if (rc == LL_OK) rc = j->chain->collect(nullptr, nullptr, nullptr, &done, err);
       j->steps_done = done;
+      // a cancelled chain ends here, after collect: none of its kernels is in flight
+      if (rc == LL_OK && done < j->n_steps && j->cancel.load()) {
+        rc = LL_ECANCELED;
+        err = "cancelled after " + std::to_string(done) + " steps";
+      }
       if (rc != LL_OK || done >= j->n_steps) complete_job(s, j, rc, err);
       else still.push_back(j);
     }
@@ -315,6 +328,30 @@ int ll_poll(ll_server* s, uint64_t id, int* state, ll_job_result* res) {
     if (res->eps && nw) memcpy(res->eps, j->eps.data(), 2 * nw * sizeof(double));
     if (j->state == LL_JOB_FAILED) g_srv_err = j->err;
   }
+  return LL_OK;
+}
+
+int ll_cancel(ll_server* s, uint64_t id) {
+  if (!s) return sfail(LL_EINVAL, "null server");
+  std::lock_guard<std::mutex> lock(s->mu);
+  auto it = s->jobs.find(id);
+  if (it == s->jobs.end()) return sfail(LL_ENOTFOUND, "unknown job id");
+  Job* j = it->second;
+  if (j->state == LL_JOB_DONE || j->state == LL_JOB_FAILED) return LL_OK;
+  auto q = std::find(s->queue.begin(), s->queue.end(), j);
+  if (q != s->queue.end()) {
+    // still queued: nothing of it is on the device and its footprint is not in `used`
+    s->queue.erase(q);
+    j->status = LL_ECANCELED;
+    j->err = "cancelled before admission";
+    j->state = LL_JOB_FAILED;
+    j->t_done = now_s();
+    drop_inputs(j);
+    s->cv.notify_all();
+    return LL_OK;
+  }
+  // admitted or running: the scheduler ends it after its current round
+  j->cancel.store(true);
   return LL_OK;
 }
 

@@ -16,7 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libll.so")
 
 LL_OK, LL_EINVAL, LL_ENOMEM, LL_EBREAKDOWN, LL_ENOTPD, LL_ETIMEOUT, LL_ECUDA = 0, 1, 2, 3, 4, 5, 6
-LL_PENDING, LL_ENOTFOUND, LL_EUNSUPPORTED = 7, 8, 9
+LL_PENDING, LL_ENOTFOUND, LL_EUNSUPPORTED, LL_ECANCELED = 7, 8, 9, 10
 LL_EXTRAP_NO, LL_EXTRAP_CONSTANT, LL_EXTRAP_OSC = 0, 1, 2
 APPROX = {"ipa": 0, "rpa": 1, "tddft": 2}
 FLAVOUR = {"ph": 0, "nh": 1}
@@ -68,6 +68,7 @@ def _load():
         "ll_server_set_chunk": (C.c_int, [vp, C.c_int]),
         "ll_submit": (C.c_int, [vp, vp, C.POINTER(C.c_uint64)]),
         "ll_poll": (C.c_int, [vp, C.c_uint64, C.POINTER(C.c_int), vp]),
+        "ll_cancel": (C.c_int, [vp, C.c_uint64]),
         "ll_server_stats": (C.c_int, [vp, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t), C.POINTER(C.c_int),
                                       C.POINTER(C.c_int)]),
         "ll_server_last_error": (C.c_char_p, []),
@@ -87,7 +88,7 @@ EXPORTS = ("ll_create", "ll_destroy", "ll_lanczos", "ll_lanczos_spectrum", "ll_s
            "ll_lanczos_spectrum_x", "ll_spectrum_x",
            "ll_apply", "ll_get_map", "ll_get_start", "ll_footprint", "ll_profile", "ll_profile_read", "ll_last_error",
            "ll_version", "ll_fma_peak", "ll_server_create",
-           "ll_server_set_chunk", "ll_submit", "ll_poll", "ll_server_stats", "ll_server_last_error",
+           "ll_server_set_chunk", "ll_submit", "ll_poll", "ll_cancel", "ll_server_stats", "ll_server_last_error",
            "ll_server_destroy")
 PROF_CLASSES = ("zinv", "xy1", "hxc", "xy2", "zfwd", "update")
 
@@ -365,6 +366,11 @@ class Server:
             if st.value == JOB_FAILED:
                 res["error"] = _lib.ll_server_last_error().decode()
         return st.value, res
+
+    def cancel(self, job_id: int):
+        """ll_cancel: a queued job ends at once, a running one after the current round; either
+        ends FAILED with status LL_ECANCELED and keeps the coefficients of its finished steps."""
+        _srv_check(_lib.ll_cancel(self._h, C.c_uint64(job_id)))
 
     def stats(self):
         used, peak = C.c_size_t(0), C.c_size_t(0)

@@ -122,3 +122,40 @@ def test_malformed_job_fails_without_stopping_the_loop(ll):
     assert res[j_bad][0] == 3 and res[j_bad][1]["status"] == 1
     assert res[j_ok][0] == 2 and res[j_ok][1]["steps_done"] == 10
     srv.close()
+
+
+def test_cancel_queued_and_running_jobs(ll):
+    """A cancelled queued job ends at once with no steps; a cancelled running chain stops after
+    its current round with the coefficients of the steps it finished (those of the same job
+    run alone), its memory returns to the budget and the next job takes its slot."""
+    small = w.get_bundle(w.config_small())
+    opts = dict(flavour="ph", precision="fp64", approx="tddft")
+    n_long = 20000
+    srv = ll.Server(hbm_budget_bytes=16 << 30, max_slots=1, chunk=8)
+    long_id = srv.submit(n_long, WGRID, 0.1, **_system(small, max_steps=n_long, **opts))
+    queued_id = srv.submit(10, None, 0.1, **_system(small, max_steps=10, **opts))
+    t0 = time.time()
+    while True:
+        st, r = srv.poll(long_id)
+        if st == 1 and r["steps_done"] >= 16:
+            break
+        assert st in (0, 1) and time.time() - t0 < 120, r.get("error")
+        time.sleep(0.002)
+    srv.cancel(queued_id)
+    st, r = srv.poll(queued_id)
+    assert st == 3 and r["status"] == ll.LL_ECANCELED and r["steps_done"] == 0
+    srv.cancel(long_id)
+    st, r = _wait(srv, [long_id], timeout=120)[long_id]
+    m = r["steps_done"]
+    assert st == 3 and r["status"] == ll.LL_ECANCELED, r.get("error")
+    assert 16 <= m < n_long and m % 8 == 0
+    beta, gamma, z, _ = _alone(small, opts, m)
+    assert np.array_equal(r["beta"], beta) and np.array_equal(r["gamma"], gamma) and np.array_equal(r["z"], z)
+    assert np.all(np.isfinite(r["chi"])) and np.any(r["chi"] != 0)
+    assert srv.stats()["used"] == 0
+    nxt = srv.submit(10, None, 0.1, **_system(small, max_steps=10, **opts))
+    st, r = _wait(srv, [nxt])[nxt]
+    assert st == 2 and r["steps_done"] == 10, r.get("error")
+    srv.cancel(nxt)                                # already ended: unchanged
+    assert srv.poll(nxt)[0] == 2
+    srv.close()

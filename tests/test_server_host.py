@@ -1,4 +1,6 @@
-"""Host-side behaviour of the request loop that needs no GPU: refusals at submit."""
+"""Host-side behaviour of the request loop that needs no GPU: refusals at submit, cancel."""
+import time
+
 import numpy as np
 import pytest
 
@@ -48,3 +50,22 @@ def test_server_arguments(ll):
         ll.Server(hbm_budget_bytes=0, max_slots=1)
     with pytest.raises(ll.LLError):
         ll.Server(hbm_budget_bytes=1 << 30, max_slots=0)
+
+
+def test_cancel_unknown_and_ended_jobs(ll):
+    """ll_cancel: LL_ENOTFOUND for an unknown id; a job that has ended keeps its outcome."""
+    b = w.get_bundle(w.config_tiny())
+    srv = ll.Server(hbm_budget_bytes=1 << 34, max_slots=2)
+    with pytest.raises(ll.LLError) as e:
+        srv.cancel(777)
+    assert e.value.code == ll.LL_ENOTFOUND
+    jid = srv.submit(5, None, 0.1, **_system(b))
+    t0 = time.time()
+    while srv.poll(jid)[0] not in (2, 3):       # without a GPU the job fails at admission
+        assert time.time() - t0 < 60
+        time.sleep(0.01)
+    st, r = srv.poll(jid)
+    srv.cancel(jid)
+    st2, r2 = srv.poll(jid)
+    assert (st2, r2["status"]) == (st, r["status"]) and r2["status"] != ll.LL_ECANCELED
+    srv.close()
