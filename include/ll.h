@@ -238,7 +238,8 @@ int ll_server_create(size_t hbm_budget_bytes, int max_slots, ll_server** out);
 /* Steps queued per chain per round (default 64). */
 int ll_server_set_chunk(ll_server* s, int steps);
 /* Copies the job; LL_ENOMEM when its footprint exceeds the whole budget, LL_EINVAL when the
- * descriptor is malformed (further checks happen at admission and end the job FAILED). */
+ * descriptor is malformed: a missing array, an empty sphere, a NaN or an infinity in any
+ * floating-point input (further checks happen at admission and end the job FAILED). */
 int ll_submit(ll_server* s, const ll_job_desc* job, uint64_t* job_id);
 /* *state = LL_JOB_*; when res is given, fills it (results once the job has ended). */
 int ll_poll(ll_server* s, uint64_t job_id, int* state, ll_job_result* res);

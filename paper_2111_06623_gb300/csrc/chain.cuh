@@ -92,6 +92,28 @@ struct HostSphere {
 
 static inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
 
+// Every floating-point input of a system finite: a NaN or an infinity would pass into every
+// coefficient of the chain without tripping the breakdown checks.  The array pointers and the
+// sphere sizes npw_k, npw_kq must already be valid.
+static inline bool inputs_finite(const ll_system_desc* d, std::string& err) {
+  long sk = 0, sq = 0;
+  for (int k = 0; k < d->nks; ++k) sk += d->npw_k[k], sq += d->npw_kq[k];
+  const long n3 = (long)d->nfft * d->nfft * d->nfft, nb = d->nbnd, np = d->nproj;
+  const struct { const double* p; long len; const char* what; } in[] = {
+      {&d->lattice[0][0], 9, "lattice"},     {d->q_cart, 3, "q_cart"},
+      {d->kcart, 3L * d->nks, "kcart"},      {d->u_k, 2 * nb * sk, "u_k"},
+      {d->u_kq, 2 * nb * sq, "u_kq"},        {d->eps_k, (long)d->nks * nb, "eps_k"},
+      {d->vloc_r, n3, "vloc_r"},             {d->rho_r, n3, "rho_r"},
+      {d->beta_kq, 2 * np * sq, "beta_kq"}, {d->dij, np, "dij"}};
+  for (const auto& a : in)
+    for (long i = 0; i < a.len; ++i)
+      if (!std::isfinite(a.p[i])) {
+        err = std::string("non-finite value in ") + a.what + " at index " + std::to_string(i);
+        return false;
+      }
+  return true;
+}
+
 static inline bool build_sphere(int nks, const int* npw, const int* mil, int n, HostSphere& h, std::string& err) {
   h.nks = nks;
   h.npw.assign(npw, npw + nks);
@@ -231,25 +253,7 @@ class Chain : public ChainBase {
     if (!build_sphere(nks_, d->npw_kq, d->miller_kq, n, hq_, err)) return LL_EINVAL;
     for (int k = 0; k < nks_; ++k)
       if (d->npw_kq[k] < nbnd_ + 1) { err = "sphere smaller than the occupied manifold"; return LL_EINVAL; }
-    {
-      // every floating-point input finite: a NaN or an infinity would pass into every
-      // coefficient of the chain without tripping the breakdown checks
-      long sk = 0, sq = 0;
-      for (int k = 0; k < nks_; ++k) sk += d->npw_k[k], sq += d->npw_kq[k];
-      const long n3 = (long)n * n * n;
-      const struct { const double* p; long len; const char* what; } in[] = {
-          {&d->lattice[0][0], 9, "lattice"},       {d->q_cart, 3, "q_cart"},
-          {d->kcart, 3L * nks_, "kcart"},          {d->u_k, 2L * nbnd_ * sk, "u_k"},
-          {d->u_kq, 2L * nbnd_ * sq, "u_kq"},      {d->eps_k, (long)nks_ * nbnd_, "eps_k"},
-          {d->vloc_r, n3, "vloc_r"},               {d->rho_r, n3, "rho_r"},
-          {d->beta_kq, 2L * nproj_ * sq, "beta_kq"}, {d->dij, (long)nproj_, "dij"}};
-      for (const auto& a : in)
-        for (long i = 0; i < a.len; ++i)
-          if (!std::isfinite(a.p[i])) {
-            err = std::string("non-finite value in ") + a.what + " at index " + std::to_string(i);
-            return LL_EINVAL;
-          }
-    }
+    if (!inputs_finite(d, err)) return LL_EINVAL;
     double b[3][3];
     recip(d->lattice, b);
     omega_ = fabs(d->lattice[0][0] * (d->lattice[1][1] * d->lattice[2][2] - d->lattice[1][2] * d->lattice[2][1]) -

@@ -254,6 +254,12 @@ int ll_submit(ll_server* s, const ll_job_desc* jd, uint64_t* job_id) {
       !d->miller_k || !d->miller_kq || !d->u_k || !d->u_kq || !d->eps_k || !d->vloc_r || !d->rho_r ||
       (d->nproj > 0 && (!d->beta_kq || !d->dij)) || (jd->n_omega > 0 && !jd->omega_ev))
     return sfail(LL_EINVAL, "malformed job");
+  {
+    std::string err;
+    for (int k = 0; k < d->nks; ++k)
+      if (d->npw_k[k] < 1 || d->npw_kq[k] < 1) return sfail(LL_EINVAL, "malformed job: empty plane-wave sphere");
+    if (!ll::inputs_finite(d, err)) return sfail(LL_EINVAL, "malformed job: " + err);
+  }
   size_t fp = 0;
   if (ll_footprint(d, &fp) != LL_OK) return sfail(LL_EINVAL, "footprint");
   if (fp > s->budget) return sfail(LL_ENOMEM, "job footprint exceeds the whole HBM budget");

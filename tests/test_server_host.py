@@ -69,3 +69,15 @@ def test_cancel_unknown_and_ended_jobs(ll):
     st2, r2 = srv.poll(jid)
     assert (st2, r2["status"]) == (st, r["status"]) and r2["status"] != ll.LL_ECANCELED
     srv.close()
+
+
+def test_non_finite_job_refused_at_submit(ll):
+    b = w.get_bundle(w.config_tiny())
+    srv = ll.Server(hbm_budget_bytes=1 << 34, max_slots=2)
+    eps = np.array(b.eps_k, copy=True)
+    eps[1, 2] = np.nan
+    with pytest.raises(ll.LLError) as e:
+        srv.submit(5, None, 0.1, **_system(b, eps_k=eps))
+    assert e.value.code == ll.LL_EINVAL and "non-finite value in eps_k" in str(e.value)
+    assert srv.stats()["queued"] == 0
+    srv.close()
