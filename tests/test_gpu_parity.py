@@ -12,6 +12,8 @@ recursion amplifies rounding chaotically (a 1e-14 relative change of the local p
 moves the oracle's own 300-step loss function by 3e-3), so a pointwise comparison of two
 arithmetics there measures amplified rounding noise, not error.
 """
+from types import SimpleNamespace
+
 import numpy as np
 import pytest
 
@@ -112,10 +114,25 @@ def _coef_rel(got, want, n):
     return max(b, g, z)
 
 
+_ORACLE_RUNS = {}
+
+
+def _oracle(bundle, flavour, n, n_run=300):
+    """The oracle's first n coefficients (beta, gamma, z) on a bundle, in its own approximation.
+    Each recursion is sequential, so the first n coefficients of a longer run are those of an
+    n-step run: one run per bundle and flavour, of max(n, n_run) steps, serves every test."""
+    key = (id(bundle), flavour)
+    hit = _ORACLE_RUNS.get(key)
+    if hit is None or hit[0] is not bundle or len(hit[1].beta) < n:
+        hit = (bundle, lanczos.run(System(bundle), max(n, n_run), flavour))
+        _ORACLE_RUNS[key] = hit
+    co = hit[1]
+    return SimpleNamespace(beta=co.beta[:n], gamma=co.gamma[:n], z=co.z[:n])
+
+
 def test_ph_coefficients_small_fp64(lib, small):
     """Plain method, FP64: 300 pseudo-Hermitian steps (the small two-atom workload)."""
-    sys = System(small)
-    ref = lanczos.pseudo_hermitian(sys, 300)
+    ref = _oracle(small, "ph", 300)
     ch = chain_from_bundle(small, max_steps=300)
     got = ch.lanczos(300)
     assert _coef_rel(got, ref, 100) < 1e-10
@@ -135,8 +152,7 @@ def test_ph_resume_matches_single_call(lib, small):
 
 
 def test_nh_coefficients_small_fp64(lib, small):
-    sys = System(small)
-    ref = lanczos.non_hermitian(sys, 120)
+    ref = _oracle(small, "nh", 120)
     ch = chain_from_bundle(small, flavour="nh", max_steps=120)
     got = ch.lanczos(120)
     assert _coef_rel(got, ref, 100) < 1e-10
@@ -144,8 +160,7 @@ def test_nh_coefficients_small_fp64(lib, small):
 
 @pytest.mark.parametrize("flavour", ["ph", "nh"])
 def test_fp32_spectrum_small(lib, small, flavour):
-    sys = System(small)
-    ref = lanczos.run(sys, 300, flavour)
+    ref = _oracle(small, flavour, 300)
     ch = chain_from_bundle(small, flavour=flavour, precision="fp32", max_steps=300)
     got = ch.lanczos(300)
     assert _loss_err(got, (ref.beta, ref.gamma, ref.z), small.spec.omega, small.spec.q_cart) < 1e-3
@@ -162,8 +177,7 @@ def test_other_approximations_tiny(lib, tiny, approx):
 
 
 def test_device_spectrum_matches_oracle(lib, small):
-    sys = System(small)
-    ref = lanczos.pseudo_hermitian(sys, 200)
+    ref = _oracle(small, "ph", 200)
     ch = chain_from_bundle(small, max_steps=200)
     ch.lanczos(200)
     chi, ei, e = ch.spectrum(WGRID, ETA)
@@ -228,8 +242,7 @@ def test_split_path_single_application(lib, small, kb, precision, tol, monkeypat
 
 def test_split_path_coefficients_small(lib, small, monkeypatch):
     """Forced split path, 120 pseudo-Hermitian FP64 steps: the oracle's first 100 coefficients."""
-    sys = System(small)
-    ref = lanczos.pseudo_hermitian(sys, 120)
+    ref = _oracle(small, "ph", 120)
     monkeypatch.setenv("LL_SPLIT_PERK", "1")
     got = chain_from_bundle(small, max_steps=120).lanczos(120)
     assert _coef_rel(got, ref, 100) < 1e-10
@@ -269,8 +282,7 @@ def test_cubic8_non_hermitian(lib, cubic8):
 
 def test_split_path_non_hermitian_small(lib, small, monkeypatch):
     """Forced split path, 120 non-Hermitian FP64 steps: the oracle's first 100 coefficients."""
-    sys = System(small)
-    ref = lanczos.non_hermitian(sys, 120)
+    ref = _oracle(small, "nh", 120)
     monkeypatch.setenv("LL_SPLIT_PERK", "1")
     got = chain_from_bundle(small, flavour="nh", max_steps=120).lanczos(120)
     assert _coef_rel(got, ref, 100) < 1e-10
@@ -282,8 +294,7 @@ def test_extrapolated_spectrum(lib, small, kind):
     (ll_spectrum_x) and from the chain's own (ll_lanczos_spectrum_x), against the oracle's
     extrapolation and LAPACK solve on the same coefficients."""
     from oracle.extrapolation import extrapolate
-    sys = System(small)
-    ref = lanczos.pseudo_hermitian(sys, 200)
+    ref = _oracle(small, "ph", 200)
     s = small.spec
     eb, eg, ez = extrapolate(ref.beta, ref.gamma, ref.z, kind, 5000)
     rchi, _, _ = spectrum.spectrum(eb, eg, ez, s.omega, s.q_cart, WGRID, ETA)
