@@ -260,6 +260,15 @@ class Chain:
         return int(b.value)
 
 
+def footprint(**system) -> int:
+    """ll_footprint: an upper bound of the device bytes one chain of this system would hold
+    (what the request loop admits by), computed on the host without creating the chain."""
+    d, _keep = _make_desc(**system)
+    b = C.c_size_t(0)
+    _check(_lib.ll_footprint(C.byref(d), C.byref(b)))
+    return int(b.value)
+
+
 EXTRAP = {"no": LL_EXTRAP_NO, "constant": LL_EXTRAP_CONSTANT, "osc": LL_EXTRAP_OSC}
 
 

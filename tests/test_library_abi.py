@@ -111,3 +111,16 @@ def test_rejects_non_finite_input(ll, name, bad):
     with pytest.raises(ll.LLError) as e:
         ll.Chain(**args)
     assert e.value.code == ll.LL_EINVAL and f"non-finite value in {name}" in str(e.value)
+
+
+def test_footprint_bound_orders(ll):
+    """ll_footprint on the host: it grows with the coefficient capacity, with FP64 orbitals over
+    FP32 ones, and with the non-Hermitian chain's second vector; the KB workload's FP32 chain
+    at 1000 steps is a few GB at most (it is admitted under budgets of that order)."""
+    small = _desc_args(w.get_bundle(w.config_small()))
+    fp = lambda **kw: ll.footprint(**{**small, **kw})
+    assert fp(max_steps=100) < fp(max_steps=3000)
+    assert fp(precision="fp32") < fp(precision="fp64")
+    assert fp(flavour="ph") < fp(flavour="nh")
+    kb = _desc_args(w.get_bundle(w.config_kb()))
+    assert 1 << 20 < ll.footprint(**{**kb, "precision": "fp32", "max_steps": 1000}) < 8 << 30
