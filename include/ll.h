@@ -250,6 +250,10 @@ int ll_poll(ll_server* s, uint64_t job_id, int* state, ll_job_result* res);
  * A job that reaches its last step in that round, or that has already ended, keeps its
  * outcome (LL_OK).  LL_ENOTFOUND for an unknown id. */
 int ll_cancel(ll_server* s, uint64_t job_id);
+/* Frees the record of a job that has ended (after its results were polled); its id is unknown
+ * from then on.  LL_PENDING while the job is queued or running, LL_ENOTFOUND for an unknown id.
+ * Without it a server keeps every ended job's results until ll_server_destroy. */
+int ll_release(ll_server* s, uint64_t job_id);
 /* Device bytes held by running chains now and at most so far; running and queued jobs. */
 int ll_server_stats(ll_server* s, size_t* used, size_t* peak, int* running, int* queued);
 const char* ll_server_last_error(void);

@@ -104,13 +104,15 @@ void finish(ll_server* s, Job* j, int status, const std::string& err) {
   s->cv.notify_all();
 }
 
-void start_job(ll_server* s, Job* j) {
+// Creates the job's chain; true when it runs.  On false the job has ended (FAILED), and the
+// scheduler must not touch it again: its owner may release it at once.
+bool start_job(ll_server* s, Job* j) {
   std::string err;
   j->t_start = now_s();
   if (cudaStreamCreateWithFlags(&j->stream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     finish(s, j, LL_ECUDA, "stream creation failed");
-    return;
+    return false;
   }
   j->chain = (j->desc.precision == LL_PREC_FP64) ? ll::make_chain_f64() : ll::make_chain_f32();
   // the request loop's chains launch eagerly: with many chains sharing the GPU, replayed step
@@ -120,7 +122,7 @@ void start_job(ll_server* s, Job* j) {
   const int rc = j->chain->create(&j->desc, j->stream, err);
   if (rc != LL_OK) {
     finish(s, j, rc, "create: " + err);
-    return;
+    return false;
   }
   std::lock_guard<std::mutex> lock(s->mu);
   // account the real allocation instead of the estimate
@@ -129,6 +131,7 @@ void start_job(ll_server* s, Job* j) {
   j->footprint = real;
   s->peak = std::max(s->peak, s->used);
   j->state = LL_JOB_RUNNING;
+  return true;
 }
 
 void complete_job(ll_server* s, Job* j, int lanczos_rc, const std::string& lerr) {
@@ -175,8 +178,7 @@ void scheduler(ll_server* s) {
       }
     }
     for (Job* j : admit) {
-      start_job(s, j);
-      if (j->state == LL_JOB_RUNNING) {
+      if (start_job(s, j)) {
         std::lock_guard<std::mutex> lock(s->mu);
         s->running.push_back(j);
       }
@@ -358,6 +360,19 @@ int ll_cancel(ll_server* s, uint64_t id) {
   }
   // admitted or running: the scheduler ends it after its current round
   j->cancel.store(true);
+  return LL_OK;
+}
+
+int ll_release(ll_server* s, uint64_t id) {
+  if (!s) return sfail(LL_EINVAL, "null server");
+  std::lock_guard<std::mutex> lock(s->mu);
+  auto it = s->jobs.find(id);
+  if (it == s->jobs.end()) return sfail(LL_ENOTFOUND, "unknown job id");
+  Job* j = it->second;
+  // the scheduler no longer touches a job once it has ended
+  if (j->state != LL_JOB_DONE && j->state != LL_JOB_FAILED) return sfail(LL_PENDING, "the job has not ended");
+  s->jobs.erase(it);
+  delete j;
   return LL_OK;
 }
 

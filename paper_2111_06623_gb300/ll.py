@@ -69,6 +69,7 @@ def _load():
         "ll_submit": (C.c_int, [vp, vp, C.POINTER(C.c_uint64)]),
         "ll_poll": (C.c_int, [vp, C.c_uint64, C.POINTER(C.c_int), vp]),
         "ll_cancel": (C.c_int, [vp, C.c_uint64]),
+        "ll_release": (C.c_int, [vp, C.c_uint64]),
         "ll_server_stats": (C.c_int, [vp, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t), C.POINTER(C.c_int),
                                       C.POINTER(C.c_int)]),
         "ll_server_last_error": (C.c_char_p, []),
@@ -88,7 +89,7 @@ EXPORTS = ("ll_create", "ll_destroy", "ll_lanczos", "ll_lanczos_spectrum", "ll_s
            "ll_lanczos_spectrum_x", "ll_spectrum_x",
            "ll_apply", "ll_get_map", "ll_get_start", "ll_footprint", "ll_profile", "ll_profile_read", "ll_last_error",
            "ll_version", "ll_fma_peak", "ll_server_create",
-           "ll_server_set_chunk", "ll_submit", "ll_poll", "ll_cancel", "ll_server_stats", "ll_server_last_error",
+           "ll_server_set_chunk", "ll_submit", "ll_poll", "ll_cancel", "ll_release", "ll_server_stats", "ll_server_last_error",
            "ll_server_destroy")
 PROF_CLASSES = ("zinv", "xy1", "hxc", "xy2", "zfwd", "update")
 
@@ -380,6 +381,11 @@ class Server:
         """ll_cancel: a queued job ends at once, a running one after the current round; either
         ends FAILED with status LL_ECANCELED and keeps the coefficients of its finished steps."""
         _srv_check(_lib.ll_cancel(self._h, C.c_uint64(job_id)))
+
+    def release(self, job_id: int):
+        """ll_release: frees the record of an ended job (LL_PENDING while it runs)."""
+        _srv_check(_lib.ll_release(self._h, C.c_uint64(job_id)))
+        self._jobs.pop(job_id, None)
 
     def stats(self):
         used, peak = C.c_size_t(0), C.c_size_t(0)

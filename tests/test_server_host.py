@@ -81,3 +81,26 @@ def test_non_finite_job_refused_at_submit(ll):
     assert e.value.code == ll.LL_EINVAL and "non-finite value in eps_k" in str(e.value)
     assert srv.stats()["queued"] == 0
     srv.close()
+
+
+def test_release_ended_job(ll):
+    """ll_release frees an ended job's record; its id is unknown afterwards."""
+    b = w.get_bundle(w.config_tiny())
+    srv = ll.Server(hbm_budget_bytes=1 << 34, max_slots=2)
+    with pytest.raises(ll.LLError) as e:
+        srv.release(4242)
+    assert e.value.code == ll.LL_ENOTFOUND
+    jid = srv.submit(5, None, 0.1, **_system(b))
+    t0 = time.time()
+    while True:
+        try:
+            srv.release(jid)                    # LL_PENDING until the job has ended
+            break
+        except ll.LLError as err:
+            assert err.code == ll.LL_PENDING and time.time() - t0 < 60
+            time.sleep(0.01)
+    for call in (srv.poll, srv.cancel, srv.release):
+        with pytest.raises(ll.LLError) as e:
+            call(jid)
+        assert e.value.code == ll.LL_ENOTFOUND
+    srv.close()
