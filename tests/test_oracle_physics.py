@@ -5,7 +5,7 @@ import pytest
 
 import workloads as w
 from oracle import casida, lanczos, spectrum
-from oracle.liouvillian import System, axpy
+from oracle.liouvillian import System
 
 
 @pytest.fixture(scope="module")

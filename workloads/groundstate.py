@@ -11,7 +11,6 @@ LDA: Slater exchange + Perdew-Zunger 1981 correlation (Sec. 5), unpolarised.
 """
 from __future__ import annotations
 
-import functools
 import hashlib
 import json
 import os
