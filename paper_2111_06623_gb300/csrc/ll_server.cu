@@ -44,10 +44,10 @@ struct Job {
   ll::ChainBase* chain = nullptr;
   std::atomic<bool> cancel{false};  // set by ll_cancel, read by the scheduler between rounds
   cudaStream_t stream = nullptr;
-  int steps_done = 0;
+  std::atomic<int> steps_done{0};   // written by the scheduler, read by ll_poll
   std::vector<double> beta;
   std::vector<double> gamma, z, chi, eps_inv, eps;  // complex interleaved
-  double t_submit = 0, t_start = 0, t_done = 0;
+  double t_submit = 0, t_start = 0, t_done = 0;  // written and read under the server lock
 };
 
 }  // namespace
@@ -108,7 +108,6 @@ void finish(ll_server* s, Job* j, int status, const std::string& err) {
 // scheduler must not touch it again: its owner may release it at once.
 bool start_job(ll_server* s, Job* j) {
   std::string err;
-  j->t_start = now_s();
   if (cudaStreamCreateWithFlags(&j->stream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     finish(s, j, LL_ECUDA, "stream creation failed");
@@ -172,6 +171,7 @@ void scheduler(ll_server* s) {
              s->queue.front()->footprint <= s->budget - s->used) {
         Job* j = s->queue.front();
         s->queue.pop_front();
+        j->t_start = now_s();
         s->used += j->footprint;
         s->peak = std::max(s->peak, s->used);
         admit.push_back(j);
@@ -324,7 +324,8 @@ int ll_poll(ll_server* s, uint64_t id, int* state, ll_job_result* res) {
   const double t = now_s();
   res->status = j->status;
   res->steps_done = j->steps_done;
-  res->queue_s = (j->t_start > 0 ? j->t_start : t) - j->t_submit;
+  // a job that ended without admission (cancelled, server destroyed) waited until its end
+  res->queue_s = (j->t_start > 0 ? j->t_start : (j->t_done > 0 ? j->t_done : t)) - j->t_submit;
   res->run_s = j->t_start > 0 ? (j->t_done > 0 ? j->t_done : t) - j->t_start : 0.0;
   if (j->state == LL_JOB_DONE || j->state == LL_JOB_FAILED) {
     const size_t m = j->beta.size(), nw = j->chi.size() / 2;
