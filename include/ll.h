@@ -144,7 +144,9 @@ int ll_spectrum_x(const double* beta, const double* gamma, const double* z, int 
  * until the process exits), so it accepts at most LL_SPECTRUM_STATIC_MAX_COEF coefficients
  * and LL_SPECTRUM_STATIC_MAX_OMEGA frequencies and returns LL_EINVAL with a message beyond
  * that.  It calls no device allocator.  The first call on a device looks up that device's
- * address of the array (make that first call before any stream capture).  Every call on a
+ * address of the array in the current context (make that first call before any stream
+ * capture); the address is kept per device and looked up again when the device's context
+ * has changed since (after a cudaDeviceReset, for instance).  Every call on a
  * device shares the one array and leaves its contents behind: calls whose work may overlap on
  * the GPU (other host threads, other streams) race and must be serialised by the caller.
  * Returns after the results are on the host. */
@@ -189,8 +191,17 @@ int ll_profile(ll_handle* h, int enable);
  * Synchronises the stream.  Any output may be NULL. */
 int ll_profile_read(ll_handle* h, double* ms, long long* launches, long long* total);
 
-/* Device bytes a handle for this descriptor will hold (input arrays are not read). */
+/* Upper bound of the device bytes a handle for this descriptor will hold, the staging of a
+ * spectrum excluded (input arrays are not read; computed on the host).  Returns LL_EINVAL when
+ * the descriptor's sizes are missing. */
 int ll_footprint(const ll_system_desc* desc, size_t* bytes);
+
+/* Device bytes of the spectrum staging a handle adds for n_omega frequencies (the frequency
+ * grid and the chi, eps^-1, eps outputs, plus the extrapolation constants). */
+#define LL_SPECTRUM_BYTES(n_omega) ((size_t)(n_omega) * 56u + 256u)
+
+/* Device bytes the handle holds now (every allocation, the spectrum staging included). */
+int ll_bytes(ll_handle* h, size_t* bytes);
 
 const char* ll_last_error(void);
 const char* ll_version(void);

@@ -2,7 +2,9 @@
 nvcc, then linked into one shared library (CUDA runtime linked statically)."""
 from __future__ import annotations
 
+import hashlib
 import os
+import platform
 import shutil
 import subprocess
 from concurrent.futures import ThreadPoolExecutor
@@ -24,13 +26,29 @@ def _nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
+def source_hash(extra_flags: list[str] | None = None) -> str:
+    """sha256 over every source the library is built from, the flags and the nvcc version."""
+    h = hashlib.sha256()
+    files = sorted(f for f in os.listdir(SRC) if f.endswith((".cu", ".cuh")))
+    for p in [os.path.join(SRC, f) for f in files] + [os.path.join(ROOT, "include", "ll.h")]:
+        h.update(os.path.basename(p).encode() + b"\0")
+        with open(p, "rb") as fh:
+            h.update(fh.read())
+    h.update("\0".join(ARCH + FLAGS + list(extra_flags or []) + [platform.machine()]).encode())
+    r = subprocess.run([_nvcc(), "--version"], capture_output=True, text=True)
+    h.update(r.stdout.encode())
+    return h.hexdigest()
+
+
 def build_library(force: bool = False, extra_flags: list[str] | None = None) -> str:
-    srcs = [os.path.join(SRC, u + ".cu") for u in UNITS]
-    deps = srcs + [os.path.join(SRC, f) for f in os.listdir(SRC) if f.endswith(".cuh")] + \
-        [os.path.join(ROOT, "include", "ll.h")]
-    if (not force and os.path.exists(LIB_PATH)
-            and os.path.getmtime(LIB_PATH) >= max(os.path.getmtime(p) for p in deps)):
-        return LIB_PATH
+    """Build libll.so unless the one in the tree was built from exactly these sources, flags
+    and compiler (a content hash kept beside it, not file times); force=True always builds."""
+    digest = source_hash(extra_flags)
+    stamp = LIB_PATH + ".sha256"
+    if not force and os.path.exists(LIB_PATH) and os.path.exists(stamp):
+        with open(stamp) as fh:
+            if fh.read().strip() == digest:
+                return LIB_PATH
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
     flags = FLAGS + (extra_flags or [])
@@ -50,4 +68,7 @@ def build_library(force: bool = False, extra_flags: list[str] | None = None) -> 
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr[-4000:]}")
     os.replace(tmp, LIB_PATH)
+    with open(stamp + f".{os.getpid()}.tmp", "w") as fh:
+        fh.write(digest + "\n")
+    os.replace(stamp + f".{os.getpid()}.tmp", stamp)
     return LIB_PATH

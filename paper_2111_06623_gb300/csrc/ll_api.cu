@@ -1,5 +1,6 @@
 // C ABI of libll.so: argument checks, error strings, dispatch to the precision-specific
 // chain (FP64 or FP32).  See include/ll.h for the contract of every entry point.
+#include <cuda.h>
 #include <string.h>
 
 #include <mutex>
@@ -234,25 +235,68 @@ static __device__ __align__(256) unsigned char g_spectrum_scratch[kStaticBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_static_mu;
-unsigned char* g_static_addr[kMaxDevices] = {nullptr};
+// The looked-up address per device, tagged with the id of the context it was looked up in: a
+// context destroyed and re-created (cudaDeviceReset, a driver-level context switch) gets a new
+// id, and the address is looked up again in the new context.
+struct StaticSlot { unsigned long long ctx_id; unsigned char* addr; };
+StaticSlot g_static_slot[kMaxDevices] = {};
 
-// Device address of the staging array on the current device, looked up once per device.
+typedef CUresult (*PFN_ctx_get_current)(CUcontext*);
+typedef CUresult (*PFN_ctx_get_id)(CUcontext, unsigned long long*);
+
+// Id of the context current on this thread (0 when none is current yet).
+int current_ctx_id(unsigned long long* id, std::string& err) {
+  static PFN_ctx_get_current get_current = nullptr;
+  static PFN_ctx_get_id get_id = nullptr;
+  if (!get_current || !get_id) {
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    cudaError_t e1 = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
+    cudaError_t e2 = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || !f1 || !f2 || q1 != cudaDriverEntryPointSuccess ||
+        q2 != cudaDriverEntryPointSuccess) {
+      err = "driver entry points cuCtxGetCurrent/cuCtxGetId unavailable";
+      return LL_ECUDA;
+    }
+    get_current = reinterpret_cast<PFN_ctx_get_current>(f1);
+    get_id = reinterpret_cast<PFN_ctx_get_id>(f2);
+  }
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS) { err = "cuCtxGetCurrent failed"; return LL_ECUDA; }
+  *id = 0;
+  if (ctx && get_id(ctx, id) != CUDA_SUCCESS) { err = "cuCtxGetId failed"; return LL_ECUDA; }
+  return LL_OK;
+}
+
+// Device address of the staging array in the current device's current context.  The lookup
+// runs once per device and context: on the first call on a device (which also makes the
+// runtime initialise that device's primary context) and again after the context changed.
 int static_scratch(unsigned char** out, std::string& err) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) { err = std::string("cudaGetDevice: ") + cudaGetErrorString(e); return LL_ECUDA; }
   if (dev < 0 || dev >= kMaxDevices) { err = "device ordinal out of range"; return LL_EUNSUPPORTED; }
   std::lock_guard<std::mutex> lock(g_static_mu);
-  if (!g_static_addr[dev]) {
+  unsigned long long id = 0;
+  int rc = current_ctx_id(&id, err);
+  if (rc != LL_OK) return rc;
+  StaticSlot& slot = g_static_slot[dev];
+  if (id == 0 || slot.addr == nullptr || slot.ctx_id != id) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_spectrum_scratch);
     if (e != cudaSuccess || !p) {
       err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
       return LL_ECUDA;
     }
-    g_static_addr[dev] = static_cast<unsigned char*>(p);
+    if (id == 0) {   // no context was current before the lookup; the runtime has made one now
+      rc = current_ctx_id(&id, err);
+      if (rc != LL_OK) return rc;
+    }
+    slot.ctx_id = id;
+    slot.addr = static_cast<unsigned char*>(p);
   }
-  *out = g_static_addr[dev];
+  *out = slot.addr;
   return LL_OK;
 }
 
@@ -342,6 +386,12 @@ int ll_profile_read(ll_handle* h, double* ms, long long* launches, long long* to
   return rc == LL_OK ? LL_OK : fail(rc, "ll_profile_read: " + err);
 }
 
+int ll_bytes(ll_handle* h, size_t* bytes) {
+  if (!h || !bytes) return fail(LL_EINVAL, "bad arguments");
+  *bytes = h->chain->bytes();
+  return LL_OK;
+}
+
 int ll_footprint(const ll_system_desc* d, size_t* bytes) {
   if (!d || !bytes || !d->npw_k || !d->npw_kq || d->nks < 1 || d->nbnd < 1 || d->nfft < 1)
     return fail(LL_EINVAL, "bad footprint arguments");
@@ -358,7 +408,15 @@ int ll_footprint(const ll_system_desc* d, size_t* bytes) {
   const size_t orb = (size_t)d->nks * d->nbnd;
   // columns per sphere are at most the sphere size; bounded by pq for the estimate
   const size_t cb = nvec * orb * d->nfft * pq;
-  const size_t ngroups = (4 * 152 + d->nfft - 1) / d->nfft;
+  // density slot planes: 4 per SM of the current device (152 where none can be queried)
+  int nsm = 152;
+  {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+      nsm = std::max(nsm, n);
+    cudaGetLastError();
+  }
+  const size_t ngroups = (4 * (size_t)nsm + d->nfft - 1) / d->nfft;
   size_t b = elem * (vq * (3 * nvec + nvec + 2) + orb * pk + orb * n3 + cb + ngroups * n3 + 3 * n3 +
                      (size_t)d->nks * d->nproj * pq);
   // Lanczos partials: up to max(bands, plane-wave chunks) per k and step (band groups or the

@@ -149,6 +149,13 @@ void complete_job(ll_server* s, Job* j, int lanczos_rc, const std::string& lerr)
       j->eps.resize(2 * (size_t)nw);
       const int rc = j->chain->spectrum(m, LL_EXTRAP_NO, 0, j->omega.data(), nw, j->eta, j->chi.data(), j->eps_inv.data(),
                                         j->eps.data(), err);
+      {   // the spectrum's staging buffers are device memory too
+        std::lock_guard<std::mutex> lock(s->mu);
+        const size_t real = j->chain->bytes();
+        s->used = s->used - j->footprint + real;
+        j->footprint = real;
+        s->peak = std::max(s->peak, s->used);
+      }
       if (rc != LL_OK && lanczos_rc == LL_OK) {
         finish(s, j, rc, "spectrum: " + err);
         return;
@@ -167,8 +174,10 @@ void scheduler(ll_server* s) {
       if (s->running.empty() && s->queue.empty())
         s->cv.wait_for(lock, std::chrono::milliseconds(50), [&] { return s->stop || !s->queue.empty(); });
       if (s->stop) break;
+      // used can exceed the budget when a chain's real bytes exceed its estimate: no admission
+      // then (and no unsigned wrap of budget - used)
       while (!s->queue.empty() && (int)s->running.size() + (int)admit.size() < s->max_slots &&
-             s->queue.front()->footprint <= s->budget - s->used) {
+             s->used <= s->budget && s->queue.front()->footprint <= s->budget - s->used) {
         Job* j = s->queue.front();
         s->queue.pop_front();
         j->t_start = now_s();
@@ -264,6 +273,7 @@ int ll_submit(ll_server* s, const ll_job_desc* jd, uint64_t* job_id) {
   }
   size_t fp = 0;
   if (ll_footprint(d, &fp) != LL_OK) return sfail(LL_EINVAL, "footprint");
+  if (jd->n_omega > 0) fp += LL_SPECTRUM_BYTES(jd->n_omega);
   if (fp > s->budget) return sfail(LL_ENOMEM, "job footprint exceeds the whole HBM budget");
   Job* j = new Job();
   size_t sk = 0, sq = 0;

@@ -62,6 +62,7 @@ def _load():
         "ll_get_map": (C.c_int, [vp, _ip]),
         "ll_get_start": (C.c_int, [vp, _dp]),
         "ll_footprint": (C.c_int, [C.POINTER(SystemDesc), C.POINTER(C.c_size_t)]),
+        "ll_bytes": (C.c_int, [vp, C.POINTER(C.c_size_t)]),
         "ll_profile": (C.c_int, [vp, C.c_int]),
         "ll_profile_read": (C.c_int, [vp, _dp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
         "ll_server_create": (C.c_int, [C.c_size_t, C.c_int, C.POINTER(vp)]),
@@ -87,7 +88,7 @@ def _load():
 _lib = _load()
 EXPORTS = ("ll_create", "ll_destroy", "ll_lanczos", "ll_lanczos_spectrum", "ll_spectrum", "ll_spectrum_static",
            "ll_lanczos_spectrum_x", "ll_spectrum_x",
-           "ll_apply", "ll_get_map", "ll_get_start", "ll_footprint", "ll_profile", "ll_profile_read", "ll_last_error",
+           "ll_apply", "ll_get_map", "ll_get_start", "ll_footprint", "ll_bytes", "ll_profile", "ll_profile_read", "ll_last_error",
            "ll_version", "ll_fma_peak", "ll_server_create",
            "ll_server_set_chunk", "ll_submit", "ll_poll", "ll_cancel", "ll_release", "ll_server_stats", "ll_server_last_error",
            "ll_server_destroy")
@@ -259,6 +260,17 @@ class Chain:
         b = C.c_size_t(0)
         _check(_lib.ll_footprint(C.byref(self.desc), C.byref(b)))
         return int(b.value)
+
+    def bytes(self) -> int:
+        """ll_bytes: device bytes the chain holds now."""
+        b = C.c_size_t(0)
+        _check(_lib.ll_bytes(self._h, C.byref(b)))
+        return int(b.value)
+
+
+def spectrum_bytes(n_omega: int) -> int:
+    """LL_SPECTRUM_BYTES: device bytes of a chain's spectrum staging for n_omega frequencies."""
+    return int(n_omega) * 56 + 256
 
 
 def footprint(**system) -> int:

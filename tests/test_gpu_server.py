@@ -159,3 +159,20 @@ def test_cancel_queued_and_running_jobs(ll):
     srv.cancel(nxt)                                # already ended: unchanged
     assert srv.poll(nxt)[0] == 2
     srv.close()
+
+
+@pytest.mark.parametrize("cell", ["small", "kb", "cubic8"])
+@pytest.mark.parametrize("flavour,precision", [("ph", "fp32"), ("nh", "fp64")])
+def test_chain_bytes_within_footprint(ll, cell, flavour, precision):
+    """The request loop admits by ll_footprint (plus the spectrum staging): the device bytes a
+    chain really holds after its steps and its spectrum never exceed that bound."""
+    b = {"small": w.config_small, "kb": w.config_kb, "cubic8": w.config_cubic8}[cell]()
+    b = w.get_bundle(b)
+    ch = chain_from_bundle(b, flavour=flavour, precision=precision, max_steps=12)
+    ch.lanczos(12)
+    wgrid = np.linspace(0.0, 40.0, 4001)
+    ch.spectrum(wgrid, 0.1, extrapolation="osc", m_total=200)
+    held = ch.bytes()
+    bound = ch.footprint() + ll.spectrum_bytes(len(wgrid))
+    ch.close()
+    assert 0 < held <= bound, (held, bound)

@@ -41,6 +41,21 @@ def test_static_matches_allocating_entry_twice(lib):
             assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(b)), call
 
 
+def test_static_at_the_limits_then_smaller(lib):
+    """The largest accepted call uses the end of every region of the static array; a smaller
+    call right after it must not see what the larger one left behind."""
+    omega_cell, q = 270.011394, np.array([0.0612396, 0.0, 0.0])
+    big_w = np.linspace(0.0, 40.0, lib.SPECTRUM_STATIC_MAX_OMEGA)
+    small_w = np.linspace(1.0, 30.0, 777)
+    for m, w, seed in [(lib.SPECTRUM_STATIC_MAX_COEF, big_w, 5), (97, small_w, 6)]:
+        beta, gamma, z = _coefficients(m, seed)
+        ref = lib.spectrum(beta, gamma, z, omega_cell, q, w, 0.1)
+        got = lib.spectrum_static(beta, gamma, z, omega_cell, q, w, 0.1)
+        for a, b in zip(got, ref):
+            assert a.shape == b.shape
+            assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(b)), m
+
+
 def test_static_rejects_oversize(lib):
     beta, gamma, z = _coefficients(lib.SPECTRUM_STATIC_MAX_COEF + 2, 3)
     with pytest.raises(lib.LLError) as e:
