@@ -5,10 +5,12 @@ Conventions (fixed for the whole oracle):
   psi(r_j) = sum_G c_G e^{i G.r_j}                  (no 1/N^3; u(r) = psi(r)/sqrt(Omega))
   f_G = (1/N^3) sum_j f(r_j) e^{-i G.r_j}
 A Miller index m maps to the grid frequency index m mod N.
+The 3D transforms are scipy.fft's (pocketfft, the same plain DFT definitions as numpy.fft).
 """
 from __future__ import annotations
 
 import numpy as np
+import scipy.fft as sfft
 
 
 def grid_index(miller: np.ndarray, n: int) -> np.ndarray:
@@ -24,12 +26,12 @@ def to_grid(coef: np.ndarray, miller: np.ndarray, n: int) -> np.ndarray:
     g = np.zeros(lead + (n ** 3,), dtype=np.complex128)
     g[..., grid_index(miller, n)] = coef
     g = g.reshape(lead + (n, n, n))
-    return np.fft.ifftn(g, axes=(-3, -2, -1)) * n ** 3
+    return sfft.ifftn(g, axes=(-3, -2, -1)) * n ** 3
 
 
 def to_sphere(f: np.ndarray, miller: np.ndarray, n: int) -> np.ndarray:
     """f_G = (1/N^3) sum_j f(r_j) e^{-iG.r_j} at the sphere's G: (..., N, N, N) -> (..., npw)."""
-    fg = np.fft.fftn(f, axes=(-3, -2, -1)) / n ** 3
+    fg = sfft.fftn(f, axes=(-3, -2, -1)) / n ** 3
     lead = fg.shape[:-3]
     return fg.reshape(lead + (n ** 3,))[..., grid_index(miller, n)]
 

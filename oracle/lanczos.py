@@ -62,11 +62,14 @@ class Coefficients:
         return float(self.beta[0])
 
 
-def pseudo_hermitian(sys: System, nsteps: int, breakdown_tol: float = 1e-28) -> Coefficients:
+def pseudo_hermitian(sys: System, nsteps: int, breakdown_tol: float = 1e-28, on_step=None) -> Coefficients:
+    """on_step(j), when given, is called once step j's coefficients are known (timing hook)."""
     y = sys.starting_vector()
     r, r_upper = y, False                        # r_1 = (0, y): lower half
     x = sys.apply_op(r, upper=False)             # X_1 = D y
     applies = 1
+    if on_step:
+        on_step(1)
     b2 = sys.inner(r, x).real
     if b2 <= 0:
         raise Breakdown("metric not positive at step 1")
@@ -88,12 +91,15 @@ def pseudo_hermitian(sys: System, nsteps: int, breakdown_tol: float = 1e-28) -> 
         if b2 <= breakdown_tol * beta[0] ** 2:
             raise Breakdown(f"non-positive metric or breakdown at step {j + 1}: {b2:.3e}")
         beta.append(np.sqrt(b2))
+        if on_step:
+            on_step(j + 1)
     beta = np.array(beta)
     return Coefficients(beta=beta, gamma=beta.astype(np.complex128), z=np.array(z, dtype=np.complex128),
                         applies=applies, flavour="ph")
 
 
-def non_hermitian(sys: System, nsteps: int, breakdown_tol: float = 1e-28) -> Coefficients:
+def non_hermitian(sys: System, nsteps: int, breakdown_tol: float = 1e-28, on_step=None) -> Coefficients:
+    """on_step(j), when given, is called once step j's coefficients are known (timing hook)."""
     y = sys.starting_vector()
     b1 = np.sqrt(sys.inner(y, y).real)
     v = scale(1.0 / b1, y)                       # v_1 = w_1 = (0, y)/|y|: lower halves
@@ -125,9 +131,12 @@ def non_hermitian(sys: System, nsteps: int, breakdown_tol: float = 1e-28) -> Coe
         upper = not upper
         beta.append(bn)
         gamma.append(gn)
+        if on_step:
+            on_step(j + 1)
     return Coefficients(beta=np.array(beta, dtype=np.float64), gamma=np.array(gamma, dtype=np.complex128),
                         z=np.array(z, dtype=np.complex128), applies=applies, flavour="nh")
 
 
-def run(sys: System, nsteps: int, flavour: str) -> Coefficients:
-    return pseudo_hermitian(sys, nsteps) if flavour == "ph" else non_hermitian(sys, nsteps)
+def run(sys: System, nsteps: int, flavour: str, on_step=None) -> Coefficients:
+    return (pseudo_hermitian(sys, nsteps, on_step=on_step) if flavour == "ph"
+            else non_hermitian(sys, nsteps, on_step=on_step))

@@ -22,6 +22,7 @@ projectors; the Hartree kernel runs over every frequency of the FFT box.
 from __future__ import annotations
 
 import numpy as np
+import scipy.fft as sfft
 
 from . import basis, xc
 
@@ -65,8 +66,9 @@ class System:
             raise ValueError("Q + G = 0 on the grid: Q must not be a reciprocal lattice vector")
         self.whart = 4 * np.pi / qg2
         self.fxc = xc.fxc(self.rho) if self.approx == "tddft" else np.zeros_like(self.rho)
-        # ground-state orbitals u_{vk}(r) (times sqrt(Omega)) on the grid
-        self.ur = [basis.to_grid(self.uk[k], self.mk[k], n) for k in range(self.nks)]
+        # ground-state orbitals u_{vk}(r) (times sqrt(Omega)) on the grid, each k-point's
+        # transformed when first used (a rank of the k-point split touches only its own block)
+        self.ur = _LazyGrids(self.uk, self.mk, n)
         self.map_k_kq = [basis.intersection_map(self.mk[k], self.mkq[k]) for k in range(self.nks)]
 
     # ----- batches -------------------------------------------------------------------
@@ -132,7 +134,7 @@ class System:
 
     def hxc_potential(self, nr):
         """v'(r) = sum_G 4 pi n'(G)/|Q+G|^2 e^{iG.r} + f_xc(n0(r)) n'(r)."""
-        vh = np.fft.ifftn(self.whart * np.fft.fftn(nr))
+        vh = sfft.ifftn(self.whart * sfft.fftn(nr))
         return vh + self.fxc * nr
 
     def apply_k(self, x):
@@ -160,6 +162,24 @@ class System:
         new_up = self.apply_op(lo, upper=False) if lo is not None else None
         new_lo = self.apply_op(up, upper=True) if up is not None else None
         return new_up, new_lo
+
+
+class _LazyGrids:
+    """ur[k] = u_{vk}(r) sqrt(Omega) on the grid (basis.to_grid), computed once on first access."""
+
+    def __init__(self, coefs, millers, n):
+        self.coefs, self.millers, self.n = coefs, millers, n
+        self.cache = {}
+
+    def __len__(self):
+        return len(self.coefs)
+
+    def __getitem__(self, k):
+        g = self.cache.get(k)
+        if g is None:
+            g = basis.to_grid(self.coefs[k], self.millers[k], self.n)
+            self.cache[k] = g
+        return g
 
 
 def axpy(a, x, y):

@@ -401,6 +401,20 @@ def load_bundle(spec: SystemSpec, path: str) -> Bundle:
                   beta_kq=beta, dij=z["dij"], scf_iters=int(z["scf_iters"]), gap_min=float(z["gap_min"]))
 
 
+def bundle_digest(b: Bundle) -> str:
+    """sha256 (16 hex digits) of every array a chain consumes, in a fixed order: two bundles
+    with the same digest are the same input to the last bit.  (A bundle rebuilt by another
+    machine's LAPACK differs in the last bits of the orbitals, and so in its digest.)"""
+    h = hashlib.sha256()
+    arrays = [b.kcart, b.eps_k, b.vloc_r, b.rho_r, b.dij] + list(b.miller_k) + list(b.miller_kq) + \
+        list(b.u_k) + list(b.u_kq) + list(b.beta_kq)
+    for a in arrays:
+        a = np.ascontiguousarray(a)
+        h.update(str(a.dtype).encode() + str(a.shape).encode())
+        h.update(a.tobytes())
+    return h.hexdigest()[:16]
+
+
 def cached_bundle(spec: SystemSpec) -> Bundle | None:
     """The cached bundle of spec, or None when it has not been built here."""
     path = os.path.join(cache_dir(), f"{spec.name}_{_spec_key(spec)}.npz")
