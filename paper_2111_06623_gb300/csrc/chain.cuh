@@ -13,6 +13,9 @@
 
 #include "ll.h"
 #include "split.cuh"
+#include "tcproj.cuh"
+
+#include <type_traits>
 
 namespace ll {
 
@@ -225,7 +228,7 @@ class Chain : public ChainBase {
   ~Chain() override {
     for (cudaGraphExec_t& g : graph_)
       if (g) cudaGraphExecDestroy(g);
-    for (void* p : ptrs_) cudaFree(p);
+    for (auto& p : ptrs_) cudaFree(p.first);
   }
   size_t bytes() const override { return bytes_; }
 
@@ -338,6 +341,17 @@ class Chain : public ChainBase {
       split_ = best == 0 || 4 * best < nbnd_ || (env && env[0] == '1' && env[1] == 0);
       nchunk_ = split_ ? (pq + kChunk - 1) / kChunk : 1;
       npk_ = split_ ? nchunk_ : ngrp_;
+      // FP32 path: the split path's dot blocks on the tensor cores (tcproj.cuh) where their
+      // rows fit one M = 128 tile (LL_TC=0 in the environment keeps them on the CUDA cores)
+      const char* tce = getenv("LL_TC");
+      const bool tc = std::is_same<T, float>::value && split_ && !(tce && tce[0] == '0' && tce[1] == 0);
+      tc_nb_op_ = round_up(3 * nbnd_, 32);
+      tc_nb_u_ = round_up(nbnd_, 32);
+      tc_op_ = tc && nproj_ + 2 * nbnd_ <= 128 && tc_nb_op_ <= 256 && nproj_ + 3 * nbnd_ <= kTcMaxF4 * kTcThreads / kTcF4;
+      tc_u_ = tc && 2 * nbnd_ <= 128;
+      tc_u2_ = tc && 4 * nbnd_ <= 128;
+      tc_nb_ap_ = round_up(2 * nbnd_, 32);
+      tc_ap_ = tc && tc_nb_ap_ <= 128;
     }
     const long nzp = (long)nks_ * npk_;               // partials per vector and step
     const long nzv = nzp * nvec_;
@@ -497,7 +511,9 @@ class Chain : public ChainBase {
           const size_t sm = (size_t)(2 * nbnd_) * kTileP * sizeof(cplx<T>);
           if ((rc = set_smem(k_sp_nh_start<T>, sm, err))) return rc;
           k_sp_nh_start<T><<<dim3(nks_, nchunk_), 256, sm, st_>>>(j, upper, nks_, nbnd_, pq, dq_.npw, nchunk_, XV(),
-                                                                  XW(), VpNH(), Wp(), Vc(), y_, ukq_, co, sp_s_);
+                                                                  XW(), VpNH(), Wp(), Vc(), y_, ukq_, co, sp_s_,
+                                                                  tc_u2_ ? 0 : 1);
+          if (tc_u2_ && (rc = tc_dots<TC_U2>(1, tc_nb_u_, nullptr, XV(), XW(), nullptr, sp_s_, err))) return rc;
           k_sp_nh_proj<T><<<dim3(nks_, nchunk_), 256, 0, st_>>>(nks_, nbnd_, pq, dq_.npw, nchunk_, XV(), XW(), ukq_,
                                                                 sp_s_, spart_);
           prof_.count(LL_PROF_UPDATE, 1);
@@ -585,8 +601,10 @@ class Chain : public ChainBase {
     if (herr[0] != DEV_OK) {
       steps_ = std::min(steps_, herr[1] - 1);
       queued_ = steps_;
-      status = (herr[0] == DEV_NOTPD) ? LL_ENOTPD : LL_EBREAKDOWN;
-      err = (status == LL_ENOTPD) ? "pseudo-Hermitian metric not positive" : "Lanczos breakdown";
+      status = (herr[0] == DEV_NOTPD) ? LL_ENOTPD : (herr[0] == DEV_TIMEOUT ? LL_ETIMEOUT : LL_EBREAKDOWN);
+      err = (status == LL_ENOTPD)     ? "pseudo-Hermitian metric not positive"
+            : (status == LL_ETIMEOUT) ? "a bounded tensor-core wait gave up"
+                                      : "Lanczos breakdown";
       stopped_ = true;
     }
     if (done) *done = steps_;
@@ -754,6 +772,59 @@ class Chain : public ChainBase {
     }
     return LL_EUNSUPPORTED;
   }
+  // The split path's chunk dot blocks on the tensor cores (FP32 path only; tcproj.cuh).
+  template <int MODE>
+  int tc_dots(int nvec, int nb, const cplx<T>* x, const cplx<T>* t, const cplx<T>* t2, cplx<double>* cpart,
+              cplx<double>* spart, std::string& err) {
+    if constexpr (std::is_same<T, float>::value) {
+      TcDotsArgs a;
+      a.nks = nks_; a.nbnd = nbnd_; a.npw_pad = hq_.npw_pad; a.nchunk = nchunk_; a.nproj = nproj_; a.nb = nb;
+      a.npw = dq_.npw;
+      a.x = reinterpret_cast<const float4*>(x);
+      a.t = reinterpret_cast<const float4*>(t);
+      a.t2 = reinterpret_cast<const float4*>(t2);
+      a.ukq = reinterpret_cast<const float4*>(ukq_);
+      a.bkq = reinterpret_cast<const float4*>(bkq_);
+      a.cpart = cpart; a.spart = spart; a.err = err_; a.jdev = jdev_;
+      const size_t sm = tc_dots_smem(nb);
+      int rc;
+      if ((rc = set_smem(k_tc_dots<MODE>, sm, err))) return rc;
+      k_tc_dots<MODE><<<dim3(nks_, nvec, nchunk_), kTcThreads, sm, st_>>>(a);
+      LL_CK(cudaGetLastError());
+      return LL_OK;
+    } else {
+      err = "tensor-core projections are FP32-path only";
+      return LL_EUNSUPPORTED;
+    }
+  }
+
+  // t <- t + B c - U S on the tensor cores (FP32 path only; tcproj.cuh): nproj 0 applies P_c
+  // alone (the update), x and part give the norm partial.
+  int tc_apply(int nvec, int nproj, const cplx<T>* x, cplx<T>* t, double* part, std::string& err) {
+    if constexpr (std::is_same<T, float>::value) {
+      TcApplyArgs a;
+      a.nks = nks_; a.nbnd = nbnd_; a.npw_pad = hq_.npw_pad; a.nchunk = nchunk_; a.nproj = nproj;
+      a.nb = tc_nb_ap_;
+      a.nks_k = (2 * (nproj + nbnd_) + 15) / 16;
+      a.npw = dq_.npw;
+      a.x = part ? reinterpret_cast<const float2*>(x) : nullptr;
+      a.t = reinterpret_cast<float2*>(t);
+      a.ukq = reinterpret_cast<const float2*>(ukq_);
+      a.bkq = reinterpret_cast<const float2*>(bkq_);
+      a.coef = reinterpret_cast<const float2*>(sp_coef_);
+      a.part = part; a.err = err_; a.jdev = jdev_;
+      const size_t sm = tc_apply_smem(a.nb, a.nks_k);
+      int rc;
+      if ((rc = set_smem(k_tc_apply, sm, err))) return rc;
+      k_tc_apply<<<dim3(nks_, nvec, nchunk_), kTcThreads, sm, st_>>>(a);
+      LL_CK(cudaGetLastError());
+      return LL_OK;
+    } else {
+      err = "tensor-core projections are FP32-path only";
+      return LL_EUNSUPPORTED;
+    }
+  }
+
   // split per-k path (split.cuh): several CTAs per k-point, chunk partials reduced in order
   template <int N>
   int zfwd_split_n(int nvec, const cplx<T>* in, cplx<T>* out, std::string& err) {
@@ -767,11 +838,19 @@ class Chain : public ChainBase {
     if ((rc = set_smem(k_sp_dots<T>, sm_d, err)) || (rc = set_smem(k_sp_coef<T>, sm_c, err)) ||
         (rc = set_smem(k_sp_apply<T>, sm_a, err)))
       return rc;
-    k_sp_dots<T><<<dim3(nks_, nvec, nchunk_), 256, sm_d, st_>>>(nks_, nbnd_, pq, dq_.npw, nchunk_, nproj_, in, out,
-                                                                ukq_, bkq_, sp_c_, sp_s_);
+    if (tc_op_) {
+      if ((rc = tc_dots<TC_OP>(nvec, tc_nb_op_, in, out, nullptr, sp_c_, sp_s_, err))) return rc;
+    } else {
+      k_sp_dots<T><<<dim3(nks_, nvec, nchunk_), 256, sm_d, st_>>>(nks_, nbnd_, pq, dq_.npw, nchunk_, nproj_, in, out,
+                                                                  ukq_, bkq_, sp_c_, sp_s_);
+    }
     k_sp_coef<T><<<nks_ * nvec, 256, sm_c, st_>>>(nks_, nbnd_, nchunk_, nproj_, dij_, ub_, sp_c_, sp_s_, sp_coef_);
-    k_sp_apply<T><<<dim3(nks_, nvec, nchunk_), 256, sm_a, st_>>>(nks_, nbnd_, pq, dq_.npw, nchunk_, nproj_, in, out,
-                                                                 ukq_, bkq_, sp_coef_, part_);
+    if (tc_ap_) {
+      if ((rc = tc_apply(nvec, nproj_, in, out, part_, err))) return rc;
+    } else {
+      k_sp_apply<T><<<dim3(nks_, nvec, nchunk_), 256, sm_a, st_>>>(nks_, nbnd_, pq, dq_.npw, nchunk_, nproj_, in,
+                                                                   out, ukq_, bkq_, sp_coef_, part_);
+    }
     LL_CK(cudaGetLastError());
     return LL_OK;
   }
@@ -783,14 +862,19 @@ class Chain : public ChainBase {
     if ((rc = set_smem(k_sp_start<T>, sm, err))) return rc;
     Coef co{beta_, gamma_, zpart_, err_};
     k_sp_start<T><<<dim3(nks_, nchunk_), 256, sm, st_>>>(jdev_, nks_, nbnd_, pq, dq_.npw, nchunk_, part_, R(), X(), Vp(),
-                                                         y_, ukq_, co, tol_, sp_s_);
+                                                         y_, ukq_, co, tol_, sp_s_, tc_u_ ? 0 : 1);
+    if (tc_u_ && (rc = tc_dots<TC_U>(1, tc_nb_u_, nullptr, R(), nullptr, nullptr, sp_s_, err))) return rc;
     // P_c with the chunk-reduced coefficients, tiled (U read once per chunk for all bands),
     // then the axis-3 inverse FFTs over many CTAs per k
     const size_t sm_a = (size_t)nbnd_ * (nbnd_ + kSub) * sizeof(cplx<T>);
     if ((rc = set_smem(k_sp_apply<T>, sm_a, err))) return rc;
     k_sp_coef<T><<<nks_, 256, 0, st_>>>(nks_, nbnd_, nchunk_, 0, dij_, ub_, sp_c_, sp_s_, sp_coef_);
-    k_sp_apply<T><<<dim3(nks_, 1, nchunk_), 256, sm_a, st_>>>(nks_, nbnd_, pq, dq_.npw, nchunk_, 0, nullptr, R(), ukq_,
-                                                              bkq_, sp_coef_, nullptr);
+    if (tc_ap_) {
+      if ((rc = tc_apply(1, 0, nullptr, R(), nullptr, err))) return rc;
+    } else {
+      k_sp_apply<T><<<dim3(nks_, 1, nchunk_), 256, sm_a, st_>>>(nks_, nbnd_, pq, dq_.npw, nchunk_, 0, nullptr, R(),
+                                                                ukq_, bkq_, sp_coef_, nullptr);
+    }
     k_zinv<T, N><<<dim3(nks_, 1, zsplit()), 128, 0, st_>>>(dq_, R(), nbnd_, cbuf_, cb_ncol_);
     LL_CK(cudaGetLastError());
     return LL_OK;
@@ -986,7 +1070,7 @@ class Chain : public ChainBase {
     void* q = nullptr;
     const size_t nbytes = sizeof(U) * (size_t)std::max(1L, count);
     if (cudaMalloc(&q, nbytes) != cudaSuccess) { cudaGetLastError(); return LL_ENOMEM; }
-    ptrs_.push_back(q);
+    ptrs_.push_back({q, nbytes});
     bytes_ += nbytes;
     *p = static_cast<U*>(q);
     return LL_OK;
@@ -994,8 +1078,14 @@ class Chain : public ChainBase {
   template <typename U>
   void release(U* p) {
     if (!p) return;
-    auto it = std::find(ptrs_.begin(), ptrs_.end(), (void*)p);
-    if (it != ptrs_.end()) { cudaFree(p); ptrs_.erase(it); }
+    auto it = std::find_if(ptrs_.begin(), ptrs_.end(), [&](const std::pair<void*, size_t>& a) {
+      return a.first == (void*)p;
+    });
+    if (it != ptrs_.end()) {
+      cudaFree(p);
+      bytes_ -= it->second;
+      ptrs_.erase(it);
+    }
   }
   int upload_sphere(const HostSphere& h, SphereDev& dsph, std::string& err) {
     int *npw, *ncol, *nrow, *cs;
@@ -1048,7 +1138,7 @@ class Chain : public ChainBase {
   double omega_ = 0, q_[3] = {0, 0, 0}, tol_ = 0;
   HostSphere hk_, hq_;
   SphereDev dk_{}, dq_{};
-  std::vector<void*> ptrs_;
+  std::vector<std::pair<void*, size_t>> ptrs_;   // every allocation and its size
   size_t bytes_ = 0;
   T *whart_ = nullptr, *kin_ = nullptr, *vloc_ = nullptr, *fxc_ = nullptr;
   double *rho_ = nullptr, *eps_ = nullptr, *dij_ = nullptr, *part_ = nullptr, *beta_ = nullptr;
@@ -1062,6 +1152,9 @@ class Chain : public ChainBase {
   bool eager_done_[2] = {false, false};
   cudaGraphExec_t graph_[2] = {nullptr, nullptr};   // one captured step per parity of j
   bool split_ = false;      // per-k work split over chunks of plane waves (split.cuh)
+  bool tc_op_ = false, tc_u_ = false, tc_u2_ = false;   // split-path dot blocks on the tensor cores
+  bool tc_ap_ = false;                                    // split-path projections applied on the tensor cores
+  int tc_nb_op_ = 32, tc_nb_u_ = 32, tc_nb_ap_ = 32;      // N of those MMAs (Bop rows, padded to 32)
   int nchunk_ = 1;          // plane-wave chunks per k on the split path
   int bpc_ = 1, ngrp_ = 1;  // bands per CTA of the per-k kernels, band groups per k
   int npk_ = 1;             // partial sums per k of the Lanczos scalars (ngrp_, or nchunk_ split)

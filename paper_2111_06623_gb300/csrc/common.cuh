@@ -50,6 +50,6 @@ struct FastDiv {
 
 // Device status word: the kernels never trap; a detected fault sets a code here and the
 // host turns it into an ll_status after the call.
-enum DevErr : int { DEV_OK = 0, DEV_NOTPD = 1, DEV_BREAKDOWN = 2, DEV_BOUNDS = 3 };
+enum DevErr : int { DEV_OK = 0, DEV_NOTPD = 1, DEV_BREAKDOWN = 2, DEV_BOUNDS = 3, DEV_TIMEOUT = 4 };
 
 }  // namespace ll

@@ -96,7 +96,8 @@ __global__ void __launch_bounds__(256) k_sp_start(const int* __restrict__ jdev, 
                                                   const double* __restrict__ part, cplx<T>* __restrict__ R,
                                                   const cplx<T>* __restrict__ X, cplx<T>* __restrict__ Vp,
                                                   const cplx<T>* __restrict__ y, const cplx<T>* __restrict__ ukq,
-                                                  Coef co, double tol, cplx<double>* __restrict__ spart) {
+                                                  Coef co, double tol, cplx<double>* __restrict__ spart,
+                                                  int dots) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int j = *jdev, r_upper = (j % 2 == 0) ? 1 : 0;   // step index from the device counter
   cplx<T>* tile = reinterpret_cast<cplx<T>*>(smem_raw);
@@ -145,6 +146,7 @@ __global__ void __launch_bounds__(256) k_sp_start(const int* __restrict__ jdev, 
     R[i] = X[i] * ib - Vp[i] * bb;
     Vp[i] = r * ib;
   }
+  if (!dots) return;   // the partial U^H r_{j+1} comes from the tensor-core kernel
   __syncthreads();
   chunk_dots<T>(ukq + base, npw_pad, R + base, npw_pad, g0, max(g0, min(g1, npw[k])), nbnd, nbnd, tile,
                 spart + ((long)k * nchunk + c) * nbnd * nbnd);
@@ -349,7 +351,7 @@ __global__ void __launch_bounds__(256) k_sp_nh_start(int j, int upper, int nks, 
                                                      cplx<T>* __restrict__ XW, const cplx<T>* __restrict__ Vp,
                                                      const cplx<T>* __restrict__ Wp, const cplx<T>* __restrict__ Vc,
                                                      const cplx<T>* __restrict__ y, const cplx<T>* __restrict__ ukq,
-                                                     Coef co, cplx<double>* __restrict__ spart2) {
+                                                     Coef co, cplx<double>* __restrict__ spart2, int dots) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx<T>* tile = reinterpret_cast<cplx<T>*>(smem_raw);
   __shared__ double zred[2][8];
@@ -387,6 +389,7 @@ __global__ void __launch_bounds__(256) k_sp_nh_start(int j, int upper, int nks, 
     XV[i] = XV[i] - cmul(g, Vp[i]);
     XW[i] = XW[i] - cmul(bc, Wp[i]);
   }
+  if (!dots) return;   // the partials U^H v_hat, U^H w_hat come from the tensor-core kernel
   __syncthreads();
   const int ge = max(g0, min(g1, npw[k]));
   cplx<double>* out = spart2 + ((long)k * nchunk + c) * 2 * nbnd * nbnd;
