@@ -232,9 +232,9 @@ def profiled_traffic():
         return None
 
 
-def _time_chain(b, precision, steps, warmup, stream, profile=False, flavour="ph"):
+def _time_chain(b, precision, steps, warmup, stream, profile=False, flavour="ph", extra=64):
     import torch
-    ch = _chain(b, precision, warmup + steps + 64, stream, flavour)
+    ch = _chain(b, precision, warmup + steps + extra, stream, flavour)
     ch.lanczos(warmup)
     torch.cuda.synchronize()
     if profile:
@@ -249,6 +249,23 @@ def _time_chain(b, precision, steps, warmup, stream, profile=False, flavour="ph"
     return ch, coefs, ms, prof
 
 
+def _golden(b, case: str, n: int):
+    """The oracle's first n coefficients of a workload from the committed golden file
+    (tests/golden/oracle_<case>.txt, written by the oracle), when the bundle is the very input
+    they were computed on (same digest); else None."""
+    import workloads as w
+    from tests.golden import write_workload_golden as gold
+    g = gold.load(case)
+    if g is None or g[1] < n or g[0] != w.bundle_digest(b):
+        return None
+    return g[2][:n], g[3][:n], g[4][:n]
+
+
+def _loss_err(a, ref, b, m):
+    la, lr = _loss(a, b, m), _loss(ref, b, m)
+    return float(np.max(np.abs(la - lr)) / np.max(np.abs(lr)))
+
+
 def _loss(coefs, b, m):
     from paper_2111_06623_gb300 import ll
     w = np.linspace(0.0, 40.0, 4001)
@@ -257,22 +274,22 @@ def _loss(coefs, b, m):
     return -ei.imag
 
 
-def _oracle_sample(b, nk_sample: int, nsteps: int):
-    """Seconds per pseudo-Hermitian oracle step on the first nk_sample k-points."""
-    import copy
-
-    from oracle import lanczos
-    from oracle.liouvillian import System
-    sub = copy.copy(b)
-    for f in ("miller_k", "miller_kq", "u_k", "u_kq", "beta_kq"):
-        setattr(sub, f, getattr(b, f)[:nk_sample])
-    sub.kfrac, sub.kcart, sub.eps_k, sub.eps_kq = b.kfrac[:nk_sample], b.kcart[:nk_sample], b.eps_k[:nk_sample], \
-        b.eps_kq[:nk_sample]
-    sys_ = System(sub)
-    lanczos.pseudo_hermitian(sys_, 1)
+def oracle_timing(spec, warm: int, timed: int, world: int | None = None):
+    """The FP64 oracle on every host core: one pseudo-Hermitian chain of the whole workload
+    (every k-point) through oracle.pool (the k-point split over one single-threaded process per
+    core, gloo sums).  Returns (seconds per step over steps warm+1 .. warm+timed, processes,
+    wall seconds including start-up)."""
+    from oracle import pool
     t0 = time.perf_counter()
-    lanczos.pseudo_hermitian(sys_, nsteps)
-    return (time.perf_counter() - t0) / nsteps
+    _, marks, used = pool.run(spec, warm + timed, "ph", world=world)
+    per = (marks[warm + timed] - marks[warm]) / timed
+    return per, used, time.perf_counter() - t0
+
+
+def oracle_sample_text(spec, warm, timed, used, nks):
+    return (f"steps {warm + 1}-{warm + timed} (after {warm} untimed) of one pseudo-Hermitian chain of the whole "
+            f"workload ({nks} k-points, FP64 NumPy/SciPy oracle), k-point split over {used} single-threaded "
+            f"processes (one per host core); measured, not scaled")
 
 
 def _serving(b_kb, n_jobs: int, seed: int = 7):
@@ -407,24 +424,25 @@ def _batch(n_small: int, n_cubic: int, steps: int = 1500):
             "q_pool": "64 q, |q| ~ U(0.05, 0.6) 2pi/a, Gaussian directions, default_rng(4); first q of the pool per cell"}
 
 
+REF_MAX_STEPS = 40      # timed oracle steps at most in one reference run (a few minutes of CPU)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    b = _bundle()
-    nk = 8
     t0 = time.perf_counter()
-    _oracle_sample(b, nk, max(1, args.warmup))
-    per_step = _oracle_sample(b, nk, args.steps)
-    frac = nk / b.nks
-    value = frac / per_step
-    sample = (f"one pseudo-Hermitian oracle step (NumPy FP64) on {nk} of the {b.nks} k-points per step; "
-              f"value scaled to the full workload")
+    b = _bundle()
+    warm = max(1, min(args.warmup, 10))
+    timed = max(1, min(args.steps, REF_MAX_STEPS))
+    per, used, _ = oracle_timing(b.spec, warm, timed)
+    value = 1.0 / per
+    sample = oracle_sample_text(b.spec, warm, timed, used, b.nks)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
+            "steps": timed, "warmup": warm, "ms_per_step": 1e3 * per, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample_kpoints": nk},
-            "cpu_baseline": {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "config": {"workload": WORKLOAD, "kpoints": int(b.nks), "orbitals": int(b.nks * b.spec.nbnd)},
+            "cpu_baseline": {"value": value, "unit": "steps/s", "cores": used, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": time.perf_counter() - t0}
     print(json.dumps(line), flush=True)
@@ -436,7 +454,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-steps", type=int, default=20, help="timed oracle steps of the CPU baseline (0: none)")
     ap.add_argument("--serving-jobs", type=int, default=32)
     ap.add_argument("--workload", default="kb", choices=["kb", "cubic8", "sc16"],
                     help="cell of the timed chain with --headline-only (profiling); the benchmark line is the KB workload")
@@ -477,8 +495,9 @@ def main():
 
     # FP32 path: the headline, with per-kernel-class device time
     barrier()
+    extra = 64 + SPEC_WINDOW + 64      # room for the spectrum check and the latency samples
     with Clocks(local) as clk:
-        ch32, c32, ms32, _ = _time_chain(b, "fp32", K, W, stream)
+        ch32, c32, ms32, _ = _time_chain(b, "fp32", K, W, stream, extra=extra)
     barrier()
     clocks = clk.summary()
     # the same steps again with per-kernel-class CUDA events (eager launches: a profiled step is
@@ -490,7 +509,7 @@ def main():
         nh = small = None
     else:
         # FP64 path on the same number of steps
-        ch64, c64, ms64, _ = _time_chain(b, "fp64", K, W, stream)
+        ch64, c64, ms64, _ = _time_chain(b, "fp64", K, W, stream, extra=extra)
         # the non-Hermitian recursion (two applications per step), FP32, same steps
         chnh, _, msnh, _ = _time_chain(b, "fp32", K, W, stream, flavour="nh")
         chnh.close()
@@ -499,11 +518,23 @@ def main():
         # steps and the spectrum, on the device
         small = _small_cell(stream)
     sc16 = None if args.headline_only else _sc16(stream)
+    # the spectrum check spans the first SPEC_WINDOW coefficients whatever K is: the chains run
+    # on, untimed, to that many steps
+    kt = len(c32[0])
+    if not args.headline_only:
+        for ch in (ch32, ch64):
+            if ch.steps < SPEC_WINDOW:
+                ch.lanczos(SPEC_WINDOW - ch.steps)
+        c32, c64 = ch32.lanczos(0), ch64.lanczos(0)
     m = min(SPEC_WINDOW, len(c32[0]), len(c64[0]))
-    l32, l64 = _loss(c32, b, m), _loss(c64, b, m)
-    spec_err = float(np.max(np.abs(l32 - l64)) / np.max(np.abs(l64)))
-    lf32, lf64 = _loss(c32, b, len(c32[0])), _loss(c64, b, len(c64[0]))
-    spec_err_full = float(np.max(np.abs(lf32 - lf64)) / np.max(np.abs(lf64)))
+    spec_err = _loss_err(c32, c64, b, m)
+    spec_err_full = _loss_err(tuple(c[:kt] for c in c32), tuple(c[:kt] for c in c64), b, kt)
+    vs_oracle = None
+    ref = None if args.headline_only else _golden(b, "kb_ph", m)
+    if ref is not None:
+        vs_oracle = {"coefficients": m, "source": "tests/golden/oracle_kb_ph.txt (same bundle digest)",
+                     "loss_err_fp32": _loss_err(c32, ref, b, m), "loss_err_fp64": _loss_err(c64, ref, b, m),
+                     "coef_err_fp64": float(np.max(np.abs(c64[0][:m] - ref[0]) / np.abs(ref[0])))}
     # per-step latency (single-step calls, host sync included)
     lat = []
     for _ in range(0 if args.headline_only else 50):
@@ -577,14 +608,10 @@ def main():
              if args.batch_small + args.batch_cubic > 0 and not args.headline_only else None)
 
     cpu = None
-    if rank == 0 and not args.headline_only:
-        nk = 8
-        t1 = _oracle_sample(b, nk, 1)
-        n = max(1, int(args.cpu_seconds / max(t1, 1e-3)))
-        per = _oracle_sample(b, nk, n)
-        cpu = {"value": (nk / b.nks) / per, "unit": "steps/s", "cores": 1, "kind": "oracle",
-               "sample": f"{n} pseudo-Hermitian oracle steps (NumPy FP64, single-threaded FFTs) on {nk} of "
-                         f"{b.nks} k-points, scaled to the full workload"}
+    if rank == 0 and not args.headline_only and args.cpu_steps > 0:
+        per, used, wall = oracle_timing(b.spec, 10, args.cpu_steps)
+        cpu = {"value": 1.0 / per, "unit": "steps/s", "cores": used, "kind": "oracle",
+               "sample": oracle_sample_text(b.spec, 10, args.cpu_steps, used, b.nks), "wall_s": wall}
 
     if rank == 0:
         line = {
@@ -598,7 +625,7 @@ def main():
             "nh_fp32": nh, "small_cell": small, "sc16": sc16,
             "speedup_fp32_vs_fp64": ms64 / ms32,
             "spectrum_err_fp32_vs_fp64": spec_err, "spectrum_window_steps": m,
-            "spectrum_err_fp32_vs_fp64_all_steps": spec_err_full,
+            "spectrum_err_fp32_vs_fp64_timed_steps": spec_err_full, "spectrum_vs_oracle": vs_oracle,
             "step_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))} if lat else None,
             "kernel_ms": ms_cls, "kernel_launches": launches, "ms_per_step_eager_profiled": ms32_prof / K,
             "roofline": roofline, "step_roofline": step_roofline, "serving": serving, "batch": batch, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(total), "clocks": clocks,

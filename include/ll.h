@@ -73,7 +73,15 @@ typedef struct {
   int precision;            /* LL_PREC_*: FP64 everywhere, or FP32 orbitals/FFTs with FP64
                                Lanczos scalars                                             */
   int max_steps;            /* capacity of the device coefficient arrays                   */
+  int where;                /* LL_WHERE_HOST (0) or LL_WHERE_DEVICE (1): where u_k, u_kq,
+                               beta_kq, vloc_r and rho_r live.  Device arrays (e.g. a torch
+                               CUDA tensor's data_ptr()) must be on the current device and
+                               stay untouched until ll_create returns; they are read on the
+                               device (no host copy).  The index arrays (npw, miller), kcart,
+                               eps_k and dij are always host arrays.                         */
 } ll_system_desc;
+
+enum { LL_WHERE_HOST = 0, LL_WHERE_DEVICE = 1 };
 
 /* Builds the device state of one chain (Sec. 2.4-2.5): index maps (sphere(k+Q) -> sphere(k)
  * intersection, column/plane tables), u_{vk}(r) grids, f_xc(n0), the Hartree kernel
@@ -199,6 +207,15 @@ int ll_footprint(const ll_system_desc* desc, size_t* bytes);
 /* Device bytes of the spectrum staging a handle adds for n_omega frequencies (the frequency
  * grid and the chi, eps^-1, eps outputs, plus the extrapolation constants). */
 #define LL_SPECTRUM_BYTES(n_omega) ((size_t)(n_omega) * 56u + 256u)
+
+/* f-sum printout (Sec. 2.1; the check of Sec. 3.3's post-processing): *moment = the trapezoid
+ * integral over the grid of omega (-Im eps^-1(omega)) d omega (Ha^2; omega_ev in eV, eps_inv
+ * complex interleaved, both host arrays of n_omega >= 2 points, increasing omega), computed on
+ * the device in a fixed order; *expected (may be NULL) = (pi/2) omega_p^2 = (pi/2) 4 pi
+ * nelec / omega_cell, which the moment approaches as the grid covers the spectrum (exactly
+ * for a local potential; non-local projectors violate it slightly).  LL_EINVAL on bad sizes. */
+int ll_fsum(const double* omega_ev, const double* eps_inv, int n_omega, double nelec, double omega_cell,
+            double* moment, double* expected, void* stream);
 
 /* Device bytes the handle holds now (every allocation, the spectrum staging included). */
 int ll_bytes(ll_handle* h, size_t* bytes);

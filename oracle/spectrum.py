@@ -52,6 +52,20 @@ def loss(eps_inv: np.ndarray) -> np.ndarray:
     return -np.imag(eps_inv)
 
 
+def fsum_moment(omega_ev: np.ndarray, eps_inv: np.ndarray) -> float:
+    """First frequency moment of the loss function, int omega (-Im eps^-1(omega)) d omega, by
+    the trapezoid rule on the given grid (eV in, Ha^2 out).  The f-sum rule (Sec. 2.1) makes
+    it (pi/2) omega_p^2 over all frequencies for a local potential."""
+    w = np.asarray(omega_ev, dtype=np.float64) / HA_EV
+    f = w * loss(np.asarray(eps_inv))
+    return float(np.sum(0.5 * (f[1:] + f[:-1]) * np.diff(w)))
+
+
+def fsum_expected(nelec: float, omega_cell: float) -> float:
+    """(pi/2) omega_p^2 with omega_p^2 = 4 pi n, n = nelec / Omega (Ha^2)."""
+    return 0.5 * np.pi * 4.0 * np.pi * nelec / omega_cell
+
+
 def default_grid() -> np.ndarray:
     """0-40 eV inclusive, 4001 points (0.01 eV step)."""
     return np.linspace(0.0, 40.0, 4001)

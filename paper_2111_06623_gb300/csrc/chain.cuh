@@ -98,18 +98,25 @@ static inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
 // Every floating-point input of a system finite: a NaN or an infinity would pass into every
 // coefficient of the chain without tripping the breakdown checks.  The array pointers and the
 // sphere sizes npw_k, npw_kq must already be valid.
-static inline bool inputs_finite(const ll_system_desc* d, std::string& err) {
+struct FiniteCheck { const double* p; long len; const char* what; bool device; };
+
+// The floating-point input arrays of a descriptor, with where they live.
+static inline std::vector<FiniteCheck> input_arrays(const ll_system_desc* d) {
   long sk = 0, sq = 0;
   for (int k = 0; k < d->nks; ++k) sk += d->npw_k[k], sq += d->npw_kq[k];
   const long n3 = (long)d->nfft * d->nfft * d->nfft, nb = d->nbnd, np = d->nproj;
-  const struct { const double* p; long len; const char* what; } in[] = {
-      {&d->lattice[0][0], 9, "lattice"},     {d->q_cart, 3, "q_cart"},
-      {d->kcart, 3L * d->nks, "kcart"},      {d->u_k, 2 * nb * sk, "u_k"},
-      {d->u_kq, 2 * nb * sq, "u_kq"},        {d->eps_k, (long)d->nks * nb, "eps_k"},
-      {d->vloc_r, n3, "vloc_r"},             {d->rho_r, n3, "rho_r"},
-      {d->beta_kq, 2 * np * sq, "beta_kq"}, {d->dij, np, "dij"}};
-  for (const auto& a : in)
-    for (long i = 0; i < a.len; ++i)
+  const bool dv = d->where == LL_WHERE_DEVICE;
+  return {{&d->lattice[0][0], 9, "lattice", false},  {d->q_cart, 3, "q_cart", false},
+          {d->kcart, 3L * d->nks, "kcart", false},    {d->u_k, 2 * nb * sk, "u_k", dv},
+          {d->u_kq, 2 * nb * sq, "u_kq", dv},         {d->eps_k, (long)d->nks * nb, "eps_k", false},
+          {d->vloc_r, n3, "vloc_r", dv},              {d->rho_r, n3, "rho_r", dv},
+          {d->beta_kq, 2 * np * sq, "beta_kq", dv},  {d->dij, np, "dij", false}};
+}
+
+static inline bool inputs_finite(const ll_system_desc* d, std::string& err) {
+  for (const auto& a : input_arrays(d))
+    if (!a.device)
+      for (long i = 0; i < a.len; ++i)
       if (!std::isfinite(a.p[i])) {
         err = std::string("non-finite value in ") + a.what + " at index " + std::to_string(i);
         return false;
@@ -257,6 +264,33 @@ class Chain : public ChainBase {
     for (int k = 0; k < nks_; ++k)
       if (d->npw_kq[k] < nbnd_ + 1) { err = "sphere smaller than the occupied manifold"; return LL_EINVAL; }
     if (!inputs_finite(d, err)) return LL_EINVAL;
+    if (d->where != LL_WHERE_HOST && d->where != LL_WHERE_DEVICE) { err = "bad where"; return LL_EINVAL; }
+    const bool dev_in = d->where == LL_WHERE_DEVICE;
+    if (dev_in) {   // device-resident arrays: device pointers, and finite (checked on the device)
+      unsigned long long* first = nullptr;
+      int rc0;
+      if ((rc0 = alloc(&first, 1))) return rc0;
+      for (const auto& a : input_arrays(d)) {
+        if (!a.device || a.len == 0) continue;
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, a.p) != cudaSuccess ||
+            (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
+          cudaGetLastError();
+          err = std::string(a.what) + " is not a device pointer (where = LL_WHERE_DEVICE)";
+          return LL_EINVAL;
+        }
+        unsigned long long h = 0;
+        LL_CK(cudaMemsetAsync(first, 0xFF, sizeof(h), st_));
+        k_first_nonfinite<<<152, 256, 0, st_>>>(a.p, a.len, first);
+        LL_CK(cudaMemcpyAsync(&h, first, sizeof(h), cudaMemcpyDeviceToHost, st_));
+        LL_CK(cudaStreamSynchronize(st_));
+        if (h != ~0ull) {
+          err = std::string("non-finite value in ") + a.what + " at index " + std::to_string(h);
+          return LL_EINVAL;
+        }
+      }
+      release(first);
+    }
     double b[3][3];
     recip(d->lattice, b);
     omega_ = fabs(d->lattice[0][0] * (d->lattice[1][1] * d->lattice[2][2] - d->lattice[1][2] * d->lattice[2][1]) -
@@ -291,20 +325,26 @@ class Chain : public ChainBase {
         kin[(size_t)k * pq + i] = (T)(0.5 * (g[0] * g[0] + g[1] * g[1] + g[2] * g[2]));
       }
     }
-    // padded orbital tables
-    std::vector<cplx<T>> uk = pad_batch(d->u_k, hk_, nbnd_);
-    std::vector<cplx<T>> ukq = pad_batch(d->u_kq, hq_, nbnd_);
-    std::vector<cplx<T>> bkq = nproj_ ? pad_batch(d->beta_kq, hq_, nproj_) : std::vector<cplx<T>>(1);
-    // grids transposed to [j3][j2][j1]
-    std::vector<T> vl(n3);
-    std::vector<double> rh(n3);
-    for (int j1 = 0; j1 < n; ++j1)
-      for (int j2 = 0; j2 < n; ++j2)
-        for (int j3 = 0; j3 < n; ++j3) {
-          const long src = ((long)j1 * n + j2) * n + j3, dst = ((long)j3 * n + j2) * n + j1;
-          vl[dst] = (T)d->vloc_r[src];
-          rh[dst] = d->rho_r[src];
-        }
+    // padded orbital tables and grids transposed to [j3][j2][j1]: on the host for host inputs;
+    // from device inputs by the k_pad_rows / k_grids_in kernels below
+    std::vector<cplx<T>> uk, ukq, bkq(1);
+    std::vector<T> vl;
+    std::vector<double> rh;
+    if (!dev_in) {
+      uk = pad_batch(d->u_k, hk_, nbnd_);
+      ukq = pad_batch(d->u_kq, hq_, nbnd_);
+      if (nproj_) bkq = pad_batch(d->beta_kq, hq_, nproj_);
+      vl.resize(n3);
+      rh.resize(n3);
+      for (int j1 = 0; j1 < n; ++j1)
+        for (int j2 = 0; j2 < n; ++j2)
+          for (int j3 = 0; j3 < n; ++j3) {
+            const long src = ((long)j1 * n + j2) * n + j3, dst = ((long)j3 * n + j2) * n + j1;
+            vl[dst] = (T)d->vloc_r[src];
+            rh[dst] = d->rho_r[src];
+          }
+    }
+    const long bkq_len = nproj_ ? (long)nks_ * nproj_ * pq : 1;
 
     int rc;
     if ((rc = tw_tables_upload(st_)) != cudaSuccess) { err = "twiddle upload failed"; return LL_ECUDA; }
@@ -356,7 +396,7 @@ class Chain : public ChainBase {
     const long nzp = (long)nks_ * npk_;               // partials per vector and step
     const long nzv = nzp * nvec_;
     if ((rc = alloc(&whart_, n3)) || (rc = alloc(&kin_, (long)nks_ * pq)) || (rc = alloc(&uk_, (long)nks_ * nbnd_ * pk)) ||
-        (rc = alloc(&ukq_, vq)) || (rc = alloc(&bkq_, (long)bkq.size())) || (rc = alloc(&eps_, (long)nks_ * nbnd_)) ||
+        (rc = alloc(&ukq_, vq)) || (rc = alloc(&bkq_, bkq_len)) || (rc = alloc(&eps_, (long)nks_ * nbnd_)) ||
         (rc = alloc(&dij_, std::max(1, nproj_))) || (rc = alloc(&vloc_, n3)) || (rc = alloc(&rho_, n3)) ||
         (rc = alloc(&fxc_, n3)) || (rc = alloc(&ur_, (long)nks_ * nbnd_ * n3)) ||
         (rc = alloc(&cbuf_, (long)norb * n * cb_ncol_)) || (rc = alloc(&nprt_, (long)ngroups_ * n3)) ||
@@ -378,13 +418,28 @@ class Chain : public ChainBase {
     (void)err;
     LL_CK(cudaMemcpyAsync(whart_, wh.data(), n3 * sizeof(T), cudaMemcpyHostToDevice, st_));
     LL_CK(cudaMemcpyAsync(kin_, kin.data(), kin.size() * sizeof(T), cudaMemcpyHostToDevice, st_));
-    LL_CK(cudaMemcpyAsync(uk_, uk.data(), uk.size() * sizeof(cplx<T>), cudaMemcpyHostToDevice, st_));
-    LL_CK(cudaMemcpyAsync(ukq_, ukq.data(), ukq.size() * sizeof(cplx<T>), cudaMemcpyHostToDevice, st_));
-    LL_CK(cudaMemcpyAsync(bkq_, bkq.data(), bkq.size() * sizeof(cplx<T>), cudaMemcpyHostToDevice, st_));
+    if (!dev_in) {
+      LL_CK(cudaMemcpyAsync(uk_, uk.data(), uk.size() * sizeof(cplx<T>), cudaMemcpyHostToDevice, st_));
+      LL_CK(cudaMemcpyAsync(ukq_, ukq.data(), ukq.size() * sizeof(cplx<T>), cudaMemcpyHostToDevice, st_));
+      LL_CK(cudaMemcpyAsync(bkq_, bkq.data(), bkq.size() * sizeof(cplx<T>), cudaMemcpyHostToDevice, st_));
+      LL_CK(cudaMemcpyAsync(vloc_, vl.data(), n3 * sizeof(T), cudaMemcpyHostToDevice, st_));
+      LL_CK(cudaMemcpyAsync(rho_, rh.data(), n3 * sizeof(double), cudaMemcpyHostToDevice, st_));
+    } else {
+      int *offk = nullptr, *offq = nullptr;
+      if ((rc = alloc(&offk, nks_ + 1)) || (rc = alloc(&offq, nks_ + 1))) return rc;
+      LL_CK(cudaMemcpyAsync(offk, hk_.off.data(), (nks_ + 1) * sizeof(int), cudaMemcpyHostToDevice, st_));
+      LL_CK(cudaMemcpyAsync(offq, hq_.off.data(), (nks_ + 1) * sizeof(int), cudaMemcpyHostToDevice, st_));
+      k_pad_rows<T><<<dim3(nks_, nbnd_), 256, 0, st_>>>(d->u_k, offk, dk_.npw, nbnd_, hk_.npw_pad, uk_);
+      k_pad_rows<T><<<dim3(nks_, nbnd_), 256, 0, st_>>>(d->u_kq, offq, dq_.npw, nbnd_, pq, ukq_);
+      if (nproj_) k_pad_rows<T><<<dim3(nks_, nproj_), 256, 0, st_>>>(d->beta_kq, offq, dq_.npw, nproj_, pq, bkq_);
+      k_grids_in<T><<<256, 256, 0, st_>>>(n, d->vloc_r, d->rho_r, vloc_, rho_);
+      LL_CK(cudaGetLastError());
+      LL_CK(cudaStreamSynchronize(st_));   // the caller may reuse its arrays once ll_create returns
+      release(offk);
+      release(offq);
+    }
     LL_CK(cudaMemcpyAsync(eps_, d->eps_k, sizeof(double) * nks_ * nbnd_, cudaMemcpyHostToDevice, st_));
     if (nproj_) LL_CK(cudaMemcpyAsync(dij_, d->dij, sizeof(double) * nproj_, cudaMemcpyHostToDevice, st_));
-    LL_CK(cudaMemcpyAsync(vloc_, vl.data(), n3 * sizeof(T), cudaMemcpyHostToDevice, st_));
-    LL_CK(cudaMemcpyAsync(rho_, rh.data(), n3 * sizeof(double), cudaMemcpyHostToDevice, st_));
     LL_CK(cudaMemsetAsync(err_, 0, 2 * sizeof(int), st_));
     LL_CK(cudaMemsetAsync(vecs_, 0, 3L * nvec_ * vq * sizeof(cplx<T>), st_));
     LL_CK(cudaMemsetAsync(zpart_, 0, (long)(cap_ + 1) * nzp * sizeof(cplx<double>), st_));

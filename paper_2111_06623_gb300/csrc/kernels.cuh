@@ -830,6 +830,39 @@ __device__ __forceinline__ double pz81_fxc(double n) {
   return fx + dvc * (-rs / (3.0 * n));
 }
 
+// ---- set-up from device-resident inputs (ll_system_desc.where = LL_WHERE_DEVICE) --------
+
+// The smallest index of a NaN or infinity among n values into *first, which the caller sets
+// to all ones beforehand (left so when every value is finite).
+static __global__ void k_first_nonfinite(const double* __restrict__ p, long n, unsigned long long* first) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    if (!isfinite(p[i])) atomicMin(first, (unsigned long long)i);
+}
+
+// Packed complex rows [k][row][npw[k]] (k blocks at nrow * off[k]) -> padded [k][row][npw_pad]
+// in T, zero on the padding.  grid (nks, nrow), block 256.
+template <typename T>
+__global__ void k_pad_rows(const double* __restrict__ src, const int* __restrict__ off, const int* __restrict__ npw,
+                           int nrow, int npw_pad, cplx<T>* __restrict__ dst) {
+  const int k = blockIdx.x, r = blockIdx.y, n = npw[k];
+  const double* s = src + 2 * ((long)nrow * off[k] + (long)r * n);
+  cplx<T>* d = dst + ((long)k * nrow + r) * npw_pad;
+  for (int g = threadIdx.x; g < npw_pad; g += blockDim.x) d[g] = g < n ? mk((T)s[2 * g], (T)s[2 * g + 1]) : czero<T>();
+}
+
+// Grids [j1][j2][j3] -> [j3][j2][j1]: V in T, the density in double.
+template <typename T>
+__global__ void k_grids_in(int n, const double* __restrict__ vloc, const double* __restrict__ rho, T* __restrict__ vl,
+                           double* __restrict__ rh) {
+  const long n3 = (long)n * n * n;
+  for (long dst = (long)blockIdx.x * blockDim.x + threadIdx.x; dst < n3; dst += (long)gridDim.x * blockDim.x) {
+    const long j1 = dst % n, j2 = (dst / n) % n, j3 = dst / ((long)n * n);
+    const long src = (j1 * n + j2) * n + j3;
+    vl[dst] = (T)vloc[src];
+    rh[dst] = rho[src];
+  }
+}
+
 template <typename T>
 __global__ void k_fxc(long n3, const double* __restrict__ rho, T* __restrict__ fxc, int on) {
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n3; i += (long)gridDim.x * blockDim.x)

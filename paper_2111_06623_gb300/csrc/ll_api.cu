@@ -351,6 +351,55 @@ int ll_spectrum_static(const double* beta, const double* gamma, const double* z,
   return LL_OK;
 }
 
+// f-sum printout (Sec. 2.1): the trapezoid first moment of the loss function over the grid,
+// one block, every thread a strided partial, the partials summed in a fixed order.
+namespace {
+__global__ void k_fsum(int n, const double* __restrict__ w_ev, const ll::cplx<double>* __restrict__ ei,
+                       double* __restrict__ out) {
+  __shared__ double part[256];
+  const double ha = 27.211386245988;
+  double s = 0.0;
+  for (int i = threadIdx.x; i + 1 < n; i += blockDim.x) {
+    const double w0 = w_ev[i] / ha, w1 = w_ev[i + 1] / ha;
+    s += 0.5 * (w0 * -ei[i].y + w1 * -ei[i + 1].y) * (w1 - w0);
+  }
+  part[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)blockDim.x; ++i) t += part[i];
+    out[0] = t;
+  }
+}
+}  // namespace
+
+int ll_fsum(const double* omega_ev, const double* eps_inv, int n_omega, double nelec, double omega_cell,
+            double* moment, double* expected, void* stream) {
+  if (!omega_ev || !eps_inv || n_omega < 2 || !(omega_cell > 0) || !(nelec >= 0) || !moment)
+    return fail(LL_EINVAL, "bad f-sum arguments");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  double *dw = nullptr, *de = nullptr, *dout = nullptr;
+  cudaError_t e = cudaMallocAsync(&dw, n_omega * sizeof(double), st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&de, 2 * (size_t)n_omega * sizeof(double), st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&dout, sizeof(double), st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dw, omega_ev, n_omega * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(de, eps_inv, 2 * (size_t)n_omega * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    k_fsum<<<1, 256, 0, st>>>(n_omega, dw, reinterpret_cast<const ll::cplx<double>*>(de), dout);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(moment, dout, sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (dw) cudaFreeAsync(dw, st);
+  if (de) cudaFreeAsync(de, st);
+  if (dout) cudaFreeAsync(dout, st);
+  cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(LL_ECUDA, std::string("ll_fsum: ") + cudaGetErrorString(e));
+  if (expected) *expected = 0.5 * 3.14159265358979323846 * 4.0 * 3.14159265358979323846 * nelec / omega_cell;
+  return LL_OK;
+}
+
 int ll_apply(ll_handle* h, int upper, const double* x, double* out) {
   if (!h || !x || !out) return fail(LL_EINVAL, "bad apply arguments");
   std::string err;

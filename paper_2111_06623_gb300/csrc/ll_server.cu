@@ -78,6 +78,21 @@ void copy_in(std::vector<V>& dst, const V* src, size_t n) {
   dst.assign(src, src + n);
 }
 
+// n doubles from host or device memory into dst; false when a device copy fails.
+bool copy_any(std::vector<double>& dst, const double* src, size_t n, bool device) {
+  if (!device) {
+    copy_in(dst, src, n);
+    return true;
+  }
+  dst.resize(n);
+  if (n == 0) return true;
+  if (cudaMemcpy(dst.data(), src, n * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return true;
+}
+
 // The job's copies of the ground state are not needed once it has ended.
 void drop_inputs(Job* j) {
   for (auto* v : {&j->u_k, &j->u_kq, &j->beta_kq, &j->vloc, &j->rho}) std::vector<double>().swap(*v);
@@ -265,12 +280,9 @@ int ll_submit(ll_server* s, const ll_job_desc* jd, uint64_t* job_id) {
       !d->miller_k || !d->miller_kq || !d->u_k || !d->u_kq || !d->eps_k || !d->vloc_r || !d->rho_r ||
       (d->nproj > 0 && (!d->beta_kq || !d->dij)) || (jd->n_omega > 0 && !jd->omega_ev))
     return sfail(LL_EINVAL, "malformed job");
-  {
-    std::string err;
-    for (int k = 0; k < d->nks; ++k)
-      if (d->npw_k[k] < 1 || d->npw_kq[k] < 1) return sfail(LL_EINVAL, "malformed job: empty plane-wave sphere");
-    if (!ll::inputs_finite(d, err)) return sfail(LL_EINVAL, "malformed job: " + err);
-  }
+  if (d->where != LL_WHERE_HOST && d->where != LL_WHERE_DEVICE) return sfail(LL_EINVAL, "malformed job: bad where");
+  for (int k = 0; k < d->nks; ++k)
+    if (d->npw_k[k] < 1 || d->npw_kq[k] < 1) return sfail(LL_EINVAL, "malformed job: empty plane-wave sphere");
   size_t fp = 0;
   if (ll_footprint(d, &fp) != LL_OK) return sfail(LL_EINVAL, "footprint");
   if (jd->n_omega > 0) fp += LL_SPECTRUM_BYTES(jd->n_omega);
@@ -287,14 +299,19 @@ int ll_submit(ll_server* s, const ll_job_desc* jd, uint64_t* job_id) {
   copy_in(j->npw_kq, d->npw_kq, d->nks);
   copy_in(j->miller_k, d->miller_k, 3 * sk);
   copy_in(j->miller_kq, d->miller_kq, 3 * sq);
-  copy_in(j->u_k, d->u_k, 2 * sk * d->nbnd);
-  copy_in(j->u_kq, d->u_kq, 2 * sq * d->nbnd);
+  // the job keeps host copies of its ground state (device-resident inputs are copied down
+  // now: the caller may free them once ll_submit returns)
+  const bool dev = d->where == LL_WHERE_DEVICE;
+  bool ok = copy_any(j->u_k, d->u_k, 2 * sk * d->nbnd, dev) && copy_any(j->u_kq, d->u_kq, 2 * sq * d->nbnd, dev) &&
+            copy_any(j->vloc, d->vloc_r, n3, dev) && copy_any(j->rho, d->rho_r, n3, dev);
   copy_in(j->eps_k, d->eps_k, (size_t)d->nks * d->nbnd);
-  copy_in(j->vloc, d->vloc_r, n3);
-  copy_in(j->rho, d->rho_r, n3);
   if (d->nproj > 0) {
-    copy_in(j->beta_kq, d->beta_kq, 2 * sq * d->nproj);
+    ok = ok && copy_any(j->beta_kq, d->beta_kq, 2 * sq * d->nproj, dev);
     copy_in(j->dij, d->dij, d->nproj);
+  }
+  if (!ok) {
+    delete j;
+    return sfail(LL_EINVAL, "malformed job: device input arrays could not be read");
   }
   if (jd->n_omega > 0) copy_in(j->omega, jd->omega_ev, jd->n_omega);
   j->desc = *d;
@@ -310,6 +327,14 @@ int ll_submit(ll_server* s, const ll_job_desc* jd, uint64_t* job_id) {
   j->desc.rho_r = j->rho.data();
   j->desc.beta_kq = d->nproj > 0 ? j->beta_kq.data() : nullptr;
   j->desc.dij = d->nproj > 0 ? j->dij.data() : nullptr;
+  j->desc.where = LL_WHERE_HOST;
+  {
+    std::string err;
+    if (!ll::inputs_finite(&j->desc, err)) {
+      delete j;
+      return sfail(LL_EINVAL, "malformed job: " + err);
+    }
+  }
   j->n_steps = jd->n_steps;
   j->eta = jd->eta_ev;
   j->footprint = fp;

@@ -38,8 +38,24 @@ class SystemDesc(C.Structure):
         ("nproj", C.c_int), ("q_cart", C.c_double * 3), ("kcart", _dp), ("npw_k", _ip), ("miller_k", _ip),
         ("npw_kq", _ip), ("miller_kq", _ip), ("u_k", _dp), ("u_kq", _dp), ("eps_k", _dp), ("vloc_r", _dp),
         ("rho_r", _dp), ("beta_kq", _dp), ("dij", _dp), ("approx", C.c_int), ("flavour", C.c_int),
-        ("precision", C.c_int), ("max_steps", C.c_int),
+        ("precision", C.c_int), ("max_steps", C.c_int), ("where", C.c_int),
     ]
+
+
+LL_WHERE_HOST, LL_WHERE_DEVICE = 0, 1
+
+
+def _on_device(a) -> bool:
+    """True for a CUDA tensor (torch), whose data_ptr() is a device address."""
+    return bool(getattr(a, "is_cuda", False))
+
+
+def _dev_ptr(t, what: str):
+    """The device address of a contiguous float64 / complex128 CUDA tensor (packed layout)."""
+    import torch
+    if t.dtype not in (torch.float64, torch.complex128) or not t.is_contiguous():
+        raise ValueError(f"{what}: a contiguous float64 or complex128 CUDA tensor is required")
+    return C.cast(C.c_void_p(t.data_ptr()), _dp)
 
 
 def _load():
@@ -63,6 +79,7 @@ def _load():
         "ll_get_start": (C.c_int, [vp, _dp]),
         "ll_footprint": (C.c_int, [C.POINTER(SystemDesc), C.POINTER(C.c_size_t)]),
         "ll_bytes": (C.c_int, [vp, C.POINTER(C.c_size_t)]),
+        "ll_fsum": (C.c_int, [_dp, _dp, C.c_int, C.c_double, C.c_double, _dp, _dp, vp]),
         "ll_profile": (C.c_int, [vp, C.c_int]),
         "ll_profile_read": (C.c_int, [vp, _dp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
         "ll_server_create": (C.c_int, [C.c_size_t, C.c_int, C.POINTER(vp)]),
@@ -88,7 +105,7 @@ def _load():
 _lib = _load()
 EXPORTS = ("ll_create", "ll_destroy", "ll_lanczos", "ll_lanczos_spectrum", "ll_spectrum", "ll_spectrum_static",
            "ll_lanczos_spectrum_x", "ll_spectrum_x",
-           "ll_apply", "ll_get_map", "ll_get_start", "ll_footprint", "ll_bytes", "ll_profile", "ll_profile_read", "ll_last_error",
+           "ll_apply", "ll_get_map", "ll_get_start", "ll_footprint", "ll_bytes", "ll_fsum", "ll_profile", "ll_profile_read", "ll_last_error",
            "ll_version", "ll_fma_peak", "ll_server_create",
            "ll_server_set_chunk", "ll_submit", "ll_poll", "ll_cancel", "ll_release", "ll_server_stats", "ll_server_last_error",
            "ll_server_destroy")
@@ -125,10 +142,29 @@ def _cat_complex(blocks) -> np.ndarray:
 
 def _make_desc(*, lattice, nfft, kcart, miller_k, miller_kq, u_k, u_kq, eps_k, vloc_r, rho_r, beta_kq=None,
                dij=None, q_cart, approx="tddft", flavour="ph", precision="fp64", max_steps=1000):
-    """An ll_system_desc and the arrays it points into (keep them alive while it is used)."""
+    """An ll_system_desc and the arrays it points into (keep them alive while it is used).
+
+    u_k, u_kq, beta_kq, vloc_r and rho_r are host arrays (u_k, u_kq, beta_kq as lists of
+    per-k (rows, npw) arrays), or all of them CUDA tensors (torch) already in the packed layout
+    of ll_system_desc: the descriptor then points at device memory (where = LL_WHERE_DEVICE)."""
     nks = len(miller_k)
-    nbnd = int(u_k[0].shape[0])
-    nproj = int(beta_kq[0].shape[0]) if beta_kq is not None and len(beta_kq) and beta_kq[0].shape[0] else 0
+    dev = _on_device(u_k)
+    if dev:
+        nbnd = int(np.shape(eps_k)[1])
+        nproj = int(len(dij)) if dij is not None and beta_kq is not None else 0
+    else:
+        nbnd = int(u_k[0].shape[0])
+        nproj = int(beta_kq[0].shape[0]) if beta_kq is not None and len(beta_kq) and beta_kq[0].shape[0] else 0
+    if dev:
+        arrs = {"u_k": u_k, "u_kq": u_kq, "vloc_r": vloc_r, "rho_r": rho_r}
+        if nproj:
+            arrs["beta_kq"] = beta_kq
+        for name, t in arrs.items():
+            if not _on_device(t):
+                raise ValueError(f"{name}: with u_k on the device every large array must be a CUDA tensor")
+        return _make_desc_device(lattice=lattice, nfft=nfft, kcart=kcart, miller_k=miller_k, miller_kq=miller_kq,
+                                 arrs=arrs, eps_k=eps_k, dij=dij, nbnd=nbnd, nproj=nproj, q_cart=q_cart,
+                                 approx=approx, flavour=flavour, precision=precision, max_steps=max_steps)
     k = dict(
         kcart=np.ascontiguousarray(kcart, dtype=np.float64),
         npw_k=np.array([len(m) for m in miller_k], dtype=np.int32),
@@ -156,6 +192,37 @@ def _make_desc(*, lattice, nfft, kcart, miller_k, miller_kq, u_k, u_kq, eps_k, v
     d.dij = _d(k["dij"])
     d.approx, d.flavour, d.precision = APPROX[approx], FLAVOUR[flavour], PRECISION[precision]
     d.max_steps = int(max_steps)
+    d.where = LL_WHERE_HOST
+    return d, k
+
+
+def _make_desc_device(*, lattice, nfft, kcart, miller_k, miller_kq, arrs, eps_k, dij, nbnd, nproj, q_cart, approx,
+                      flavour, precision, max_steps):
+    k = dict(
+        kcart=np.ascontiguousarray(kcart, dtype=np.float64),
+        npw_k=np.array([len(m) for m in miller_k], dtype=np.int32),
+        miller_k=np.ascontiguousarray(np.concatenate(miller_k), dtype=np.int32),
+        npw_kq=np.array([len(m) for m in miller_kq], dtype=np.int32),
+        miller_kq=np.ascontiguousarray(np.concatenate(miller_kq), dtype=np.int32),
+        eps_k=np.ascontiguousarray(eps_k, dtype=np.float64),
+        dij=np.ascontiguousarray(dij if nproj else np.zeros(1), dtype=np.float64),
+        device=arrs,
+    )
+    d = SystemDesc()
+    for i in range(3):
+        for j in range(3):
+            d.lattice[i][j] = float(lattice[i][j])
+        d.q_cart[i] = float(q_cart[i])
+    d.nfft, d.nks, d.nbnd, d.nproj = int(nfft), len(miller_k), nbnd, nproj
+    d.kcart, d.npw_k, d.miller_k = _d(k["kcart"]), _i(k["npw_k"]), _i(k["miller_k"])
+    d.npw_kq, d.miller_kq = _i(k["npw_kq"]), _i(k["miller_kq"])
+    d.u_k, d.u_kq = _dev_ptr(arrs["u_k"], "u_k"), _dev_ptr(arrs["u_kq"], "u_kq")
+    d.vloc_r, d.rho_r = _dev_ptr(arrs["vloc_r"], "vloc_r"), _dev_ptr(arrs["rho_r"], "rho_r")
+    d.beta_kq = _dev_ptr(arrs["beta_kq"], "beta_kq") if nproj else None
+    d.eps_k, d.dij = _d(k["eps_k"]), _d(k["dij"])
+    d.approx, d.flavour, d.precision = APPROX[approx], FLAVOUR[flavour], PRECISION[precision]
+    d.max_steps = int(max_steps)
+    d.where = LL_WHERE_DEVICE
     return d, k
 
 
@@ -266,6 +333,18 @@ class Chain:
         b = C.c_size_t(0)
         _check(_lib.ll_bytes(self._h, C.byref(b)))
         return int(b.value)
+
+
+def fsum(omega_ev, eps_inv, nelec: float, omega_cell: float, stream=None):
+    """ll_fsum: (trapezoid first moment of -Im eps^-1 over the grid, (pi/2) omega_p^2), Ha^2."""
+    w = np.ascontiguousarray(omega_ev, dtype=np.float64)
+    e = np.ascontiguousarray(eps_inv, dtype=np.complex128)
+    if e.shape != w.shape:
+        raise ValueError("omega_ev and eps_inv differ in length")
+    m, x = C.c_double(0.0), C.c_double(0.0)
+    _check(_lib.ll_fsum(_d(w), _d(e.view(np.float64)), len(w), float(nelec), float(omega_cell), C.byref(m),
+                        C.byref(x), C.c_void_p(stream) if stream else None))
+    return m.value, x.value
 
 
 def spectrum_bytes(n_omega: int) -> int:

@@ -149,3 +149,6 @@ def test_fsum_integral_of_loss_function(approx, flavour):
     moment = float(np.sum(0.5 * (f[1:] + f[:-1]) * np.diff(wha)))
     wp2 = 4 * np.pi * spec.nelec / spec.omega
     assert abs(moment / (0.5 * np.pi * wp2) - 1.0) < 5e-3
+    # the oracle's f-sum printout is this trapezoid and this closed form
+    assert spectrum.fsum_moment(wev, eps_inv) == pytest.approx(moment, rel=1e-14)
+    assert spectrum.fsum_expected(spec.nelec, spec.omega) == pytest.approx(0.5 * np.pi * wp2, rel=1e-15)
