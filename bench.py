@@ -294,13 +294,17 @@ def oracle_sample_text(spec, warm, timed, used, nks):
 
 def _serving(b_kb, n_jobs: int, seed: int = 7):
     """A Poisson stream (mean 20 jobs/s, arrivals from default_rng(seed)) of Lanczos jobs
-    through the request loop under a 150 GB HBM budget: each job picks a cell uniformly (the
-    two-atom cell at one of four q of the many-Q pool, the KB workload, the eight-atom cell at
-    one of two q of the pool) and U[500, 3000] pseudo-Hermitian FP32 steps.  Returns
-    throughput and the p50/p99 time from submission to the finished spectrum."""
+    through the request loop under a 150 GB HBM budget: each job picks a configuration
+    uniformly -- the small two-atom cell at one of four q of the many-Q pool, the KB workload,
+    the sixteen-atom cell (the eight-atom cell at one of two q of the pool where the
+    sixteen-atom ground state is not cached) -- and U[500, 3000] pseudo-Hermitian FP32 steps.
+    Returns throughput and the p50/p99 time from submission to the finished spectrum."""
+    import workloads as w
     from paper_2111_06623_gb300 import ll
     pools = _batch_bundles(4, 2)
-    cells = [pools["fcc2_10ry_18"], [b_kb], pools["cubic8_20ry_32"]]
+    b16 = w.cached_bundle(w.config_sc16())
+    third = [b16] if b16 is not None else pools["cubic8_20ry_32"]
+    cells = [pools["fcc2_10ry_18"], [b_kb], third]
     rng = np.random.default_rng(seed)
     wgrid = np.linspace(0.0, 40.0, 4001)
     srv = ll.Server(hbm_budget_bytes=150 << 30, max_slots=16, chunk=32)
@@ -331,11 +335,16 @@ def _serving(b_kb, n_jobs: int, seed: int = 7):
     peak = srv.stats()["peak"]
     srv.close()
     v = np.array(list(lat.values()))
+    per_cfg = {}
+    for pk, ns in zip(picks, steps):
+        c = per_cfg.setdefault(["fcc2_10ry_18", "fcc2kb_25ry_32", third[0].spec.name][pk], {"jobs": 0, "steps": 0})
+        c["jobs"] += 1
+        c["steps"] += int(ns)
     return {"jobs": n_jobs, "steps_per_s": done / wall, "p50_s": float(np.percentile(v, 50)),
             "p99_s": float(np.percentile(v, 99)), "wall_s": wall, "peak_hbm_gb": peak / 2 ** 30,
-            "budget_gb": 150, "slots": 16,
-            "stream": ("Poisson 20 jobs/s (seed 7); cell U{2-atom at 4 q, KB workload, 8-atom at 2 q}; "
-                       "U[500, 3000] FP32 PH steps")}
+            "budget_gb": 150, "slots": 16, "per_config": per_cfg,
+            "stream": (f"Poisson 20 jobs/s (seed 7), first {n_jobs} jobs of the stream; configuration "
+                       f"U{{2-atom 10 Ry at 4 q, KB workload, {third[0].spec.name}}}; U[500, 3000] FP32 PH steps")}
 
 
 def q_pool(n: int = 64) -> np.ndarray:
@@ -373,13 +382,18 @@ def _with_q(spec, q):
     return spec
 
 
-def _batch(n_small: int, n_cubic: int, steps: int = 1500):
+def _batch(n_small: int, n_cubic: int, steps: int = 1500, n_sc16: int = 1):
     """Many independent chains on one GPU at once: n_small momentum transfers of the pool on
-    the two-atom cell and n_cubic on the eight-atom cell, all submitted together to the request
-    loop (one stream per chain), steps FP32 pseudo-Hermitian steps each.  Returns the whole
-    batch's steps/s and the wall time to the last spectrum."""
+    the two-atom cell, n_cubic on the eight-atom cell and (where its ground state is cached)
+    the sixteen-atom cell at its configured q, all submitted together to the request loop (one
+    stream per chain), steps FP32 pseudo-Hermitian steps each.  Returns the whole batch's
+    steps/s and the wall time to the last spectrum."""
+    import workloads as w
     from paper_2111_06623_gb300 import ll
     pools = _batch_bundles(n_small, n_cubic)
+    if n_sc16 > 0:
+        b16 = w.cached_bundle(w.config_sc16())
+        pools["sc16kb_30ry_48"] = [b16] if b16 is not None else []
     jobs = [(cell, b) for cell, bs in pools.items() for b in bs]
     wgrid = np.linspace(0.0, 40.0, 4001)
     srv = ll.Server(hbm_budget_bytes=150 << 30, max_slots=len(jobs), chunk=32)
@@ -455,13 +469,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=20, help="timed oracle steps of the CPU baseline (0: none)")
-    ap.add_argument("--serving-jobs", type=int, default=32)
+    ap.add_argument("--serving-jobs", type=int, default=16, help="jobs of the Poisson stream (400 in the paper-derived stream)")
     ap.add_argument("--workload", default="kb", choices=["kb", "cubic8", "sc16"],
                     help="cell of the timed chain with --headline-only (profiling); the benchmark line is the KB workload")
     ap.add_argument("--headline-only", action="store_true",
                     help="time the FP32 chain on the KB workload only (no other legs): for profiling")
     ap.add_argument("--batch-small", type=int, default=16, help="chains of the two-atom cell in the many-Q batch")
     ap.add_argument("--batch-cubic", type=int, default=2, help="chains of the eight-atom cell in the many-Q batch")
+    ap.add_argument("--batch-sc16", type=int, default=1, help="chains of the sixteen-atom cell in the batch (0 or 1)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")
@@ -604,7 +619,7 @@ def main():
                      "measured_fma_tflops": {"fp32": fma32, "fp64": fma64},
                      "frac_nominal_of_measured_fma": nom * value / world / 1e12 / fma32 if fma32 else None}
     serving = _serving(b, args.serving_jobs) if args.serving_jobs > 0 and not args.headline_only else None
-    batch = (_batch(args.batch_small, args.batch_cubic)
+    batch = (_batch(args.batch_small, args.batch_cubic, n_sc16=args.batch_sc16)
              if args.batch_small + args.batch_cubic > 0 and not args.headline_only else None)
 
     cpu = None

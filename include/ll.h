@@ -97,6 +97,19 @@ enum { LL_WHERE_HOST = 0, LL_WHERE_DEVICE = 1 };
 int ll_create(const ll_system_desc* desc, void* stream, ll_handle** out);
 int ll_destroy(ll_handle* h);
 
+/* ll_create for another momentum transfer Q on the ground state of an existing chain `share`
+ * (Sec. 2.1: Q = q + G may lie beyond the first Brillouin zone; Sec. 5 runs one recursion per
+ * Q on one ground state).  The u_{vk}(r) grids, which depend on the ground state only (N^3 nks
+ * nbnd complex values: 537 MB in FP32 on the 25 Ry, 8x8x8-k cell), are taken from `share`
+ * instead of being built and stored again; everything that depends on Q (sphere(k+Q), u_kq,
+ * beta_kq, the kinetic and Hartree tables, the vectors) is the new chain's own.  `desc` must
+ * hold host arrays and the same ground state as `share`'s: precision, grid, k-points, bands,
+ * sphere(k) and u_k (compared through a hash of those inputs; LL_EINVAL otherwise).  The
+ * coefficients are those ll_create would give, bit for bit.  The grids stay allocated until the
+ * last chain using them is destroyed; ll_bytes counts them in the chain that built them.
+ * Waits for `share`'s stream once (its grids must be complete). */
+int ll_create_sharing(const ll_system_desc* desc, ll_handle* share, void* stream, ll_handle** out);
+
 /* Runs n_steps more Lanczos steps (Sec. 2.5), continuing from the resident state
  * (restart semantics of Sec. 3.2).  On return the arrays hold every coefficient so far
  * (`*steps_done` of them; capacity max_steps):

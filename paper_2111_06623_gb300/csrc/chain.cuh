@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -22,6 +23,9 @@ namespace ll {
 struct ChainBase {
   virtual ~ChainBase() {}
   virtual int create(const ll_system_desc* d, cudaStream_t st, std::string& err) = 0;
+  // create() reusing the u_{vk}(r) grids of `donor`, a chain of the same ground state (same
+  // precision, grid, k-points, bands, sphere(k) and u_k: checked by a hash of those inputs)
+  virtual int create_shared(const ll_system_desc* d, cudaStream_t st, ChainBase* donor, std::string& err) = 0;
   virtual int lanczos(int n, double* beta, double* gamma, double* z, int* done, std::string& err) = 0;
   // asynchronous halves of lanczos(): queue n steps on the chain's stream / wait for them and
   // fetch every coefficient so far
@@ -229,6 +233,26 @@ template <int N, int MODE> struct BO {
   static constexpr int v = (MODE == XY_PASS1_DENS || MODE == XY_PASS2) ? 256 / N : 384 / N;
 };
 
+// FNV-1a (64 bit) over the inputs that determine the u_{vk}(r) grids: the precision, the grid
+// side, the k-point and band counts, the spheres of k and the u_k coefficients (host arrays).
+static inline uint64_t ground_state_hash(const ll_system_desc* d) {
+  uint64_t h = 1469598103934665603ull;
+  auto feed = [&](const void* p, size_t n) {
+    const unsigned char* c = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < n; ++i) h = (h ^ c[i]) * 1099511628211ull;
+  };
+  feed(&d->precision, sizeof(int));
+  feed(&d->nfft, sizeof(int));
+  feed(&d->nks, sizeof(int));
+  feed(&d->nbnd, sizeof(int));
+  long sk = 0;
+  for (int k = 0; k < d->nks; ++k) sk += d->npw_k[k];
+  feed(d->npw_k, sizeof(int) * (size_t)d->nks);
+  feed(d->miller_k, sizeof(int) * 3 * (size_t)sk);
+  feed(d->u_k, sizeof(double) * 2 * (size_t)d->nbnd * sk);
+  return h;
+}
+
 template <typename T>
 class Chain : public ChainBase {
  public:
@@ -238,6 +262,16 @@ class Chain : public ChainBase {
     for (auto& p : ptrs_) cudaFree(p.first);
   }
   size_t bytes() const override { return bytes_; }
+
+  int create_shared(const ll_system_desc* d, cudaStream_t st, ChainBase* donor, std::string& err) override {
+    Chain<T>* dn = dynamic_cast<Chain<T>*>(donor);
+    if (!dn) { err = "the sharing chain has another precision"; return LL_EINVAL; }
+    if (!dn->ur_share_ || dn->gs_hash_ == 0) { err = "the sharing chain holds no shareable grids"; return LL_EINVAL; }
+    donor_ = dn;
+    const int rc = create(d, st, err);
+    donor_ = nullptr;
+    return rc;
+  }
 
   int create(const ll_system_desc* d, cudaStream_t st, std::string& err) override {
     st_ = st;
@@ -290,6 +324,14 @@ class Chain : public ChainBase {
         }
       }
       release(first);
+    }
+    gs_hash_ = dev_in ? 0 : ground_state_hash(d);
+    if (donor_) {
+      if (dev_in) { err = "grids are shared between chains of host inputs only"; return LL_EINVAL; }
+      if (gs_hash_ != donor_->gs_hash_ || donor_->N_ != N_ || donor_->nks_ != nks_ || donor_->nbnd_ != nbnd_) {
+        err = "the ground state differs from the sharing chain's (grid, k-points, bands, sphere(k) or u_k)";
+        return LL_EINVAL;
+      }
     }
     double b[3][3];
     recip(d->lattice, b);
@@ -398,7 +440,7 @@ class Chain : public ChainBase {
     if ((rc = alloc(&whart_, n3)) || (rc = alloc(&kin_, (long)nks_ * pq)) || (rc = alloc(&uk_, (long)nks_ * nbnd_ * pk)) ||
         (rc = alloc(&ukq_, vq)) || (rc = alloc(&bkq_, bkq_len)) || (rc = alloc(&eps_, (long)nks_ * nbnd_)) ||
         (rc = alloc(&dij_, std::max(1, nproj_))) || (rc = alloc(&vloc_, n3)) || (rc = alloc(&rho_, n3)) ||
-        (rc = alloc(&fxc_, n3)) || (rc = alloc(&ur_, (long)nks_ * nbnd_ * n3)) ||
+        (rc = alloc(&fxc_, n3)) || (rc = ur_alloc((long)nks_ * nbnd_ * n3)) ||
         (rc = alloc(&cbuf_, (long)norb * n * cb_ncol_)) || (rc = alloc(&nprt_, (long)ngroups_ * n3)) ||
         (rc = alloc(&nr_, n3)) || (rc = alloc(&ng_, n3)) || (rc = alloc(&vpr_, n3)) ||
         (rc = alloc(&y_, vq)) || (rc = alloc(&map_, (long)nks_ * pq)) || (rc = alloc(&part_, std::max(2L * nks_, nzv))) ||
@@ -474,9 +516,12 @@ class Chain : public ChainBase {
     k_gather_y<T><<<nks_, 128, 0, st_>>>(nks_, nbnd_, pq, pk, map_, uk_, y_);
     k_project<T><<<dim3(nks_, 1), 128, 0, st_>>>(nks_, nbnd_, pq, dq_.npw, ukq_, y_);
     LL_CK(cudaGetLastError());
-    // u_{vk}(r) grids: columns of sphere(k), then the planes
-    if ((rc = launch_zinv(dk_, uk_, 1)) || (rc = launch_xy(dk_, nks_ * nbnd_, 0, -1, 2, err))) return rc;
-    LL_CK(cudaGetLastError());
+    // u_{vk}(r) grids: columns of sphere(k), then the planes (unless a chain of the same ground
+    // state lends its grids)
+    if (!donor_) {
+      if ((rc = launch_zinv(dk_, uk_, 1)) || (rc = launch_xy(dk_, nks_ * nbnd_, 0, -1, 2, err))) return rc;
+      LL_CK(cudaGetLastError());
+    }
 
 
     // start of the recursion
@@ -1120,6 +1165,23 @@ class Chain : public ChainBase {
         }
   }
 
+  // The u_{vk}(r) grids: own (counted in bytes_, freed with the last chain that uses them) or
+  // the donor's.
+  int ur_alloc(long count) {
+    if (donor_) {
+      ur_share_ = donor_->ur_share_;
+      ur_ = donor_->ur_;
+      return LL_OK;
+    }
+    void* q = nullptr;
+    const size_t nbytes = sizeof(cplx<T>) * (size_t)std::max(1L, count);
+    if (cudaMalloc(&q, nbytes) != cudaSuccess) { cudaGetLastError(); return LL_ENOMEM; }
+    ur_share_ = std::shared_ptr<void>(q, [](void* a) { cudaFree(a); });
+    ur_ = static_cast<cplx<T>*>(q);
+    bytes_ += nbytes;
+    return LL_OK;
+  }
+
   template <typename U>
   int alloc(U** p, long count) {
     void* q = nullptr;
@@ -1194,6 +1256,9 @@ class Chain : public ChainBase {
   HostSphere hk_, hq_;
   SphereDev dk_{}, dq_{};
   std::vector<std::pair<void*, size_t>> ptrs_;   // every allocation and its size
+  std::shared_ptr<void> ur_share_;               // the u_{vk}(r) grids, possibly shared
+  uint64_t gs_hash_ = 0;                         // ground_state_hash of the inputs (0: not shareable)
+  Chain<T>* donor_ = nullptr;                    // during create_shared only
   size_t bytes_ = 0;
   T *whart_ = nullptr, *kin_ = nullptr, *vloc_ = nullptr, *fxc_ = nullptr;
   double *rho_ = nullptr, *eps_ = nullptr, *dij_ = nullptr, *part_ = nullptr, *beta_ = nullptr;

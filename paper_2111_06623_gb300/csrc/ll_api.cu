@@ -113,6 +113,27 @@ int ll_create(const ll_system_desc* desc, void* stream, ll_handle** out) {
   return LL_OK;
 }
 
+int ll_create_sharing(const ll_system_desc* desc, ll_handle* share, void* stream, ll_handle** out) {
+  if (!desc || !out || !share) return fail(LL_EINVAL, "null descriptor, sharing handle or output");
+  *out = nullptr;
+  if (desc->precision != LL_PREC_FP64 && desc->precision != LL_PREC_FP32) return fail(LL_EINVAL, "bad precision");
+  ll_handle* h = new (std::nothrow) ll_handle();
+  if (!h) return fail(LL_ENOMEM, "host allocation");
+  h->stream = static_cast<cudaStream_t>(stream);
+  cudaGetDevice(&h->device);
+  if (share->stream && share->stream != h->stream) cudaStreamSynchronize(share->stream);   // its grids are built
+  h->chain = (desc->precision == LL_PREC_FP64) ? ll::make_chain_f64() : ll::make_chain_f32();
+  std::string err;
+  int rc = h->chain->create_shared(desc, h->stream, share->chain, err);
+  if (rc != LL_OK) {
+    delete h->chain;
+    delete h;
+    return fail(rc, "ll_create_sharing: " + err);
+  }
+  *out = h;
+  return LL_OK;
+}
+
 int ll_destroy(ll_handle* h) {
   if (!h) return LL_OK;
   if (h->stream) cudaStreamSynchronize(h->stream);

@@ -1,13 +1,15 @@
 // Request loop of libll.so: continuous batching of Lanczos chains of different sizes.
 //
-// A scheduler thread owns every running chain.  Each round it (1) admits queued jobs, in
-// arrival order, while a slot is free and the job's device footprint fits the remaining HBM
-// budget, creating the chain on a stream of its own; (2) queues the next chunk of Lanczos steps
-// of every running chain on that chain's stream, so that the chains' kernels overlap on the
-// GPU; (3) waits for the round, and finishes the chains that reached their step count: the
-// spectrum on the device, the coefficients and spectrum copied to the job, the chain's memory
-// released for the next admissions.  Jobs are independent: a chain's result does not depend
-// on what runs beside it (deterministic kernels, no shared state).
+// Three kinds of thread share the work.  The scheduler admits queued jobs, in arrival order,
+// while a slot is free and the job's device footprint fits the remaining HBM budget, and
+// drives every running chain: each chain has a chunk of Lanczos steps in flight on a stream
+// of its own, marked by a CUDA event; when a chain's event has completed, the scheduler
+// queues its next chunk at once (no chain waits for a slower one) or hands the chain on when
+// it is done.  Two worker threads take the host-heavy ends of a job off the scheduler: the
+// creation of a chain (host validation, the upload of the ground state, the set-up kernels)
+// and its completion (spectrum on the device, coefficients and spectrum to the job, device
+// memory released).  Jobs are independent: a chain's result does not depend on what runs
+// beside it (deterministic kernels, no shared state).
 #include <string.h>
 
 #include <algorithm>
@@ -42,8 +44,10 @@ struct Job {
   double eta = 0.0;
   size_t footprint = 0;
   ll::ChainBase* chain = nullptr;
-  std::atomic<bool> cancel{false};  // set by ll_cancel, read by the scheduler between rounds
+  std::atomic<bool> cancel{false};  // set by ll_cancel, read by the scheduler between chunks
   cudaStream_t stream = nullptr;
+  cudaEvent_t chunk_done = nullptr;  // recorded after the chunk in flight
+  bool in_flight = false;            // scheduler thread only
   std::atomic<int> steps_done{0};   // written by the scheduler, read by ll_poll
   std::vector<double> beta;
   std::vector<double> gamma, z, chi, eps_inv, eps;  // complex interleaved
@@ -59,10 +63,17 @@ struct ll_server {
   std::condition_variable cv;
   bool stop = false;
   std::deque<Job*> queue;
-  std::vector<Job*> running;
+  std::vector<Job*> running;       // chains the scheduler drives (scheduler thread only)
+  int n_running = 0;               // running.size(), for ll_server_stats
+  int active = 0;                  // admitted jobs that have not ended (creating, running, completing)
+  struct Task { int kind; Job* job; int rc; std::string err; };   // kind 0: create, 1: complete
+  std::deque<Task> tasks;          // for the workers
+  std::vector<Job*> ready;         // created chains waiting to be driven
+  bool workers_stop = false;
   std::map<uint64_t, Job*> jobs;
   uint64_t next_id = 1;
   std::thread th;
+  std::vector<std::thread> workers;
 };
 
 namespace {
@@ -105,12 +116,17 @@ void finish(ll_server* s, Job* j, int status, const std::string& err) {
     delete j->chain;
     j->chain = nullptr;
   }
+  if (j->chunk_done) {
+    cudaEventDestroy(j->chunk_done);
+    j->chunk_done = nullptr;
+  }
   if (j->stream) {
     cudaStreamDestroy(j->stream);
     j->stream = nullptr;
   }
   std::lock_guard<std::mutex> lock(s->mu);
   s->used -= j->footprint;
+  --s->active;
   j->status = status;
   j->err = err;
   j->state = (status == LL_OK) ? LL_JOB_DONE : LL_JOB_FAILED;
@@ -123,9 +139,10 @@ void finish(ll_server* s, Job* j, int status, const std::string& err) {
 // scheduler must not touch it again: its owner may release it at once.
 bool start_job(ll_server* s, Job* j) {
   std::string err;
-  if (cudaStreamCreateWithFlags(&j->stream, cudaStreamNonBlocking) != cudaSuccess) {
+  if (cudaStreamCreateWithFlags(&j->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&j->chunk_done, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
-    finish(s, j, LL_ECUDA, "stream creation failed");
+    finish(s, j, LL_ECUDA, "stream or event creation failed");
     return false;
   }
   j->chain = (j->desc.precision == LL_PREC_FP64) ? ll::make_chain_f64() : ll::make_chain_f32();
@@ -180,73 +197,131 @@ void complete_job(ll_server* s, Job* j, int lanczos_rc, const std::string& lerr)
   finish(s, j, lanczos_rc, lerr);
 }
 
+// Worker thread: creates chains of admitted jobs and completes ended ones.
+void worker(ll_server* s) {
+  cudaSetDevice(s->device);
+  while (true) {
+    ll_server::Task t;
+    {
+      std::unique_lock<std::mutex> lock(s->mu);
+      s->cv.wait(lock, [&] { return s->workers_stop || !s->tasks.empty(); });
+      if (s->tasks.empty()) return;   // stopping, nothing left to do
+      t = std::move(s->tasks.front());
+      s->tasks.pop_front();
+    }
+    if (t.kind == 0) {
+      if (start_job(s, t.job)) {
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->ready.push_back(t.job);
+        s->cv.notify_all();
+      }
+    } else {
+      complete_job(s, t.job, t.rc, t.err);
+    }
+  }
+}
+
+void push_task(ll_server* s, int kind, Job* j, int rc, const std::string& err) {
+  std::lock_guard<std::mutex> lock(s->mu);
+  s->tasks.push_back({kind, j, rc, err});
+  s->cv.notify_all();
+}
+
 void scheduler(ll_server* s) {
   cudaSetDevice(s->device);
   while (true) {
-    std::vector<Job*> admit;
+    std::vector<Job*> fresh;
+    int chunk;
     {
       std::unique_lock<std::mutex> lock(s->mu);
-      if (s->running.empty() && s->queue.empty())
-        s->cv.wait_for(lock, std::chrono::milliseconds(50), [&] { return s->stop || !s->queue.empty(); });
+      if (s->running.empty() && s->ready.empty() && s->queue.empty())
+        s->cv.wait_for(lock, std::chrono::milliseconds(50),
+                       [&] { return s->stop || !s->queue.empty() || !s->ready.empty(); });
       if (s->stop) break;
-      // used can exceed the budget when a chain's real bytes exceed its estimate: no admission
-      // then (and no unsigned wrap of budget - used)
-      while (!s->queue.empty() && (int)s->running.size() + (int)admit.size() < s->max_slots &&
-             s->used <= s->budget && s->queue.front()->footprint <= s->budget - s->used) {
+      // admission: in arrival order, while a slot is free and the footprint fits (no admission
+      // while used exceeds the budget, which a chain's real bytes can make happen)
+      while (!s->queue.empty() && s->active < s->max_slots && s->used <= s->budget &&
+             s->queue.front()->footprint <= s->budget - s->used) {
         Job* j = s->queue.front();
         s->queue.pop_front();
         j->t_start = now_s();
         s->used += j->footprint;
         s->peak = std::max(s->peak, s->used);
-        admit.push_back(j);
+        ++s->active;
+        s->tasks.push_back({0, j, LL_OK, std::string()});
+        s->cv.notify_all();
       }
-    }
-    for (Job* j : admit) {
-      if (start_job(s, j)) {
-        std::lock_guard<std::mutex> lock(s->mu);
-        s->running.push_back(j);
-      }
-    }
-    std::vector<Job*> run;
-    int chunk;
-    {
-      std::lock_guard<std::mutex> lock(s->mu);
-      run = s->running;
+      fresh.swap(s->ready);
       chunk = s->chunk;
     }
-    if (run.empty()) continue;
-    // one round: queue a chunk of steps on every running chain, then wait for each
-    std::vector<int> rcs(run.size(), LL_OK);
-    std::vector<std::string> errs(run.size());
-    for (size_t i = 0; i < run.size(); ++i) {
-      const int n = std::min(chunk, run[i]->n_steps - run[i]->chain->steps_queued());
-      if (n > 0 && !run[i]->cancel.load()) rcs[i] = run[i]->chain->enqueue(n, errs[i]);
-    }
+    for (Job* j : fresh) s->running.push_back(j);
+    bool progressed = !fresh.empty();
     std::vector<Job*> still;
-    for (size_t i = 0; i < run.size(); ++i) {
-      Job* j = run[i];
-      int done = 0;
-      std::string err = errs[i];
-      int rc = rcs[i];
-      if (rc == LL_OK) rc = j->chain->collect(nullptr, nullptr, nullptr, &done, err);
-      j->steps_done = done;
-      // a cancelled chain ends here, after collect: none of its kernels is in flight
-      if (rc == LL_OK && done < j->n_steps && j->cancel.load()) {
-        rc = LL_ECANCELED;
-        err = "cancelled after " + std::to_string(done) + " steps";
+    for (Job* j : s->running) {
+      if (j->in_flight) {
+        const cudaError_t q = cudaEventQuery(j->chunk_done);
+        if (q == cudaErrorNotReady) {
+          still.push_back(j);
+          continue;
+        }
+        j->in_flight = false;
+        progressed = true;
+        int done = 0;
+        std::string err;
+        int rc = (q == cudaSuccess) ? LL_OK : LL_ECUDA;
+        if (q != cudaSuccess) err = std::string("chunk: ") + cudaGetErrorString(q);
+        if (rc == LL_OK) rc = j->chain->collect(nullptr, nullptr, nullptr, &done, err);
+        j->steps_done = done;
+        // a cancelled chain ends here, with none of its kernels in flight
+        if (rc == LL_OK && done < j->n_steps && j->cancel.load()) {
+          rc = LL_ECANCELED;
+          err = "cancelled after " + std::to_string(done) + " steps";
+        }
+        if (rc != LL_OK || done >= j->n_steps) {
+          push_task(s, 1, j, rc, err);
+          continue;
+        }
       }
-      if (rc != LL_OK || done >= j->n_steps) complete_job(s, j, rc, err);
-      else still.push_back(j);
+      if (j->cancel.load()) {   // cancelled before its first chunk
+        push_task(s, 1, j, LL_ECANCELED, "cancelled after " + std::to_string(j->steps_done.load()) + " steps");
+        progressed = true;
+        continue;
+      }
+      // the next chunk of this chain, at once
+      std::string err;
+      const int n = std::min(chunk, j->n_steps - j->chain->steps_queued());
+      int rc = j->chain->enqueue(n, err);
+      if (rc == LL_OK && cudaEventRecord(j->chunk_done, j->stream) != cudaSuccess) {
+        cudaGetLastError();
+        rc = LL_ECUDA;
+        err = "event record failed";
+      }
+      if (rc != LL_OK) {
+        int done = 0;
+        std::string e2;
+        j->chain->collect(nullptr, nullptr, nullptr, &done, e2);
+        j->steps_done = done;
+        push_task(s, 1, j, rc, err);
+        progressed = true;
+        continue;
+      }
+      j->in_flight = true;
+      progressed = true;
+      still.push_back(j);
     }
-    std::lock_guard<std::mutex> lock(s->mu);
     s->running.swap(still);
+    {
+      std::lock_guard<std::mutex> lock(s->mu);
+      s->n_running = (int)s->running.size();
+    }
+    if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(100));
   }
-  std::vector<Job*> left;
-  {
-    std::lock_guard<std::mutex> lock(s->mu);
-    left.swap(s->running);
+  // shutting down: end every chain once its chunk has finished
+  for (Job* j : s->running) {
+    if (j->stream) cudaStreamSynchronize(j->stream);
+    finish(s, j, LL_ECUDA, "server destroyed");
   }
-  for (Job* j : left) finish(s, j, LL_ECUDA, "server destroyed");
+  s->running.clear();
 }
 
 }  // namespace
@@ -261,6 +336,7 @@ int ll_server_create(size_t hbm_budget_bytes, int max_slots, ll_server** out) {
   cudaGetDevice(&s->device);
   cudaGetLastError();
   s->th = std::thread(scheduler, s);
+  for (int i = 0; i < 2; ++i) s->workers.emplace_back(worker, s);
   *out = s;
   return LL_OK;
 }
@@ -417,7 +493,7 @@ int ll_server_stats(ll_server* s, size_t* used, size_t* peak, int* running, int*
   std::lock_guard<std::mutex> lock(s->mu);
   if (used) *used = s->used;
   if (peak) *peak = s->peak;
-  if (running) *running = (int)s->running.size();
+  if (running) *running = s->n_running;
   if (queued) *queued = (int)s->queue.size();
   return LL_OK;
 }
@@ -438,6 +514,19 @@ int ll_server_destroy(ll_server* s) {
     s->cv.notify_all();
   }
   if (s->th.joinable()) s->th.join();
+  {   // the workers finish what they hold; chains created meanwhile are never driven
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->workers_stop = true;
+    s->cv.notify_all();
+  }
+  for (auto& w : s->workers)
+    if (w.joinable()) w.join();
+  std::vector<Job*> orphans;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    orphans.swap(s->ready);
+  }
+  for (Job* j : orphans) finish(s, j, LL_ECUDA, "server destroyed");
   for (auto& kv : s->jobs) delete kv.second;
   delete s;
   return LL_OK;

@@ -65,6 +65,7 @@ def _load():
     vp = C.c_void_p
     sig = {
         "ll_create": (C.c_int, [C.POINTER(SystemDesc), vp, C.POINTER(vp)]),
+        "ll_create_sharing": (C.c_int, [C.POINTER(SystemDesc), vp, vp, C.POINTER(vp)]),
         "ll_destroy": (C.c_int, [vp]),
         "ll_lanczos": (C.c_int, [vp, C.c_int, _dp, _dp, _dp, _dp, _ip]),
         "ll_lanczos_spectrum": (C.c_int, [vp, C.c_int, _dp, C.c_int, C.c_double, _dp, _dp, _dp]),
@@ -103,7 +104,7 @@ def _load():
 
 
 _lib = _load()
-EXPORTS = ("ll_create", "ll_destroy", "ll_lanczos", "ll_lanczos_spectrum", "ll_spectrum", "ll_spectrum_static",
+EXPORTS = ("ll_create", "ll_create_sharing", "ll_destroy", "ll_lanczos", "ll_lanczos_spectrum", "ll_spectrum", "ll_spectrum_static",
            "ll_lanczos_spectrum_x", "ll_spectrum_x",
            "ll_apply", "ll_get_map", "ll_get_start", "ll_footprint", "ll_bytes", "ll_fsum", "ll_profile", "ll_profile_read", "ll_last_error",
            "ll_version", "ll_fma_peak", "ll_server_create",
@@ -229,7 +230,9 @@ def _make_desc_device(*, lattice, nfft, kcart, miller_k, miller_kq, arrs, eps_k,
 class Chain:
     """One Lanczos chain resident on the device (ll_create ... ll_destroy)."""
 
-    def __init__(self, *, stream=None, **system):
+    def __init__(self, *, stream=None, share=None, **system):
+        """share: a Chain of the same ground state whose u(r) grids this one uses
+        (ll_create_sharing: another momentum transfer Q on one ground state)."""
         d, k = _make_desc(**system)
         self._keep = k
         self.desc = d
@@ -238,7 +241,11 @@ class Chain:
         self.lattice = np.asarray(system["lattice"], dtype=np.float64)
         self.q_cart = np.asarray(system["q_cart"], dtype=np.float64)
         h = C.c_void_p()
-        _check(_lib.ll_create(C.byref(d), C.c_void_p(stream) if stream else None, C.byref(h)))
+        st = C.c_void_p(stream) if stream else None
+        if share is not None:
+            _check(_lib.ll_create_sharing(C.byref(d), share._h, st, C.byref(h)))
+        else:
+            _check(_lib.ll_create(C.byref(d), st, C.byref(h)))
         self._h = h
         self.steps = 0
 
