@@ -429,7 +429,7 @@ class Chain : public ChainBase {
       const bool tc = std::is_same<T, float>::value && split_ && !(tce && tce[0] == '0' && tce[1] == 0);
       tc_nb_op_ = round_up(3 * nbnd_, 32);
       tc_nb_u_ = round_up(nbnd_, 32);
-      tc_op_ = tc && nproj_ + 2 * nbnd_ <= 128 && tc_nb_op_ <= 256 && nproj_ + 3 * nbnd_ <= kTcMaxF4 * kTcThreads / kTcF4;
+      tc_op_ = tc && nproj_ + 2 * nbnd_ <= 128 && tc_nb_op_ <= 256 && nproj_ + 3 * nbnd_ <= kTcMaxRows;
       tc_u_ = tc && 2 * nbnd_ <= 128;
       tc_u2_ = tc && 4 * nbnd_ <= 128;
       tc_nb_ap_ = round_up(2 * nbnd_, 32);
@@ -886,7 +886,7 @@ class Chain : public ChainBase {
       a.ukq = reinterpret_cast<const float4*>(ukq_);
       a.bkq = reinterpret_cast<const float4*>(bkq_);
       a.cpart = cpart; a.spart = spart; a.err = err_; a.jdev = jdev_;
-      const size_t sm = tc_dots_smem(nb);
+      const size_t sm = tc_dots_smem(nb, tc_nsrc<MODE>(nbnd_, nproj_));
       int rc;
       if ((rc = set_smem(k_tc_dots<MODE>, sm, err))) return rc;
       k_tc_dots<MODE><<<dim3(nks_, nvec, nchunk_), kTcThreads, sm, st_>>>(a);
