@@ -79,6 +79,16 @@ typedef struct {
                                stay untouched until ll_create returns; they are read on the
                                device (no host copy).  The index arrays (npw, miller), kcart,
                                eps_k and dij are always host arrays.                         */
+  /* k-point symmetry by the small group of Q (Sec. 2.6).  With kweight (host, [nks], > 0) the
+   * k-points are the representatives of the stars of a full mesh with these star sizes: every
+   * sum over k of the recursions is the weighted sum (the library folds sqrt(w_k nks / sum w)
+   * into u_k).  With nsym > 1, sym (host, [nsym][3][3] int, the identity among them) holds
+   * the operations of the small group of Q on the FFT grid indices, (j1, j2, j3) -> M j mod N
+   * for the grid points r_j = sum_i (j_i/N) a_i, and the response density is averaged over
+   * them before v'_HXC is formed.  NULL / 0: the plain full-mesh sums.                      */
+  const double* kweight;
+  int nsym;
+  const int* sym;
 } ll_system_desc;
 
 enum { LL_WHERE_HOST = 0, LL_WHERE_DEVICE = 1 };

@@ -42,9 +42,9 @@ class KSplit:
         return self.sys.project_c(x, self.ks)
 
     def inner(self, a, b) -> complex:
-        local = sum(np.vdot(ak, bk) for ak, bk in zip(a, b))
+        local = sum(self.sys.kw[k] * np.vdot(ak, bk) for k, ak, bk in zip(self.ks, a, b))
         tot = self.allreduce(np.array([complex(local).real, complex(local).imag]))
-        return complex(tot[0], tot[1]) / self.nks
+        return complex(tot[0], tot[1]) / self.sys.nfull
 
     def apply_op(self, x, upper: bool):
         d = self.sys.apply_d(x, self.ks)

@@ -18,6 +18,15 @@ Operators (Eqs. 24-28, Hartree units):
 Readings: P_c is applied to the whole output of D and K (projecting H x as well keeps
 every Lanczos vector in the conduction manifold); H_{k+Q} = kinetic + V_KS(r) + KB
 projectors; the Hartree kernel runs over every frequency of the FFT box.
+
+k-point symmetry (Sec. 2.6): when the bundle holds only the k-points of the irreducible
+wedge of the small group G_Q of Q, each with its star size m_k (sum_k m_k = N_k of the full
+mesh), every sum over the mesh becomes a weighted sum over the wedge,
+    (a, b) = (1/N_k) sum_k m_k sum_v sum_G conj(a_{vk}(G)) b_{vk}(G),
+    n~(r)  = 4 (1/N_k) sum_k m_k sum_v u*_{vk}(r) x_{vk}(r),
+and the response density is the average of n~ over the group, n'(r) = (1/|G_Q|) sum_S
+n~(S r) (the terms of the k-points of a star are the rotated terms of its representative).
+Without symmetry m_k = 1 and G_Q = {E}: the plain sums above.
 """
 from __future__ import annotations
 
@@ -36,6 +45,11 @@ class System:
         self.n = spec.nfft
         self.omega = spec.omega
         self.nks = bundle.nks
+        self.kw = (np.ones(self.nks) if getattr(bundle, "kweight", None) is None
+                   else np.asarray(bundle.kweight, dtype=np.float64))
+        self.nfull = float(np.sum(self.kw))       # N_k of the full mesh
+        self.sym = (np.eye(3, dtype=np.int64)[None] if getattr(bundle, "sym", None) is None
+                    else np.asarray(bundle.sym, dtype=np.int64))
         self.nbnd = spec.nbnd
         self.approx = approx or spec.approx
         assert self.approx in ("ipa", "rpa", "tddft")
@@ -76,7 +90,7 @@ class System:
         return [np.zeros((self.nbnd, len(m)), dtype=np.complex128) for m in self.mkq]
 
     def inner(self, a, b) -> complex:
-        return sum(np.vdot(ak, bk) for ak, bk in zip(a, b)) / self.nks
+        return sum(w * np.vdot(ak, bk) for w, ak, bk in zip(self.kw, a, b)) / self.nfull
 
     # Every per-k method takes the k index of each entry of its batch in `ks` (default: all
     # k-points in order), so that a rank holding a block of k-points can apply it to its block.
@@ -123,17 +137,32 @@ class System:
         return self.project_c(self.apply_h_minus_eps(x, ks), ks)
 
     def response_density(self, x, ks=None):
-        """n'(r) = 4 (1/N_k) sum_{vk} u*_{vk}(r) x_{vk}(r), u = psi/sqrt(Omega); with `ks`,
-        the part of the sum over those k-points."""
+        """n~(r) = 4 (1/N_k) sum_{vk} m_k u*_{vk}(r) x_{vk}(r), u = psi/sqrt(Omega); with `ks`,
+        the part of the sum over those k-points.  (Without symmetry, n' itself.)"""
         n = self.n
         nr = np.zeros((n, n, n), dtype=np.complex128)
         for k, xk in zip(self._ks(x, ks), x):
             psi = basis.to_grid(xk, self.mkq[k], n)
-            nr += np.sum(self.ur[k].conj() * psi, axis=0)
-        return 4.0 * nr / (self.omega * self.nks)
+            nr += self.kw[k] * np.sum(self.ur[k].conj() * psi, axis=0)
+        return 4.0 * nr / (self.omega * self.nfull)
+
+    def symmetrize(self, nr):
+        """n'(r_j) = (1/|G_Q|) sum_S n~(r_{M_S j}) over the small group of Q (M_S: the integer
+        matrices of its operations on the grid indices, taken mod N)."""
+        if len(self.sym) == 1:
+            return nr
+        n = self.n
+        j = np.stack(np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij"), axis=-1)
+        out = np.zeros_like(nr)
+        for m in self.sym:
+            jm = (j @ m.T) % n
+            out += nr[jm[..., 0], jm[..., 1], jm[..., 2]]
+        return out / len(self.sym)
 
     def hxc_potential(self, nr):
-        """v'(r) = sum_G 4 pi n'(G)/|Q+G|^2 e^{iG.r} + f_xc(n0(r)) n'(r)."""
+        """v'(r) = sum_G 4 pi n'(G)/|Q+G|^2 e^{iG.r} + f_xc(n0(r)) n'(r), n' the average of
+        the density over the small group of Q."""
+        nr = self.symmetrize(nr)
         vh = sfft.ifftn(self.whart * sfft.fftn(nr))
         return vh + self.fxc * nr
 

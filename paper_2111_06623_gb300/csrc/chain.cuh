@@ -250,6 +250,7 @@ static inline uint64_t ground_state_hash(const ll_system_desc* d) {
   feed(d->npw_k, sizeof(int) * (size_t)d->nks);
   feed(d->miller_k, sizeof(int) * 3 * (size_t)sk);
   feed(d->u_k, sizeof(double) * 2 * (size_t)d->nbnd * sk);
+  if (d->kweight) feed(d->kweight, sizeof(double) * (size_t)d->nks);   // folded into u_k
   return h;
 }
 
@@ -300,6 +301,32 @@ class Chain : public ChainBase {
     if (!inputs_finite(d, err)) return LL_EINVAL;
     if (d->where != LL_WHERE_HOST && d->where != LL_WHERE_DEVICE) { err = "bad where"; return LL_EINVAL; }
     const bool dev_in = d->where == LL_WHERE_DEVICE;
+    // k-point weights (stars of the small group of Q) and the group on the grid (Sec. 2.6)
+    kscale_.assign(nks_, 1.0);
+    if (d->kweight) {
+      double sw = 0.0;
+      for (int k = 0; k < nks_; ++k) {
+        if (!(d->kweight[k] > 0) || !std::isfinite(d->kweight[k])) { err = "k-point weights must be positive"; return LL_EINVAL; }
+        sw += d->kweight[k];
+      }
+      for (int k = 0; k < nks_; ++k) kscale_[k] = std::sqrt(d->kweight[k] * nks_ / sw);
+    }
+    if (d->nsym < 0 || (d->nsym > 1 && !d->sym) || d->nsym > 48) { err = "bad symmetry operations"; return LL_EINVAL; }
+    nsym_ = d->nsym > 1 ? d->nsym : 1;
+    sym_host_.assign(9, 0);
+    sym_host_[0] = sym_host_[4] = sym_host_[8] = 1;
+    if (d->nsym > 1) {
+      sym_host_.assign(d->sym, d->sym + 9 * d->nsym);
+      bool has_identity = false;
+      for (int i = 0; i < d->nsym; ++i) {
+        const int* m = d->sym + 9 * i;
+        const long det = (long)m[0] * (m[4] * m[8] - m[5] * m[7]) - (long)m[1] * (m[3] * m[8] - m[5] * m[6]) +
+                         (long)m[2] * (m[3] * m[7] - m[4] * m[6]);
+        if (det != 1 && det != -1) { err = "a symmetry operation is not unimodular"; return LL_EINVAL; }
+        has_identity |= m[0] == 1 && m[4] == 1 && m[8] == 1 && !m[1] && !m[2] && !m[3] && !m[5] && !m[6] && !m[7];
+      }
+      if (!has_identity) { err = "the symmetry operations lack the identity"; return LL_EINVAL; }
+    }
     if (dev_in) {   // device-resident arrays: device pointers, and finite (checked on the device)
       unsigned long long* first = nullptr;
       int rc0;
@@ -373,7 +400,7 @@ class Chain : public ChainBase {
     std::vector<T> vl;
     std::vector<double> rh;
     if (!dev_in) {
-      uk = pad_batch(d->u_k, hk_, nbnd_);
+      uk = pad_batch(d->u_k, hk_, nbnd_, &kscale_);
       ukq = pad_batch(d->u_kq, hq_, nbnd_);
       if (nproj_) bkq = pad_batch(d->beta_kq, hq_, nproj_);
       vl.resize(n3);
@@ -468,20 +495,27 @@ class Chain : public ChainBase {
       LL_CK(cudaMemcpyAsync(rho_, rh.data(), n3 * sizeof(double), cudaMemcpyHostToDevice, st_));
     } else {
       int *offk = nullptr, *offq = nullptr;
-      if ((rc = alloc(&offk, nks_ + 1)) || (rc = alloc(&offq, nks_ + 1))) return rc;
+      double* ksc = nullptr;
+      if ((rc = alloc(&offk, nks_ + 1)) || (rc = alloc(&offq, nks_ + 1)) || (rc = alloc(&ksc, nks_))) return rc;
       LL_CK(cudaMemcpyAsync(offk, hk_.off.data(), (nks_ + 1) * sizeof(int), cudaMemcpyHostToDevice, st_));
       LL_CK(cudaMemcpyAsync(offq, hq_.off.data(), (nks_ + 1) * sizeof(int), cudaMemcpyHostToDevice, st_));
-      k_pad_rows<T><<<dim3(nks_, nbnd_), 256, 0, st_>>>(d->u_k, offk, dk_.npw, nbnd_, hk_.npw_pad, uk_);
-      k_pad_rows<T><<<dim3(nks_, nbnd_), 256, 0, st_>>>(d->u_kq, offq, dq_.npw, nbnd_, pq, ukq_);
-      if (nproj_) k_pad_rows<T><<<dim3(nks_, nproj_), 256, 0, st_>>>(d->beta_kq, offq, dq_.npw, nproj_, pq, bkq_);
+      LL_CK(cudaMemcpyAsync(ksc, kscale_.data(), nks_ * sizeof(double), cudaMemcpyHostToDevice, st_));
+      k_pad_rows<T><<<dim3(nks_, nbnd_), 256, 0, st_>>>(d->u_k, offk, dk_.npw, nbnd_, hk_.npw_pad, ksc, uk_);
+      k_pad_rows<T><<<dim3(nks_, nbnd_), 256, 0, st_>>>(d->u_kq, offq, dq_.npw, nbnd_, pq, nullptr, ukq_);
+      if (nproj_) k_pad_rows<T><<<dim3(nks_, nproj_), 256, 0, st_>>>(d->beta_kq, offq, dq_.npw, nproj_, pq, nullptr, bkq_);
       k_grids_in<T><<<256, 256, 0, st_>>>(n, d->vloc_r, d->rho_r, vloc_, rho_);
       LL_CK(cudaGetLastError());
       LL_CK(cudaStreamSynchronize(st_));   // the caller may reuse its arrays once ll_create returns
       release(offk);
       release(offq);
+      release(ksc);
     }
     LL_CK(cudaMemcpyAsync(eps_, d->eps_k, sizeof(double) * nks_ * nbnd_, cudaMemcpyHostToDevice, st_));
     if (nproj_) LL_CK(cudaMemcpyAsync(dij_, d->dij, sizeof(double) * nproj_, cudaMemcpyHostToDevice, st_));
+    if (nsym_ > 1) {
+      if ((rc = alloc(&sym_, 9L * nsym_))) return rc;
+      LL_CK(cudaMemcpyAsync(sym_, sym_host_.data(), 9L * nsym_ * sizeof(int), cudaMemcpyHostToDevice, st_));
+    }
     LL_CK(cudaMemsetAsync(err_, 0, 2 * sizeof(int), st_));
     LL_CK(cudaMemsetAsync(vecs_, 0, 3L * nvec_ * vq * sizeof(cplx<T>), st_));
     LL_CK(cudaMemsetAsync(zpart_, 0, (long)(cap_ + 1) * nzp * sizeof(cplx<double>), st_));
@@ -1107,7 +1141,12 @@ class Chain : public ChainBase {
   template <int N>
   int hxc_n(std::string& err) {
     const T scale = (T)(4.0 / (omega_ * nks_));
-    k_hxc_fwd<T, N><<<N, 256, 0, st_>>>(nprt_, last_ng_, scale, nr_, ng_);
+    if (nsym_ > 1) {   // the density averaged over the small group of Q, then the same transforms
+      k_dens_sym<T><<<4 * nsm_, 256, 0, st_>>>(nprt_, last_ng_, N, scale, nsym_, sym_, ng_);
+      k_hxc_fwd<T, N><<<N, 256, 0, st_>>>(ng_, 1, T(1), nr_, ng_);
+    } else {
+      k_hxc_fwd<T, N><<<N, 256, 0, st_>>>(nprt_, last_ng_, scale, nr_, ng_);
+    }
     k_hxc_z<T, N><<<(N * N + 63) / 64, 64, 0, st_>>>(ng_, whart_);
     k_hxc_inv<T, N><<<N, 64, 0, st_>>>(ng_, nr_, fxc_, vpr_);
     LL_CK(cudaGetLastError());
@@ -1145,13 +1184,16 @@ class Chain : public ChainBase {
     return LL_OK;
   }
 
-  static std::vector<cplx<T>> pad_batch(const double* src, const HostSphere& h, int nb) {
+  static std::vector<cplx<T>> pad_batch(const double* src, const HostSphere& h, int nb,
+                                        const std::vector<double>* kscale = nullptr) {
     std::vector<cplx<T>> out((size_t)h.nks * nb * h.npw_pad, czero<T>());
     size_t pos = 0;
-    for (int k = 0; k < h.nks; ++k)
+    for (int k = 0; k < h.nks; ++k) {
+      const double f = kscale ? (*kscale)[k] : 1.0;
       for (int v = 0; v < nb; ++v)
         for (int i = 0; i < h.npw[k]; ++i, ++pos)
-          out[((size_t)k * nb + v) * h.npw_pad + i] = mk((T)src[2 * pos], (T)src[2 * pos + 1]);
+          out[((size_t)k * nb + v) * h.npw_pad + i] = mk((T)(f * src[2 * pos]), (T)(f * src[2 * pos + 1]));
+    }
     return out;
   }
   static void unpad_batch(const std::vector<cplx<T>>& in, const HostSphere& h, int nb, double* dst) {
@@ -1257,6 +1299,10 @@ class Chain : public ChainBase {
   SphereDev dk_{}, dq_{};
   std::vector<std::pair<void*, size_t>> ptrs_;   // every allocation and its size
   std::shared_ptr<void> ur_share_;               // the u_{vk}(r) grids, possibly shared
+  std::vector<double> kscale_;                   // sqrt(w_k nks / sum w): folded into u_k
+  std::vector<int> sym_host_;                    // small group of Q on the grid, [nsym][9]
+  int nsym_ = 1;
+  int* sym_ = nullptr;
   uint64_t gs_hash_ = 0;                         // ground_state_hash of the inputs (0: not shareable)
   Chain<T>* donor_ = nullptr;                    // during create_shared only
   size_t bytes_ = 0;

@@ -299,6 +299,31 @@ __global__ void __launch_bounds__(256) k_hxc_fwd(const cplx<T>* __restrict__ npr
   }
 }
 
+// The response density averaged over the small group of Q (Sec. 2.6): out(r_j) = (1/nsym)
+// sum_S scale n~(r_{M_S j}), n~ = the sum of the density groups (the order of k_hxc_fwd),
+// M_S the integer matrices sym[S] on the grid indices (j1, j2, j3), mod N.  Grid layout
+// [j3][j2][j1]; grid-stride loop over the N^3 points.
+template <typename T>
+__global__ void k_dens_sym(const cplx<T>* __restrict__ nprt, int ngroups, int n, T scale, int nsym,
+                           const int* __restrict__ sym, cplx<T>* __restrict__ out) {
+  const long n3 = (long)n * n * n;
+  for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < n3; p += (long)gridDim.x * blockDim.x) {
+    const int j1 = (int)(p % n), j2 = (int)((p / n) % n), j3 = (int)(p / ((long)n * n));
+    cplx<T> acc = czero<T>();
+    for (int s = 0; s < nsym; ++s) {
+      const int* m = sym + 9 * s;
+      const int i1 = (((m[0] * j1 + m[1] * j2 + m[2] * j3) % n) + n) % n;
+      const int i2 = (((m[3] * j1 + m[4] * j2 + m[5] * j3) % n) + n) % n;
+      const int i3 = (((m[6] * j1 + m[7] * j2 + m[8] * j3) % n) + n) % n;
+      const long q = ((long)i3 * n + i2) * n + i1;
+      cplx<T> v = czero<T>();
+      for (int g = 0; g < ngroups; ++g) v = v + nprt[(long)g * n3 + q];
+      acc = acc + v * scale;
+    }
+    out[p] = acc * (T(1) / (T)nsym);
+  }
+}
+
 template <typename T, int N>
 __global__ void __launch_bounds__(64) k_hxc_z(cplx<T>* __restrict__ ng, const T* __restrict__ whart) {
   const int line = blockIdx.x * blockDim.x + threadIdx.x;   // (m2, m1)
@@ -843,11 +868,13 @@ static __global__ void k_first_nonfinite(const double* __restrict__ p, long n, u
 // in T, zero on the padding.  grid (nks, nrow), block 256.
 template <typename T>
 __global__ void k_pad_rows(const double* __restrict__ src, const int* __restrict__ off, const int* __restrict__ npw,
-                           int nrow, int npw_pad, cplx<T>* __restrict__ dst) {
+                           int nrow, int npw_pad, const double* __restrict__ kscale, cplx<T>* __restrict__ dst) {
   const int k = blockIdx.x, r = blockIdx.y, n = npw[k];
   const double* s = src + 2 * ((long)nrow * off[k] + (long)r * n);
+  const double f = kscale ? kscale[k] : 1.0;   // sqrt of the k-point weight (u_k only)
   cplx<T>* d = dst + ((long)k * nrow + r) * npw_pad;
-  for (int g = threadIdx.x; g < npw_pad; g += blockDim.x) d[g] = g < n ? mk((T)s[2 * g], (T)s[2 * g + 1]) : czero<T>();
+  for (int g = threadIdx.x; g < npw_pad; g += blockDim.x)
+    d[g] = g < n ? mk((T)(f * s[2 * g]), (T)(f * s[2 * g + 1])) : czero<T>();
 }
 
 // Grids [j1][j2][j3] -> [j3][j2][j1]: V in T, the density in double.

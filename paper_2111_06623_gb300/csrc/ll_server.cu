@@ -38,7 +38,8 @@ struct Job {
   std::string err;
   // deep copy of the system (dropped when the job ends)
   std::vector<double> kcart, u_k, u_kq, eps_k, vloc, rho, beta_kq, dij, omega;
-  std::vector<int> npw_k, miller_k, npw_kq, miller_kq;
+  std::vector<int> npw_k, miller_k, npw_kq, miller_kq, sym;
+  std::vector<double> kweight;
   ll_system_desc desc{};
   int n_steps = 0;
   double eta = 0.0;
@@ -390,6 +391,8 @@ int ll_submit(ll_server* s, const ll_job_desc* jd, uint64_t* job_id) {
     return sfail(LL_EINVAL, "malformed job: device input arrays could not be read");
   }
   if (jd->n_omega > 0) copy_in(j->omega, jd->omega_ev, jd->n_omega);
+  if (d->kweight) copy_in(j->kweight, d->kweight, (size_t)d->nks);
+  if (d->nsym > 1 && d->sym) copy_in(j->sym, d->sym, 9 * (size_t)d->nsym);
   j->desc = *d;
   j->desc.kcart = j->kcart.data();
   j->desc.npw_k = j->npw_k.data();
@@ -404,6 +407,8 @@ int ll_submit(ll_server* s, const ll_job_desc* jd, uint64_t* job_id) {
   j->desc.beta_kq = d->nproj > 0 ? j->beta_kq.data() : nullptr;
   j->desc.dij = d->nproj > 0 ? j->dij.data() : nullptr;
   j->desc.where = LL_WHERE_HOST;
+  j->desc.kweight = d->kweight ? j->kweight.data() : nullptr;
+  j->desc.sym = (d->nsym > 1 && d->sym) ? j->sym.data() : nullptr;
   {
     std::string err;
     if (!ll::inputs_finite(&j->desc, err)) {

@@ -39,6 +39,7 @@ class SystemDesc(C.Structure):
         ("npw_kq", _ip), ("miller_kq", _ip), ("u_k", _dp), ("u_kq", _dp), ("eps_k", _dp), ("vloc_r", _dp),
         ("rho_r", _dp), ("beta_kq", _dp), ("dij", _dp), ("approx", C.c_int), ("flavour", C.c_int),
         ("precision", C.c_int), ("max_steps", C.c_int), ("where", C.c_int),
+        ("kweight", _dp), ("nsym", C.c_int), ("sym", _ip),
     ]
 
 
@@ -142,7 +143,8 @@ def _cat_complex(blocks) -> np.ndarray:
 
 
 def _make_desc(*, lattice, nfft, kcart, miller_k, miller_kq, u_k, u_kq, eps_k, vloc_r, rho_r, beta_kq=None,
-               dij=None, q_cart, approx="tddft", flavour="ph", precision="fp64", max_steps=1000):
+               dij=None, q_cart, approx="tddft", flavour="ph", precision="fp64", max_steps=1000, kweight=None,
+               sym=None):
     """An ll_system_desc and the arrays it points into (keep them alive while it is used).
 
     u_k, u_kq, beta_kq, vloc_r and rho_r are host arrays (u_k, u_kq, beta_kq as lists of
@@ -163,9 +165,11 @@ def _make_desc(*, lattice, nfft, kcart, miller_k, miller_kq, u_k, u_kq, eps_k, v
         for name, t in arrs.items():
             if not _on_device(t):
                 raise ValueError(f"{name}: with u_k on the device every large array must be a CUDA tensor")
-        return _make_desc_device(lattice=lattice, nfft=nfft, kcart=kcart, miller_k=miller_k, miller_kq=miller_kq,
+        d, k = _make_desc_device(lattice=lattice, nfft=nfft, kcart=kcart, miller_k=miller_k, miller_kq=miller_kq,
                                  arrs=arrs, eps_k=eps_k, dij=dij, nbnd=nbnd, nproj=nproj, q_cart=q_cart,
                                  approx=approx, flavour=flavour, precision=precision, max_steps=max_steps)
+        _set_symmetry(d, k, kweight, sym)
+        return d, k
     k = dict(
         kcart=np.ascontiguousarray(kcart, dtype=np.float64),
         npw_k=np.array([len(m) for m in miller_k], dtype=np.int32),
@@ -194,7 +198,19 @@ def _make_desc(*, lattice, nfft, kcart, miller_k, miller_kq, u_k, u_kq, eps_k, v
     d.approx, d.flavour, d.precision = APPROX[approx], FLAVOUR[flavour], PRECISION[precision]
     d.max_steps = int(max_steps)
     d.where = LL_WHERE_HOST
+    _set_symmetry(d, k, kweight, sym)
     return d, k
+
+
+def _set_symmetry(d, keep, kweight, sym):
+    """k-point weights (star sizes of the small group of Q) and the group's integer matrices on
+    the FFT grid (Sec. 2.6); None: the plain full-mesh sums."""
+    if kweight is not None:
+        keep["kweight"] = np.ascontiguousarray(kweight, dtype=np.float64)
+        d.kweight = _d(keep["kweight"])
+    if sym is not None and len(sym) > 1:
+        keep["sym"] = np.ascontiguousarray(sym, dtype=np.int32).reshape(-1)
+        d.nsym, d.sym = len(sym), _i(keep["sym"])
 
 
 def _make_desc_device(*, lattice, nfft, kcart, miller_k, miller_kq, arrs, eps_k, dij, nbnd, nproj, q_cart, approx,

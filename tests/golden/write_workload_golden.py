@@ -75,14 +75,31 @@ def write(case: str, steps: int | None = None, world: int | None = None) -> None
     print(f"{case}: {steps} steps in {dt:.0f} s on {used} processes -> {path(case)}", flush=True)
 
 
+def redigest(case: str) -> None:
+    """Rewrite only the bundle_digest line of a stored case (after a change of the digest's
+    definition), from the cached bundle; the coefficients are left as they are."""
+    mk, _, _ = CASES[case]
+    digest = w.bundle_digest(w.get_bundle(mk()))
+    with open(path(case)) as fh:
+        lines = fh.readlines()
+    lines = [f"# bundle_digest: {digest}\n" if ln.startswith("# bundle_digest:") else ln for ln in lines]
+    with open(path(case), "w") as fh:
+        fh.writelines(lines)
+    print(f"{case}: digest {digest}")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("cases", nargs="*", default=list(CASES))
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--world", type=int, default=None)
+    ap.add_argument("--redigest", action="store_true", help="rewrite the digest lines only")
     args = ap.parse_args()
     for c in args.cases:
-        write(c, args.steps, args.world)
+        if args.redigest:
+            redigest(c)
+        else:
+            write(c, args.steps, args.world)
 
 
 if __name__ == "__main__":

@@ -8,7 +8,8 @@ def chain_from_bundle(b, approx=None, flavour="ph", precision="fp64", max_steps=
     return ll.Chain(lattice=s.lattice, nfft=s.nfft, kcart=b.kcart, miller_k=b.miller_k, miller_kq=b.miller_kq,
                     u_k=b.u_k, u_kq=b.u_kq, eps_k=b.eps_k, vloc_r=b.vloc_r, rho_r=b.rho_r, beta_kq=b.beta_kq,
                     dij=b.dij, q_cart=s.q_cart, approx=approx or s.approx, flavour=flavour,
-                    precision=precision, max_steps=max_steps, stream=stream)
+                    precision=precision, max_steps=max_steps, stream=stream,
+                    kweight=getattr(b, "kweight", None), sym=getattr(b, "sym", None))
 
 
 def rel_batch(a, b):

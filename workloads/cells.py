@@ -57,6 +57,7 @@ class SystemSpec:
     steps: int = 300
     flavour: str = "ph"            # 'ph' pseudo-Hermitian | 'nh' non-Hermitian
     free_electron: bool = False    # V_ion = 0 and plane-wave occupations (Lindhard pins)
+    symmetry: bool = False         # response k-points in the irreducible wedge of the small group of Q
     extra: dict = field(default_factory=dict)
 
     @property
@@ -89,22 +90,24 @@ def _diamond(a: float) -> tuple[np.ndarray, np.ndarray]:
     return lat, tau
 
 
-def config_small() -> SystemSpec:
+def config_small(symmetry: bool = False) -> SystemSpec:
     """Two-atom diamond-structure cell, 10 Ry, 18^3 grid, 4x4x4 mesh, Q = 0.1 (2pi/a) x,
-    RPA+ALDA kernel, 300 pseudo-Hermitian steps, FP64."""
+    RPA+ALDA kernel, 300 pseudo-Hermitian steps, FP64.  symmetry: the irreducible k-points of
+    the small group of Q."""
     lat, tau = _diamond(A_LAT)
     q = 0.1 * (2 * np.pi / A_LAT) * np.array([1.0, 0.0, 0.0])
-    return SystemSpec("fcc2_10ry_18", lat, tau, 4.0, 1.0, 10.0, 18, (4, 4, 4), 4, q,
-                      approx="tddft", steps=300, flavour="ph")
+    return SystemSpec("fcc2_10ry_18" + ("_ibz" if symmetry else ""), lat, tau, 4.0, 1.0, 10.0, 18, (4, 4, 4), 4, q,
+                      approx="tddft", steps=300, flavour="ph", symmetry=symmetry)
 
 
-def config_kb() -> SystemSpec:
+def config_kb(symmetry: bool = False) -> SystemSpec:
     """Same cell and Q as config_small plus KB s/p projectors, 25 Ry, 32^3 grid,
-    8x8x8 mesh, 1000 steps of either recursion."""
+    8x8x8 mesh, 1000 steps of either recursion.  symmetry: the k-points of the irreducible
+    wedge of the small group of Q, with their weights (Sec. 2.6)."""
     lat, tau = _diamond(A_LAT)
     q = 0.1 * (2 * np.pi / A_LAT) * np.array([1.0, 0.0, 0.0])
-    return SystemSpec("fcc2kb_25ry_32", lat, tau, 4.0, 1.0, 25.0, 32, (8, 8, 8), 4, q,
-                      approx="tddft", kb=True, scf_kmesh=(4, 4, 4), steps=1000, flavour="ph")
+    return SystemSpec("fcc2kb_25ry_32" + ("_ibz" if symmetry else ""), lat, tau, 4.0, 1.0, 25.0, 32, (8, 8, 8), 4, q,
+                      approx="tddft", kb=True, scf_kmesh=(4, 4, 4), steps=1000, flavour="ph", symmetry=symmetry)
 
 
 def _diamond_cubic(a: float) -> tuple[np.ndarray, np.ndarray]:
@@ -193,6 +196,80 @@ def sphere(kcart: np.ndarray, bvec: np.ndarray, ecut_ry: float, guard: float = 1
     sel = m[g2 <= ecut_ry]
     order = np.lexsort((sel[:, 2], sel[:, 1], sel[:, 0]))
     return np.ascontiguousarray(sel[order].astype(np.int32))
+
+
+def point_operations() -> list[np.ndarray]:
+    """The 48 orthogonal operations of the cube (signed permutation matrices), Cartesian."""
+    import itertools
+    ops = []
+    for perm in itertools.permutations(range(3)):
+        for signs in itertools.product((1, -1), repeat=3):
+            r = np.zeros((3, 3))
+            for i, j in enumerate(perm):
+                r[i, j] = signs[i]
+            ops.append(r)
+    return ops
+
+
+def small_group(spec: SystemSpec, tol: float = 1e-9) -> list[np.ndarray]:
+    """The point operations R (Cartesian) of the crystal that need no fractional translation
+    (R maps every atom onto an atom of the same kind, up to a lattice vector, so the local
+    potential and the s/p projectors are invariant) and leave Q invariant (R Q = Q): the small
+    group of Q used to reduce the k-points (Sec. 2.6).  Identity first."""
+    lat = spec.lattice
+    inv_lat = np.linalg.inv(lat)
+    out = []
+    for r in point_operations():
+        if np.linalg.norm(r @ spec.q_cart - spec.q_cart) > tol * max(1.0, np.linalg.norm(spec.q_cart)):
+            continue
+        m = inv_lat.T @ r @ lat.T                 # the operation on fractional coordinates
+        if np.max(np.abs(m - np.round(m))) > tol:
+            continue
+        ok = True
+        for t in spec.tau:
+            f = (r @ t) @ inv_lat                 # fractional coordinates of R tau
+            if not any(np.max(np.abs((f - u @ inv_lat) - np.round(f - u @ inv_lat))) < tol for u in spec.tau):
+                ok = False
+                break
+        if ok:
+            out.append(r)
+    out.sort(key=lambda r: 0 if np.allclose(r, np.eye(3)) else 1)
+    return out
+
+
+def grid_operations(spec: SystemSpec, ops: list[np.ndarray]) -> np.ndarray:
+    """Integer matrices M (nsym, 3, 3) with R r_j = r_{M j} for the grid points r_j = sum_i
+    (j_i / N) a_i: M = A^-T R A^T (A rows a_i), indices taken mod N."""
+    lat = spec.lattice
+    return np.array([np.round(np.linalg.inv(lat.T) @ r @ lat.T).astype(np.int32) for r in ops], dtype=np.int32)
+
+
+def irreducible_kpoints(spec: SystemSpec, ops: list[np.ndarray]) -> tuple[np.ndarray, np.ndarray]:
+    """The k-points of the Gamma-centred mesh reduced by the operations (each star R k of the
+    mesh represented by its first member in mesh order) and their multiplicities (star sizes,
+    summing to the mesh size).  Returns (kfrac (nirr, 3), multiplicity (nirr,))."""
+    n = np.array(spec.kmesh)
+    kf = kmesh_frac(tuple(n))
+    bvec = spec.bvec
+    inv_b = np.linalg.inv(bvec)
+    index = {tuple(np.round(f * n).astype(int) % n): i for i, f in enumerate(kf)}
+    seen = np.full(len(kf), -1)
+    reps, mult = [], []
+    for i, f in enumerate(kf):
+        if seen[i] >= 0:
+            continue
+        star = set()
+        for r in ops:
+            g = ((r @ (f @ bvec)) @ inv_b) * n
+            gi = np.round(g).astype(int)
+            if np.max(np.abs(g - gi)) > 1e-6:
+                raise ValueError("an operation does not map the k-mesh onto itself")
+            star.add(index[tuple(gi % n)])
+        for j in star:
+            seen[j] = len(reps)
+        reps.append(f)
+        mult.append(len(star))
+    return np.array(reps), np.array(mult, dtype=np.float64)
 
 
 def fft_miller(n: int) -> np.ndarray:

@@ -20,7 +20,8 @@ import numpy as np
 import scipy.linalg as sla
 from scipy.special import dawsn
 
-from .cells import SystemSpec, fft_miller, kmesh_frac, sphere
+from .cells import (SystemSpec, fft_miller, grid_operations, irreducible_kpoints, kmesh_frac, small_group,
+                    sphere)
 
 PZ_GAMMA, PZ_B1, PZ_B2 = -0.1423, 1.0529, 0.3334
 PZ_A, PZ_B, PZ_C, PZ_D = 0.0311, -0.048, 0.0020, -0.0116
@@ -195,6 +196,8 @@ class Bundle:
     dij: np.ndarray            # (nproj,) Ha
     scf_iters: int = 0
     gap_min: float = 0.0       # min_k (eps_{nbnd+1,k+Q} - eps_{nbnd,k}) (Ha), positivity of D
+    kweight: np.ndarray | None = None   # (nks,) star sizes of irreducible k-points (None: every k once)
+    sym: np.ndarray | None = None       # (nsym,3,3) int: the small group of Q on the FFT grid (None: identity)
 
     @property
     def nks(self):
@@ -306,7 +309,13 @@ def scf(spec: SystemSpec, tol: float = 1e-11, maxiter: int = 80, verbose: bool =
 def build_bundle(spec: SystemSpec, verbose: bool = False) -> Bundle:
     """SCF, then the occupied states (and one more band, for the gap check) at every k and k+Q."""
     n = spec.nfft
-    kf = kmesh_frac(spec.kmesh)
+    kweight = sym = None
+    if spec.symmetry:
+        ops = small_group(spec)
+        kf, kweight = irreducible_kpoints(spec, ops)
+        sym = grid_operations(spec, ops)
+    else:
+        kf = kmesh_frac(spec.kmesh)
     kc = kf @ spec.bvec
     kq = kc + spec.q_cart[None, :]
     npw_est = 4.0 / 3.0 * np.pi * spec.ecut_ry ** 1.5 * spec.omega / (2 * np.pi) ** 3
@@ -335,7 +344,7 @@ def build_bundle(spec: SystemSpec, verbose: bool = False) -> Bundle:
                   u_kq=[np.ascontiguousarray(r[2][:nb]) for r in res_q],
                   eps_k=np.array([r[1][:nb] for r in res_k]),
                   eps_kq=np.array([r[1][:nb] for r in res_q]),
-                  vloc_r=v, rho_r=rho, beta_kq=beta, dij=dij, scf_iters=iters, gap_min=gap)
+                  vloc_r=v, rho_r=rho, beta_kq=beta, dij=dij, scf_iters=iters, gap_min=gap, kweight=kweight, sym=sym)
 
 
 def _scf_cached(spec: SystemSpec, verbose: bool, runner) -> tuple:
@@ -343,7 +352,7 @@ def _scf_cached(spec: SystemSpec, verbose: bool, runner) -> tuple:
     momentum transfer of one system reuses it (npz under .ll_cache/)."""
     d = {k: (np.asarray(v).round(12).tolist() if isinstance(v, np.ndarray) else v)
          for k, v in spec.__dict__.items()
-         if k not in ("steps", "flavour", "approx", "extra", "q_cart", "kmesh", "name", "scf_kmesh")}
+         if k not in ("steps", "flavour", "approx", "extra", "q_cart", "kmesh", "name", "scf_kmesh", "symmetry")}
     d["scf_mesh"] = list(spec.scf_kmesh or spec.kmesh)
     key = hashlib.sha1(json.dumps(d, sort_keys=True, default=str).encode()).hexdigest()[:16]
     path = os.path.join(cache_dir(), f"scf_{key}.npz")
@@ -360,6 +369,8 @@ def _scf_cached(spec: SystemSpec, verbose: bool, runner) -> tuple:
 def _spec_key(spec: SystemSpec) -> str:
     d = {k: (np.asarray(v).round(12).tolist() if isinstance(v, np.ndarray) else v)
          for k, v in spec.__dict__.items() if k not in ("steps", "flavour", "approx", "extra")}
+    if not d.get("symmetry"):      # keys of full-mesh bundles as before the option existed
+        d.pop("symmetry", None)
     return hashlib.sha1(json.dumps(d, sort_keys=True, default=str).encode()).hexdigest()[:16]
 
 
@@ -378,6 +389,8 @@ def save_bundle(b: Bundle, path: str) -> None:
                 npw_k=b.npw_k, npw_kq=b.npw_kq,
                 miller_k=np.concatenate(b.miller_k), miller_kq=np.concatenate(b.miller_kq),
                 u_k=np.concatenate([u.T for u in b.u_k]), u_kq=np.concatenate([u.T for u in b.u_kq]))
+    if b.kweight is not None:
+        arrs.update(kweight=b.kweight, sym=b.sym)
     np.savez(path, **arrs)
 
 
@@ -398,16 +411,22 @@ def load_bundle(spec: SystemSpec, path: str) -> Bundle:
                   u_k=[np.ascontiguousarray(sl(z["u_k"], sk, i).T) for i in range(nks)],
                   u_kq=[np.ascontiguousarray(sl(z["u_kq"], sq, i).T) for i in range(nks)],
                   eps_k=z["eps_k"], eps_kq=z["eps_kq"], vloc_r=z["vloc_r"], rho_r=z["rho_r"],
-                  beta_kq=beta, dij=z["dij"], scf_iters=int(z["scf_iters"]), gap_min=float(z["gap_min"]))
+                  beta_kq=beta, dij=z["dij"], scf_iters=int(z["scf_iters"]), gap_min=float(z["gap_min"]),
+                  kweight=z["kweight"] if "kweight" in z.files else None, sym=z["sym"] if "sym" in z.files else None)
 
 
 def bundle_digest(b: Bundle) -> str:
-    """sha256 (16 hex digits) of every array a chain consumes, in a fixed order: two bundles
-    with the same digest are the same input to the last bit.  (A bundle rebuilt by another
-    machine's LAPACK differs in the last bits of the orbitals, and so in its digest.)"""
+    """sha256 (16 hex digits) of every stored array a chain consumes, in a fixed order: two
+    bundles with the same digest hold the same ground state to the last bit.  (A bundle rebuilt
+    by another machine's LAPACK differs in the last bits of the orbitals, and so in its digest.)
+    The KB projectors are left out: they are a closed form of the cell and the spheres (both
+    covered), rebuilt on every load with the machine's own exp and Dawson function, so they
+    may differ in the last bit between machines reading the same file."""
     h = hashlib.sha256()
     arrays = [b.kcart, b.eps_k, b.vloc_r, b.rho_r, b.dij] + list(b.miller_k) + list(b.miller_kq) + \
-        list(b.u_k) + list(b.u_kq) + list(b.beta_kq)
+        list(b.u_k) + list(b.u_kq)
+    if b.kweight is not None:
+        arrays += [b.kweight, b.sym]
     for a in arrays:
         a = np.ascontiguousarray(a)
         h.update(str(a.dtype).encode() + str(a.shape).encode())
