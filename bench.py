@@ -71,7 +71,27 @@ def _chain(b, precision, max_steps, stream, flavour="ph"):
     return ll.Chain(lattice=s.lattice, nfft=s.nfft, kcart=b.kcart, miller_k=b.miller_k, miller_kq=b.miller_kq,
                     u_k=b.u_k, u_kq=b.u_kq, eps_k=b.eps_k, vloc_r=b.vloc_r, rho_r=b.rho_r, beta_kq=b.beta_kq,
                     dij=b.dij, q_cart=s.q_cart, approx="tddft", flavour=flavour, precision=precision,
-                    max_steps=max_steps, stream=stream)
+                    max_steps=max_steps, stream=stream, kweight=b.kweight, sym=b.sym)
+
+
+def _kb_wedge(b_full, stream, K, W):
+    """The KB workload on the irreducible wedge of the small group of Q (Sec. 2.6: 164 of the
+    512 k-points, star-size weights, the density averaged over the group): the same chain as
+    the full mesh.  FP32 steps/s over K steps, and the loss function of its first 100
+    coefficients against the oracle's full-mesh golden coefficients (when they match the
+    full-mesh bundle)."""
+    import workloads as w
+    b = w.get_bundle(w.config_kb(True))
+    ch, c, ms, _ = _time_chain(b, "fp32", K, W, stream, extra=64 + SPEC_WINDOW)
+    if ch.steps < SPEC_WINDOW:
+        ch.lanczos(SPEC_WINDOW - ch.steps)
+    c = ch.lanczos(0)
+    ch.close()
+    ref = _golden(b_full, "kb_ph", SPEC_WINDOW)
+    return {"workload": "fcc2kb_25ry_32 on the irreducible wedge of the small group of Q (C2v)",
+            "kpoints": int(b.nks), "kpoints_full_mesh": int(np.sum(b.kweight)), "steps": K,
+            "steps_per_s": K / (ms / 1e3), "ms_per_step": ms / K, "dtype": "f32",
+            "loss_err_vs_full_mesh_oracle_100": None if ref is None else _loss_err(c, ref, b_full, SPEC_WINDOW)}
 
 
 def _bundle_bytes(b) -> int:
@@ -175,18 +195,22 @@ def _step_flops(b) -> tuple[float, float]:
     return nominal, 0.5 * (dk + d)
 
 
-def _sc16(stream, steps: int = 200):
+def _sc16(stream, steps: int = 2000):
     """The sixteen-atom cell (32 bands, 48^3, 64 KB projectors, 2048 orbitals of ~6000 plane
-    waves; the split per-k path), FP32 pseudo-Hermitian steps, when its ground state is cached
-    (building it takes ~30 minutes of CPU)."""
+    waves; the split per-k path with tensor-core projections), the configured 2000 FP32
+    pseudo-Hermitian steps, when its ground state is cached (building it takes ~90 minutes of
+    CPU); with the loss function of the first 100 coefficients against the oracle's golden
+    coefficients of the same bundle."""
     import workloads as w
     b = w.cached_bundle(w.config_sc16())
     if b is None:
-        return {"skipped": "ground state not cached (workloads.get_bundle(config_sc16()) takes ~30 min of CPU)"}
-    ch, _, ms, _ = _time_chain(b, "fp32", steps, 3, stream)
+        return {"skipped": "ground state not cached (workloads.get_bundle(config_sc16()) takes ~90 min of CPU)"}
+    ch, c, ms, _ = _time_chain(b, "fp32", steps, 3, stream)
     ch.close()
+    ref = _golden(b, "sc16_ph", SPEC_WINDOW)
     return {"workload": "sc16kb_30ry_48: 16-atom 2x2x2 supercell + KB s/p, 30 Ry, 48^3, 4x4x4 k, 32 bands, PH",
-            "steps": steps, "steps_per_s": steps / (ms / 1e3), "ms_per_step": ms / steps, "dtype": "f32"}
+            "steps": steps, "steps_per_s": steps / (ms / 1e3), "ms_per_step": ms / steps, "dtype": "f32",
+            "loss_err_vs_oracle_100": None if ref is None else _loss_err(c, ref, b, SPEC_WINDOW)}
 
 
 def source_digest() -> str:
@@ -533,6 +557,7 @@ def main():
         # steps and the spectrum, on the device
         small = _small_cell(stream)
     sc16 = None if args.headline_only else _sc16(stream)
+    wedge = None if args.headline_only else _kb_wedge(b, stream, K, W)
     # the spectrum check spans the first SPEC_WINDOW coefficients whatever K is: the chains run
     # on, untimed, to that many steps
     kt = len(c32[0])
@@ -637,7 +662,7 @@ def main():
                        "l2": "per-step working set ~0.6 GB > 129 MB L2 (no flush)", "parallelism": "replicas"},
             "fp64": None if args.headline_only else {"value": world * K / (ms64 / 1e3), "ms_per_step": ms64 / K,
                                                       "dtype": "f64"},
-            "nh_fp32": nh, "small_cell": small, "sc16": sc16,
+            "nh_fp32": nh, "small_cell": small, "sc16": sc16, "kb_wedge": wedge,
             "speedup_fp32_vs_fp64": ms64 / ms32,
             "spectrum_err_fp32_vs_fp64": spec_err, "spectrum_window_steps": m,
             "spectrum_err_fp32_vs_fp64_timed_steps": spec_err_full, "spectrum_vs_oracle": vs_oracle,

@@ -1104,8 +1104,18 @@ class Chain : public ChainBase {
       return m;
     };
     // fewer orbitals per batch where the default batch's tiles exceed shared memory (FP64 at
-    // N = 48 on the 16-atom cell)
-    while (B > 1 && smem_for(B) > 200 * 1024) --B;
+    // N = 48 on the 16-atom cell), or would keep the SM below the CTA count its registers
+    // allow (N = 48: 116 KB for 8 orbitals left one 4-warp CTA per SM)
+    if (xy_occ_reg_[MODE] == 0) {
+      int occ = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_xy<T, N, MODE>, 128, 0) != cudaSuccess || occ < 1) {
+        cudaGetLastError();
+        occ = 1;
+      }
+      xy_occ_reg_[MODE] = std::min(occ, 8);
+    }
+    const size_t per_sm = 227 * 1024 - 2048 * (size_t)xy_occ_reg_[MODE];
+    while (B > 1 && (smem_for(B) > 200 * 1024 || smem_for(B) * xy_occ_reg_[MODE] > per_sm)) --B;
     const size_t smem = smem_for(B);
     a.bo = B;
     int rc;
@@ -1318,6 +1328,7 @@ class Chain : public ChainBase {
   bool eager_done_[2] = {false, false};
   cudaGraphExec_t graph_[2] = {nullptr, nullptr};   // one captured step per parity of j
   bool split_ = false;      // per-k work split over chunks of plane waves (split.cuh)
+  int xy_occ_reg_[4] = {0, 0, 0, 0};   // CTAs per SM the plane pass's registers allow, per mode
   bool tc_op_ = false, tc_u_ = false, tc_u2_ = false;   // split-path dot blocks on the tensor cores
   bool tc_ap_ = false;                                    // split-path projections applied on the tensor cores
   int tc_nb_op_ = 32, tc_nb_u_ = 32, tc_nb_ap_ = 32;      // N of those MMAs (Bop rows, padded to 32)
