@@ -15,6 +15,7 @@
 #include "ll.h"
 #include "split.cuh"
 #include "tcproj.cuh"
+#include "xypair.cuh"
 
 #include <type_traits>
 
@@ -478,6 +479,8 @@ class Chain : public ChainBase {
     {
       const char* g = getenv("LL_GRAPHS");
       use_graphs_ = use_graphs_ && !(g && g[0] == '0' && g[1] == 0);
+      const char* xp = getenv("LL_XY_PAIR");   // 1: lane pairs for every even N, 0: never (k_xy)
+      xy_pair_ = (xp && xp[1] == 0 && (xp[0] == '0' || xp[0] == '1')) ? xp[0] - '0' : -1;
     }
     // chunk partials: U^H x per vector (two per vector on the non-Hermitian update), B^H x
     if (split_ && ((rc = alloc(&sp_s_, 2 * nzv * nbnd_ * nbnd_)) || (rc = alloc(&sp_c_, nzv * std::max(1, nproj_ * nbnd_))) ||
@@ -1068,10 +1071,10 @@ class Chain : public ChainBase {
   // Orbital groups of one plane-pass launch (grid N x groups): as many CTAs as fit on the
   // GPU at once for this mode's occupancy, so that the launch is a single wave.
   template <typename K>
-  int groups_for_kernel(K kernel, size_t smem, int norb, int& cache) {
+  int groups_for_kernel(K kernel, size_t smem, int norb, int& cache, int threads = 128) {
     if (cache == 0) {
       int occ = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, 128, smem) != cudaSuccess || occ < 1) {
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem) != cudaSuccess || occ < 1) {
         cudaGetLastError();
         occ = 1;
       }
@@ -1081,6 +1084,18 @@ class Chain : public ChainBase {
   }
   template <int N, int MODE>
   int xy_nm(const SphereDev& s, int norb, int o_off, int dens_vec, std::string& err) {
+    if constexpr (N == 24 || N == 32 || N == 36 || N == 48) {
+      // every line transform split over a lane pair (xypair.cuh): half the registers per thread.
+      // Measured on GB300: faster at N = 48 (16-atom cell, pass 2 0.67 -> 0.55 ms per step),
+      // slower at N = 32 (KB workload, pass 1 0.26 -> 0.29 ms), so the default is N = 48 only
+      if (xy_pair_ == 1 || (xy_pair_ < 0 && N == 48))
+        return xy_launch<N, MODE>(k_xyp<T, N, MODE>, 4 * N, 2, s, norb, o_off, dens_vec, err);
+    }
+    return xy_launch<N, MODE>(k_xy<T, N, MODE>, 128, 128 / N, s, norb, o_off, dens_vec, err);
+  }
+  template <int N, int MODE, typename K>
+  int xy_launch(K kernel, int threads, int slots, const SphereDev& s, int norb, int o_off, int dens_vec,
+                std::string& err) {
     int B = BO<N, MODE>::v;
     XYArgs a;
     a.s = s;
@@ -1098,7 +1113,7 @@ class Chain : public ChainBase {
     auto smem_for = [&](int b) {
       size_t m = (size_t)b * cb_ncol_ + (size_t)b * s.nrow_max * NP;
       if (MODE == XY_PASS2) m += (size_t)N * N;
-      if (MODE == XY_PASS1_DENS) m += (size_t)(128 / N) * N * N;   // per-slot density planes
+      if (MODE == XY_PASS1_DENS) m += (size_t)slots * N * N;   // per-slot density planes
       m *= sizeof(cplx<T>);
       if (MODE == XY_PASS1 || MODE == XY_PASS1_DENS) m += (size_t)N * N * sizeof(T);
       return m;
@@ -1108,7 +1123,7 @@ class Chain : public ChainBase {
     // allow (N = 48: 116 KB for 8 orbitals left one 4-warp CTA per SM)
     if (xy_occ_reg_[MODE] == 0) {
       int occ = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_xy<T, N, MODE>, 128, 0) != cudaSuccess || occ < 1) {
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, 0) != cudaSuccess || occ < 1) {
         cudaGetLastError();
         occ = 1;
       }
@@ -1119,10 +1134,10 @@ class Chain : public ChainBase {
     const size_t smem = smem_for(B);
     a.bo = B;
     int rc;
-    if ((rc = set_smem(k_xy<T, N, MODE>, smem, err))) return rc;
-    const int ng = groups_for_kernel(k_xy<T, N, MODE>, smem, norb, xy_groups_[MODE]);
+    if ((rc = set_smem(kernel, smem, err))) return rc;
+    const int ng = groups_for_kernel(kernel, smem, norb, xy_groups_[MODE], threads);
     a.per_group = (norb + ng - 1) / ng;
-    k_xy<T, N, MODE><<<dim3(N, ng), 128, smem, st_>>>(a, cbuf_, vloc_, vpr_, ur_, nprt_, ur_);
+    kernel<<<dim3(N, ng), threads, smem, st_>>>(a, cbuf_, vloc_, vpr_, ur_, nprt_, ur_);
     if (MODE == XY_PASS1_DENS) last_ng_ = ng;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) { err = std::string("k_xy: ") + cudaGetErrorString(e); return LL_ECUDA; }
@@ -1329,6 +1344,7 @@ class Chain : public ChainBase {
   cudaGraphExec_t graph_[2] = {nullptr, nullptr};   // one captured step per parity of j
   bool split_ = false;      // per-k work split over chunks of plane waves (split.cuh)
   int xy_occ_reg_[4] = {0, 0, 0, 0};   // CTAs per SM the plane pass's registers allow, per mode
+  int xy_pair_ = -1;                   // plane-pass line transforms over lane pairs: 1 on, 0 off, -1 N = 48 only
   bool tc_op_ = false, tc_u_ = false, tc_u2_ = false;   // split-path dot blocks on the tensor cores
   bool tc_ap_ = false;                                    // split-path projections applied on the tensor cores
   int tc_nb_op_ = 32, tc_nb_u_ = 32, tc_nb_ap_ = 32;      // N of those MMAs (Bop rows, padded to 32)

@@ -140,4 +140,43 @@ __device__ __forceinline__ void fft_line(cplx<T> (&a)[N]) {
   }
 }
 
+// A 2H-point FFT split over a lane pair (lanes l and l ^ 1 of a warp, h = l & 1), each lane
+// holding H points, with one radix-2 step exchanged through warp shuffles (mask: the pair).
+//   fft_pair_dit: in  a[m] = x[2m + h]    out a[k] = X[H h + k]   (decimation in time)
+//   fft_pair_dif: in  a[j] = x[H h + j]   out a[m] = X[2m + h]    (decimation in frequency)
+// The transform is fft_line<T, 2H, SIGN>'s, with half the registers per lane.
+template <typename T>
+__device__ __forceinline__ cplx<T> shfl_pair(cplx<T> v, unsigned mask) {
+  return mk(__shfl_xor_sync(mask, v.x, 1), __shfl_xor_sync(mask, v.y, 1));
+}
+
+template <typename T, int H, int SIGN>
+__device__ __forceinline__ void fft_pair_dit(cplx<T> (&a)[H], int h, unsigned mask) {
+  fft_line<T, H, SIGN>(a);               // Y_h[k] = sum_m x[2m + h] W_H^(mk)
+  if (h) {
+#pragma unroll
+    for (int k = 1; k < H; ++k) a[k] = cmul(a[k], twiddle<T, 2 * H, SIGN>(k));   // W_2H^k Y_1[k]
+  }
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    const cplx<T> o = shfl_pair(a[k], mask);
+    a[k] = h ? o - a[k] : a[k] + o;        // X[k] = Y0 + W Y1,  X[k + H] = Y0 - W Y1
+  }
+}
+
+template <typename T, int H, int SIGN>
+__device__ __forceinline__ void fft_pair_dif(cplx<T> (&a)[H], int h, unsigned mask) {
+#pragma unroll
+  for (int j = 0; j < H; ++j) {
+    const cplx<T> o = shfl_pair(a[j], mask);
+    if (h) {
+      a[j] = o - a[j];                     // x[j] - x[j + H]
+      if (j) a[j] = cmul(a[j], twiddle<T, 2 * H, SIGN>(j));
+    } else {
+      a[j] = a[j] + o;                     // x[j] + x[j + H]
+    }
+  }
+  fft_line<T, H, SIGN>(a);               // even (h = 0) or odd (h = 1) outputs
+}
+
 }  // namespace ll

@@ -369,3 +369,16 @@ def test_graph_replayed_steps_match_eager(lib, small, precision):
     st.synchronize()
     for a, b in zip(eager, got):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+def test_lane_pair_plane_pass_kb(lib, kb, precision, tol, monkeypatch):
+    """The plane pass with every line transform split over a lane pair (LL_XY_PAIR=1; the
+    default at N = 48 only) on the KB workload at N = 32: both operator halves against the
+    oracle."""
+    monkeypatch.setenv("LL_XY_PAIR", "1")
+    sys = System(kb)
+    ch = chain_from_bundle(kb, precision=precision, max_steps=4)
+    x = _rand(sys, 15)
+    for upper in (False, True):
+        assert rel_batch(ch.apply(x, upper), sys.apply_op(x, upper)) < tol
