@@ -7,8 +7,11 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
+#include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -561,6 +564,9 @@ class Chain : public ChainBase {
     }
 
 
+    // the plane pass's kernel variant and batch per mode, timed on this system (cached per shape)
+    if ((rc = tune_plane_pass(err))) return rc;
+
     // start of the recursion
     if (flavour_ == LL_FLAVOUR_PH) {
       LL_CK(cudaMemcpyAsync(R(), y_, vq * sizeof(cplx<T>), cudaMemcpyDeviceToDevice, st_));
@@ -1084,19 +1090,20 @@ class Chain : public ChainBase {
   }
   template <int N, int MODE>
   int xy_nm(const SphereDev& s, int norb, int o_off, int dens_vec, std::string& err) {
+    const XyChoice c = xy_choice_[MODE];
     if constexpr (N == 24 || N == 32 || N == 36 || N == 48) {
       // every line transform split over a lane pair (xypair.cuh): half the registers per thread.
-      // Measured on GB300: faster at N = 48 (16-atom cell, pass 2 0.67 -> 0.55 ms per step),
-      // slower at N = 32 (KB workload, pass 1 0.26 -> 0.29 ms), so the default is N = 48 only
-      if (xy_pair_ == 1 || (xy_pair_ < 0 && N == 48))
-        return xy_launch<N, MODE>(k_xyp<T, N, MODE>, 4 * N, 2, s, norb, o_off, dens_vec, err);
+      // Untuned default: N = 48 only (measured on GB300: faster at N = 48, 16-atom cell pass 2
+      // 0.67 -> 0.55 ms per step; slower at N = 32, KB workload pass 1 0.26 -> 0.29 ms)
+      const bool pair = xy_pair_ >= 0 ? xy_pair_ == 1 : (c.var >= 0 ? c.var == 1 : N == 48);
+      if (pair) return xy_launch<N, MODE>(k_xyp<T, N, MODE>, 4 * N, 2, c.bo, s, norb, o_off, dens_vec, err);
     }
-    return xy_launch<N, MODE>(k_xy<T, N, MODE>, 128, 128 / N, s, norb, o_off, dens_vec, err);
+    return xy_launch<N, MODE>(k_xy<T, N, MODE>, 128, 128 / N, c.bo, s, norb, o_off, dens_vec, err);
   }
   template <int N, int MODE, typename K>
-  int xy_launch(K kernel, int threads, int slots, const SphereDev& s, int norb, int o_off, int dens_vec,
+  int xy_launch(K kernel, int threads, int slots, int bo, const SphereDev& s, int norb, int o_off, int dens_vec,
                 std::string& err) {
-    int B = BO<N, MODE>::v;
+    int B = bo > 0 ? bo : BO<N, MODE>::v;
     XYArgs a;
     a.s = s;
     a.nbnd = nbnd_;
@@ -1130,7 +1137,11 @@ class Chain : public ChainBase {
       xy_occ_reg_[MODE] = std::min(occ, 8);
     }
     const size_t per_sm = 227 * 1024 - 2048 * (size_t)xy_occ_reg_[MODE];
-    while (B > 1 && (smem_for(B) > 200 * 1024 || smem_for(B) * xy_occ_reg_[MODE] > per_sm)) --B;
+    if (bo > 0) {   // a tuned batch: only the shared-memory limit applies
+      while (B > 1 && smem_for(B) > 200 * 1024) --B;
+    } else {
+      while (B > 1 && (smem_for(B) > 200 * 1024 || smem_for(B) * xy_occ_reg_[MODE] > per_sm)) --B;
+    }
     const size_t smem = smem_for(B);
     a.bo = B;
     int rc;
@@ -1143,6 +1154,96 @@ class Chain : public ChainBase {
     if (e != cudaSuccess) { err = std::string("k_xy: ") + cudaGetErrorString(e); return LL_ECUDA; }
     return LL_OK;
   }
+  // ---- autotuner of the plane pass ----------------------------------------------------
+  // For each mode of the operator's plane pass (pass 1, pass 1 with the density, pass 2) the
+  // kernel variant (one thread or a lane pair per line transform) and the orbital batch are
+  // chosen by timing whole operator applications on a scratch copy of the starting vector
+  // (CUDA events on the chain's stream; one mode at a time, the others at their current
+  // choice).  The choice is kept per system shape and device for the whole process, so every
+  // chain of one shape in a process uses the same launches (their results agree bit for bit
+  // whatever else runs); LL_TUNE=0 keeps the untuned defaults.
+  int tune_plane_pass(std::string& err) {
+    const char* te = getenv("LL_TUNE");
+    if (te && te[0] == '0' && te[1] == 0) return LL_OK;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    char key[256];
+    snprintf(key, sizeof(key), "%d/%zu/%d/%d/%d/%d/%d/%d/%d/%d/%d/%d", dev, sizeof(T), N_, nks_, nbnd_, hq_.npw_pad,
+             cb_ncol_, hq_.nrow_max, nproj_, (int)split_, xy_pair_, nsm_);
+    {
+      std::lock_guard<std::mutex> lock(tune_mutex());
+      auto it = tune_cache().find(key);
+      if (it != tune_cache().end()) {
+        for (int m = 0; m < 3; ++m) xy_choice_[m] = {it->second[2 * m], it->second[2 * m + 1]};
+        for (int m = 0; m < 3; ++m) xy_occ_reg_[m] = xy_groups_[m] = 0;
+        return LL_OK;
+      }
+    }
+    const long vq = (long)nks_ * nbnd_ * hq_.npw_pad;
+    int rc;
+    if (!scratch_ && (rc = alloc(&scratch_, 2 * vq))) return rc;
+    cudaEvent_t ea, eb;
+    LL_CK(cudaEventCreate(&ea));
+    LL_CK(cudaEventCreate(&eb));
+    auto run = [&](int dens, float* ms) -> int {
+      LL_CK(cudaMemcpyAsync(scratch_, y_, vq * sizeof(cplx<T>), cudaMemcpyDeviceToDevice, st_));
+      LL_CK(cudaEventRecord(ea, st_));
+      int r = op(1, scratch_, scratch_ + vq, dens, err);
+      if (r) return r;
+      LL_CK(cudaEventRecord(eb, st_));
+      LL_CK(cudaEventSynchronize(eb));
+      LL_CK(cudaEventElapsedTime(ms, ea, eb));
+      return LL_OK;
+    };
+    float ms = 0.f;
+    const bool can_pair = (N_ == 24 || N_ == 32 || N_ == 36 || N_ == 48) && xy_pair_ < 0;
+    rc = run(approx_ == LL_APPROX_IPA ? -1 : 0, &ms);   // warm-up: lazy module loads, attributes
+    const int modes[3] = {XY_PASS1, XY_PASS1_DENS, XY_PASS2};
+    for (int mi = 0; mi < 3 && rc == LL_OK; ++mi) {
+      const int mode = modes[mi];
+      if (mode != XY_PASS1 && approx_ == LL_APPROX_IPA) break;   // no density without K
+      const int dens = mode == XY_PASS1 ? -1 : 0;
+      const int bdef = (mode == XY_PASS1) ? 384 / N_ : 256 / N_;
+      std::vector<XyChoice> cand;
+      for (int var = 0; var <= (can_pair ? 1 : 0); ++var) {
+        cand.push_back({var, 0});                             // the occupancy-derived batch
+        for (int b : {bdef, std::max(1, bdef / 2)}) cand.push_back({var, b});
+      }
+      float best = 1e30f;
+      XyChoice pick = xy_choice_[mode];
+      for (const XyChoice& c : cand) {
+        xy_choice_[mode] = c;
+        xy_occ_reg_[mode] = xy_groups_[mode] = 0;
+        if ((rc = run(dens, &ms)) != LL_OK) break;
+        if (ms < best) { best = ms; pick = c; }
+      }
+      xy_choice_[mode] = pick;
+      xy_occ_reg_[mode] = xy_groups_[mode] = 0;
+    }
+    cudaEventDestroy(ea);
+    cudaEventDestroy(eb);
+    if (rc != LL_OK) return rc;
+    std::lock_guard<std::mutex> lock(tune_mutex());
+    auto it = tune_cache().find(key);
+    if (it != tune_cache().end()) {   // another chain of this shape tuned meanwhile: use its choice
+      for (int m = 0; m < 3; ++m) xy_choice_[m] = {it->second[2 * m], it->second[2 * m + 1]};
+      for (int m = 0; m < 3; ++m) xy_occ_reg_[m] = xy_groups_[m] = 0;
+    } else {
+      std::array<int, 6> v;
+      for (int m = 0; m < 3; ++m) v[2 * m] = xy_choice_[m].var, v[2 * m + 1] = xy_choice_[m].bo;
+      tune_cache()[key] = v;
+    }
+    return LL_OK;
+  }
+  static std::mutex& tune_mutex() {
+    static std::mutex m;
+    return m;
+  }
+  static std::map<std::string, std::array<int, 6>>& tune_cache() {
+    static std::map<std::string, std::array<int, 6>> c;
+    return c;
+  }
+
   // mode 0: operator pass 1 (with the density when dens_vec >= 0); 1: pass 2; 2: store x(r)
   template <int N>
   int xy_n(const SphereDev& s, int norb, int o_off, int dens_vec, int mode, std::string& err) {
@@ -1344,7 +1445,9 @@ class Chain : public ChainBase {
   cudaGraphExec_t graph_[2] = {nullptr, nullptr};   // one captured step per parity of j
   bool split_ = false;      // per-k work split over chunks of plane waves (split.cuh)
   int xy_occ_reg_[4] = {0, 0, 0, 0};   // CTAs per SM the plane pass's registers allow, per mode
-  int xy_pair_ = -1;                   // plane-pass line transforms over lane pairs: 1 on, 0 off, -1 N = 48 only
+  int xy_pair_ = -1;                   // LL_XY_PAIR: 1 lane pairs for every even N, 0 never, -1 not forced
+  struct XyChoice { int var; int bo; };    // plane-pass kernel (0 k_xy, 1 k_xyp) and orbital batch
+  XyChoice xy_choice_[4] = {{-1, 0}, {-1, 0}, {-1, 0}, {-1, 0}};   // per mode; -1 / 0: the untuned default
   bool tc_op_ = false, tc_u_ = false, tc_u2_ = false;   // split-path dot blocks on the tensor cores
   bool tc_ap_ = false;                                    // split-path projections applied on the tensor cores
   int tc_nb_op_ = 32, tc_nb_u_ = 32, tc_nb_ap_ = 32;      // N of those MMAs (Bop rows, padded to 32)

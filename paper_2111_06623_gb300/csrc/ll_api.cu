@@ -487,7 +487,9 @@ int ll_footprint(const ll_system_desc* d, size_t* bytes) {
     cudaGetLastError();
   }
   const size_t ngroups = (4 * (size_t)nsm + d->nfft - 1) / d->nfft;
-  size_t b = elem * (vq * (3 * nvec + nvec + 2) + orb * pk + orb * n3 + cb + ngroups * n3 + 3 * n3 +
+  // vectors: 3 nvec Lanczos vectors, nvec partial copies, y, U_{k+Q}, and the 2-vector scratch
+  // of the plane-pass tuner and ll_apply
+  size_t b = elem * (vq * (3 * nvec + nvec + 2 + 2) + orb * pk + orb * n3 + cb + ngroups * n3 + 3 * n3 +
                      (size_t)d->nks * d->nproj * pq);
   // Lanczos partials: up to max(bands, plane-wave chunks) per k and step (band groups or the
   // split path), and the split path's chunk partials and coefficient blocks
