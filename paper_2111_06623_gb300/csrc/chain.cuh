@@ -106,7 +106,7 @@ static inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
 // Every floating-point input of a system finite: a NaN or an infinity would pass into every
 // coefficient of the chain without tripping the breakdown checks.  The array pointers and the
 // sphere sizes npw_k, npw_kq must already be valid.
-struct FiniteCheck { const double* p; long len; const char* what; bool device; };
+struct FiniteCheck { const double* p; long len; const char* what; bool device; bool large; };
 
 // The floating-point input arrays of a descriptor, with where they live.
 static inline std::vector<FiniteCheck> input_arrays(const ll_system_desc* d) {
@@ -114,16 +114,18 @@ static inline std::vector<FiniteCheck> input_arrays(const ll_system_desc* d) {
   for (int k = 0; k < d->nks; ++k) sk += d->npw_k[k], sq += d->npw_kq[k];
   const long n3 = (long)d->nfft * d->nfft * d->nfft, nb = d->nbnd, np = d->nproj;
   const bool dv = d->where == LL_WHERE_DEVICE;
-  return {{&d->lattice[0][0], 9, "lattice", false},  {d->q_cart, 3, "q_cart", false},
-          {d->kcart, 3L * d->nks, "kcart", false},    {d->u_k, 2 * nb * sk, "u_k", dv},
-          {d->u_kq, 2 * nb * sq, "u_kq", dv},         {d->eps_k, (long)d->nks * nb, "eps_k", false},
-          {d->vloc_r, n3, "vloc_r", dv},              {d->rho_r, n3, "rho_r", dv},
-          {d->beta_kq, 2 * np * sq, "beta_kq", dv},  {d->dij, np, "dij", false}};
+  return {{&d->lattice[0][0], 9, "lattice", false, false},  {d->q_cart, 3, "q_cart", false, false},
+          {d->kcart, 3L * d->nks, "kcart", false, false},    {d->u_k, 2 * nb * sk, "u_k", dv, true},
+          {d->u_kq, 2 * nb * sq, "u_kq", dv, true},          {d->eps_k, (long)d->nks * nb, "eps_k", false, false},
+          {d->vloc_r, n3, "vloc_r", dv, true},               {d->rho_r, n3, "rho_r", dv, true},
+          {d->beta_kq, 2 * np * sq, "beta_kq", dv, true},   {d->dij, np, "dij", false, false}};
 }
 
-static inline bool inputs_finite(const ll_system_desc* d, std::string& err) {
+// large_on_host: check the large arrays here too (the request loop refuses a malformed job at
+// submit); ll_create checks them on the device after they are uploaded.
+static inline bool inputs_finite(const ll_system_desc* d, std::string& err, bool large_on_host = true) {
   for (const auto& a : input_arrays(d))
-    if (!a.device)
+    if (!a.device && (large_on_host || !a.large))
       for (long i = 0; i < a.len; ++i)
       if (!std::isfinite(a.p[i])) {
         err = std::string("non-finite value in ") + a.what + " at index " + std::to_string(i);
@@ -241,9 +243,15 @@ template <int N, int MODE> struct BO {
 // side, the k-point and band counts, the spheres of k and the u_k coefficients (host arrays).
 static inline uint64_t ground_state_hash(const ll_system_desc* d) {
   uint64_t h = 1469598103934665603ull;
-  auto feed = [&](const void* p, size_t n) {
+  auto feed = [&](const void* p, size_t n) {   // FNV-1a over 8-byte words, then the tail bytes
     const unsigned char* c = static_cast<const unsigned char*>(p);
-    for (size_t i = 0; i < n; ++i) h = (h ^ c[i]) * 1099511628211ull;
+    size_t i = 0;
+    for (; i + 8 <= n; i += 8) {
+      uint64_t wv;
+      memcpy(&wv, c + i, 8);
+      h = (h ^ wv) * 1099511628211ull;
+    }
+    for (; i < n; ++i) h = (h ^ c[i]) * 1099511628211ull;
   };
   feed(&d->precision, sizeof(int));
   feed(&d->nfft, sizeof(int));
@@ -302,7 +310,7 @@ class Chain : public ChainBase {
     if (!build_sphere(nks_, d->npw_kq, d->miller_kq, n, hq_, err)) return LL_EINVAL;
     for (int k = 0; k < nks_; ++k)
       if (d->npw_kq[k] < nbnd_ + 1) { err = "sphere smaller than the occupied manifold"; return LL_EINVAL; }
-    if (!inputs_finite(d, err)) return LL_EINVAL;
+    if (!inputs_finite(d, err, false)) return LL_EINVAL;
     if (d->where != LL_WHERE_HOST && d->where != LL_WHERE_DEVICE) { err = "bad where"; return LL_EINVAL; }
     const bool dev_in = d->where == LL_WHERE_DEVICE;
     // k-point weights (stars of the small group of Q) and the group on the grid (Sec. 2.6)
@@ -331,29 +339,54 @@ class Chain : public ChainBase {
       }
       if (!has_identity) { err = "the symmetry operations lack the identity"; return LL_EINVAL; }
     }
-    if (dev_in) {   // device-resident arrays: device pointers, and finite (checked on the device)
-      unsigned long long* first = nullptr;
+    // The large arrays on the device: the caller's (where = LL_WHERE_DEVICE) or one staging copy
+    // of the host arrays; finiteness is checked and the padded tables are built there.
+    const long n3l = (long)n * n * n;
+    struct Large { const double* p; long len; const char* what; };
+    Large large[5] = {{d->u_k, 2L * nbnd_ * hk_.off[nks_], "u_k"},
+                      {d->u_kq, 2L * nbnd_ * hq_.off[nks_], "u_kq"},
+                      {d->vloc_r, n3l, "vloc_r"},
+                      {d->rho_r, n3l, "rho_r"},
+                      {d->beta_kq, 2L * nproj_ * hq_.off[nks_], "beta_kq"}};
+    double* stage = nullptr;
+    {
       int rc0;
-      if ((rc0 = alloc(&first, 1))) return rc0;
-      for (const auto& a : input_arrays(d)) {
-        if (!a.device || a.len == 0) continue;
-        cudaPointerAttributes at;
-        if (cudaPointerGetAttributes(&at, a.p) != cudaSuccess ||
-            (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
-          cudaGetLastError();
-          err = std::string(a.what) + " is not a device pointer (where = LL_WHERE_DEVICE)";
-          return LL_EINVAL;
-        }
-        unsigned long long h = 0;
-        LL_CK(cudaMemsetAsync(first, 0xFF, sizeof(h), st_));
-        k_first_nonfinite<<<152, 256, 0, st_>>>(a.p, a.len, first);
-        LL_CK(cudaMemcpyAsync(&h, first, sizeof(h), cudaMemcpyDeviceToHost, st_));
-        LL_CK(cudaStreamSynchronize(st_));
-        if (h != ~0ull) {
-          err = std::string("non-finite value in ") + a.what + " at index " + std::to_string(h);
-          return LL_EINVAL;
+      if (!dev_in) {
+        long tot = 0;
+        for (const Large& a : large) tot += a.len;
+        if ((rc0 = alloc(&stage, tot))) return rc0;
+        long off = 0;
+        for (Large& a : large) {
+          if (a.len) LL_CK(cudaMemcpyAsync(stage + off, a.p, a.len * sizeof(double), cudaMemcpyHostToDevice, st_));
+          a.p = stage + off;
+          off += a.len;
         }
       }
+      unsigned long long* first = nullptr;
+      if ((rc0 = alloc(&first, 5))) return rc0;
+      LL_CK(cudaMemsetAsync(first, 0xFF, 5 * sizeof(unsigned long long), st_));
+      for (int i = 0; i < 5; ++i) {
+        const Large& a = large[i];
+        if (a.len == 0) continue;
+        if (dev_in) {
+          cudaPointerAttributes at;
+          if (cudaPointerGetAttributes(&at, a.p) != cudaSuccess ||
+              (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
+            cudaGetLastError();
+            err = std::string(a.what) + " is not a device pointer (where = LL_WHERE_DEVICE)";
+            return LL_EINVAL;
+          }
+        }
+        k_first_nonfinite<<<152, 256, 0, st_>>>(a.p, a.len, first + i);
+      }
+      unsigned long long h[5];
+      LL_CK(cudaMemcpyAsync(h, first, sizeof(h), cudaMemcpyDeviceToHost, st_));
+      LL_CK(cudaStreamSynchronize(st_));
+      for (int i = 0; i < 5; ++i)
+        if (large[i].len && h[i] != ~0ull) {
+          err = std::string("non-finite value in ") + large[i].what + " at index " + std::to_string(h[i]);
+          return LL_EINVAL;
+        }
       release(first);
     }
     gs_hash_ = dev_in ? 0 : ground_state_hash(d);
@@ -398,25 +431,8 @@ class Chain : public ChainBase {
         kin[(size_t)k * pq + i] = (T)(0.5 * (g[0] * g[0] + g[1] * g[1] + g[2] * g[2]));
       }
     }
-    // padded orbital tables and grids transposed to [j3][j2][j1]: on the host for host inputs;
-    // from device inputs by the k_pad_rows / k_grids_in kernels below
-    std::vector<cplx<T>> uk, ukq, bkq(1);
-    std::vector<T> vl;
-    std::vector<double> rh;
-    if (!dev_in) {
-      uk = pad_batch(d->u_k, hk_, nbnd_, &kscale_);
-      ukq = pad_batch(d->u_kq, hq_, nbnd_);
-      if (nproj_) bkq = pad_batch(d->beta_kq, hq_, nproj_);
-      vl.resize(n3);
-      rh.resize(n3);
-      for (int j1 = 0; j1 < n; ++j1)
-        for (int j2 = 0; j2 < n; ++j2)
-          for (int j3 = 0; j3 < n; ++j3) {
-            const long src = ((long)j1 * n + j2) * n + j3, dst = ((long)j3 * n + j2) * n + j1;
-            vl[dst] = (T)d->vloc_r[src];
-            rh[dst] = d->rho_r[src];
-          }
-    }
+    // padded orbital tables and grids transposed to [j3][j2][j1]: built on the device from the
+    // large arrays (the caller's device arrays or their staging copy) by k_pad_rows / k_grids_in
     const long bkq_len = nproj_ ? (long)nks_ * nproj_ * pq : 1;
 
     int rc;
@@ -493,28 +509,23 @@ class Chain : public ChainBase {
     (void)err;
     LL_CK(cudaMemcpyAsync(whart_, wh.data(), n3 * sizeof(T), cudaMemcpyHostToDevice, st_));
     LL_CK(cudaMemcpyAsync(kin_, kin.data(), kin.size() * sizeof(T), cudaMemcpyHostToDevice, st_));
-    if (!dev_in) {
-      LL_CK(cudaMemcpyAsync(uk_, uk.data(), uk.size() * sizeof(cplx<T>), cudaMemcpyHostToDevice, st_));
-      LL_CK(cudaMemcpyAsync(ukq_, ukq.data(), ukq.size() * sizeof(cplx<T>), cudaMemcpyHostToDevice, st_));
-      LL_CK(cudaMemcpyAsync(bkq_, bkq.data(), bkq.size() * sizeof(cplx<T>), cudaMemcpyHostToDevice, st_));
-      LL_CK(cudaMemcpyAsync(vloc_, vl.data(), n3 * sizeof(T), cudaMemcpyHostToDevice, st_));
-      LL_CK(cudaMemcpyAsync(rho_, rh.data(), n3 * sizeof(double), cudaMemcpyHostToDevice, st_));
-    } else {
+    {
       int *offk = nullptr, *offq = nullptr;
       double* ksc = nullptr;
       if ((rc = alloc(&offk, nks_ + 1)) || (rc = alloc(&offq, nks_ + 1)) || (rc = alloc(&ksc, nks_))) return rc;
       LL_CK(cudaMemcpyAsync(offk, hk_.off.data(), (nks_ + 1) * sizeof(int), cudaMemcpyHostToDevice, st_));
       LL_CK(cudaMemcpyAsync(offq, hq_.off.data(), (nks_ + 1) * sizeof(int), cudaMemcpyHostToDevice, st_));
       LL_CK(cudaMemcpyAsync(ksc, kscale_.data(), nks_ * sizeof(double), cudaMemcpyHostToDevice, st_));
-      k_pad_rows<T><<<dim3(nks_, nbnd_), 256, 0, st_>>>(d->u_k, offk, dk_.npw, nbnd_, hk_.npw_pad, ksc, uk_);
-      k_pad_rows<T><<<dim3(nks_, nbnd_), 256, 0, st_>>>(d->u_kq, offq, dq_.npw, nbnd_, pq, nullptr, ukq_);
-      if (nproj_) k_pad_rows<T><<<dim3(nks_, nproj_), 256, 0, st_>>>(d->beta_kq, offq, dq_.npw, nproj_, pq, nullptr, bkq_);
-      k_grids_in<T><<<256, 256, 0, st_>>>(n, d->vloc_r, d->rho_r, vloc_, rho_);
+      k_pad_rows<T><<<dim3(nks_, nbnd_), 256, 0, st_>>>(large[0].p, offk, dk_.npw, nbnd_, hk_.npw_pad, ksc, uk_);
+      k_pad_rows<T><<<dim3(nks_, nbnd_), 256, 0, st_>>>(large[1].p, offq, dq_.npw, nbnd_, pq, nullptr, ukq_);
+      if (nproj_) k_pad_rows<T><<<dim3(nks_, nproj_), 256, 0, st_>>>(large[4].p, offq, dq_.npw, nproj_, pq, nullptr, bkq_);
+      k_grids_in<T><<<256, 256, 0, st_>>>(n, large[2].p, large[3].p, vloc_, rho_);
       LL_CK(cudaGetLastError());
       LL_CK(cudaStreamSynchronize(st_));   // the caller may reuse its arrays once ll_create returns
       release(offk);
       release(offq);
       release(ksc);
+      release(stage);
     }
     LL_CK(cudaMemcpyAsync(eps_, d->eps_k, sizeof(double) * nks_ * nbnd_, cudaMemcpyHostToDevice, st_));
     if (nproj_) LL_CK(cudaMemcpyAsync(dij_, d->dij, sizeof(double) * nproj_, cudaMemcpyHostToDevice, st_));
