@@ -42,7 +42,7 @@ class KSplit:
         return self.sys.project_c(x, self.ks)
 
     def inner(self, a, b) -> complex:
-        local = sum(self.sys.kw[k] * np.vdot(ak, bk) for k, ak, bk in zip(self.ks, a, b))
+        local = self.sys.inner_part(a, b, self.ks)
         tot = self.allreduce(np.array([complex(local).real, complex(local).imag]))
         return complex(tot[0], tot[1]) / self.sys.nfull
 

@@ -27,6 +27,26 @@ mesh), every sum over the mesh becomes a weighted sum over the wedge,
 and the response density is the average of n~ over the group, n'(r) = (1/|G_Q|) sum_S
 n~(S r) (the terms of the k-points of a star are the rotated terms of its representative).
 Without symmetry m_k = 1 and G_Q = {E}: the plain sums above.
+
+Metals (Sec. 2.6: the projector on empty states redefined, fractional occupations as weights
+in the band sums; the smearing approach of the static theory the paper cites).  Reading:
+with occupations f_{vk} and f_{m,k+Q} in [0, 1] (the bundle's, from Gaussian smearing), the
+independent-particle response is the transition sum over (f_v - f_m) |M|^2/(w - Delta_mv);
+each pair of levels is given to the one direction with a positive transition energy (a sharp
+step theta(eps_m - eps_v) in the projector of the static theory), which leaves every kept
+transition a weight w_vm = f_v - f_m > 0 and a positive energy, so the pseudo-Hermitian
+recursion's metric stays positive.  Per band v of k, with c_mv = max(1 - f_m/f_v, 0)
+(0 for f_v = 0; below C_MIN counted as 0) for the bands m of k+Q:
+    P_{c,v} x = x - sum_m (1 - c_mv) |u_{m,k+Q}><u_{m,k+Q}|x>           (the redefined P_c)
+    K x = { P_{c,v} v'_HXC[n'](r) u_{vk}(r) },  y = { P_{c,v} u_{vk} } (perturbation as above)
+    n'(r) = 4 (1/N_k) sum_k m_k sum_v f_{vk} u*_{vk}(r) x_{vk}(r)        (band-sum weights)
+    D x = { P'_v (H_{k+Q} - eps_{vk}) x_{vk} },  P'_v: removes the m with c_mv = 0
+and the scalar product is the metric that makes D and K Hermitian,
+    (a, b) = (1/N_k) sum_k m_k sum_v f_{vk} [ a_v^H b_v + sum_{m: c_mv > 0} (1/c_mv - 1)
+             conj(<u_m|a_v>) <u_m|b_v> ].
+Every new Lanczos vector is projected with P'_v.  Fully occupied bands (f = 1 everywhere)
+give c = 0 and f_v = 1: the insulator's P_c, D, K and product.  The response is for Q + G
+!= 0 only, so the Fermi level does not move (no shift term).
 """
 from __future__ import annotations
 
@@ -34,6 +54,21 @@ import numpy as np
 import scipy.fft as sfft
 
 from . import basis, xc
+
+# weights c_mv of the metallic projector below this count as 0 (the transition is dropped)
+C_MIN = 1e-6
+
+
+def metal_weights(f_v: np.ndarray, f_m: np.ndarray) -> np.ndarray:
+    """c[m, v] = max(1 - f_m/f_v, 0) for f_v > 0, else 0; entries below C_MIN set to 0."""
+    f_v = np.asarray(f_v, dtype=np.float64)
+    f_m = np.asarray(f_m, dtype=np.float64)
+    c = np.zeros((len(f_m), len(f_v)))
+    for v in range(len(f_v)):
+        if f_v[v] > 0.0:
+            c[:, v] = np.maximum(1.0 - f_m / f_v[v], 0.0)
+    c[c < C_MIN] = 0.0
+    return c
 
 
 class System:
@@ -84,13 +119,32 @@ class System:
         # transformed when first used (a rank of the k-point split touches only its own block)
         self.ur = _LazyGrids(self.uk, self.mk, n)
         self.map_k_kq = [basis.intersection_map(self.mk[k], self.mkq[k]) for k in range(self.nks)]
+        self.metal = getattr(bundle, "occ_k", None) is not None
+        if self.metal:
+            self.f = np.asarray(bundle.occ_k, dtype=np.float64)
+            fq = np.asarray(bundle.occ_kq, dtype=np.float64)
+            self.c = [metal_weights(self.f[k], fq[k]) for k in range(self.nks)]
 
     # ----- batches -------------------------------------------------------------------
     def zeros(self):
         return [np.zeros((self.nbnd, len(m)), dtype=np.complex128) for m in self.mkq]
 
     def inner(self, a, b) -> complex:
-        return sum(w * np.vdot(ak, bk) for w, ak, bk in zip(self.kw, a, b)) / self.nfull
+        return self.inner_part(a, b) / self.nfull
+
+    def inner_part(self, a, b, ks=None) -> complex:
+        """N_k (a, b) restricted to the k-points ks (default all): the weighted sum over k."""
+        ks = self._ks(a, ks)
+        if not self.metal:
+            return sum(self.kw[k] * np.vdot(ak, bk) for k, ak, bk in zip(ks, a, b))
+        tot = 0.0
+        for k, ak, bk in zip(ks, a, b):
+            u, c = self.ukq[k], self.c[k]
+            sa, sb = u.conj() @ ak.T, u.conj() @ bk.T             # <u_m|a_v>, (nbnd_m, nbnd_v)
+            corr = np.where(c > 0, 1.0 / np.where(c > 0, c, 1.0) - 1.0, 0.0)
+            per_v = np.einsum("vg,vg->v", ak.conj(), bk) + np.einsum("mv,mv,mv->v", corr, sa.conj(), sb)
+            tot += self.kw[k] * np.dot(self.f[k], per_v)
+        return tot
 
     # Every per-k method takes the k index of each entry of its batch in `ks` (default: all
     # k-points in order), so that a rank holding a block of k-points can apply it to its block.
@@ -98,11 +152,26 @@ class System:
         return range(len(x)) if ks is None else ks
 
     def project_c(self, x, ks=None):
-        """P_c^{k+Q} x = x - U (U^H x) with U the occupied states at k+Q (Eq. 16)."""
+        """P_c^{k+Q} x = x - U (U^H x) with U the occupied states at k+Q (Eq. 16).  A metal:
+        P'_v, which removes only the states m with c_mv = 0."""
         out = []
         for k, xk in zip(self._ks(x, ks), x):
             u = self.ukq[k]
-            out.append(xk - (u.T @ (u.conj() @ xk.T)).T)
+            s = u.conj() @ xk.T
+            if self.metal:
+                s = s * (self.c[k] == 0.0)
+            out.append(xk - (u.T @ s).T)
+        return out
+
+    def project_weighted(self, x, ks=None):
+        """The projector of K and y: P_c^{k+Q} (an insulator), P_{c,v} (a metal)."""
+        if not self.metal:
+            return self.project_c(x, ks)
+        out = []
+        for k, xk in zip(self._ks(x, ks), x):
+            u = self.ukq[k]
+            s = (u.conj() @ xk.T) * (1.0 - self.c[k])
+            out.append(xk - (u.T @ s).T)
         return out
 
     def starting_vector(self):
@@ -114,7 +183,7 @@ class System:
             hit = mp >= 0
             yk[:, hit] = self.uk[k][:, mp[hit]]
             y.append(yk)
-        return self.project_c(y)
+        return self.project_weighted(y)
 
     # ----- operators -----------------------------------------------------------------
     def apply_h_minus_eps(self, x, ks=None):
@@ -137,13 +206,17 @@ class System:
         return self.project_c(self.apply_h_minus_eps(x, ks), ks)
 
     def response_density(self, x, ks=None):
-        """n~(r) = 4 (1/N_k) sum_{vk} m_k u*_{vk}(r) x_{vk}(r), u = psi/sqrt(Omega); with `ks`,
-        the part of the sum over those k-points.  (Without symmetry, n' itself.)"""
+        """n~(r) = 4 (1/N_k) sum_{vk} m_k u*_{vk}(r) x_{vk}(r), u = psi/sqrt(Omega) (times f_vk for
+        a metal); with `ks`, the part of the sum over those k-points.  (Without symmetry, n'
+        itself.)"""
         n = self.n
         nr = np.zeros((n, n, n), dtype=np.complex128)
         for k, xk in zip(self._ks(x, ks), x):
             psi = basis.to_grid(xk, self.mkq[k], n)
-            nr += self.kw[k] * np.sum(self.ur[k].conj() * psi, axis=0)
+            if self.metal:
+                nr += self.kw[k] * np.einsum("v,v...->...", self.f[k], self.ur[k].conj() * psi)
+            else:
+                nr += self.kw[k] * np.sum(self.ur[k].conj() * psi, axis=0)
         return 4.0 * nr / (self.omega * self.nfull)
 
     def symmetrize(self, nr):
@@ -172,10 +245,11 @@ class System:
         return self.apply_v(self.hxc_potential(self.response_density(x)))
 
     def apply_v(self, v, ks=None):
-        """K's last step: P_c^{k+Q} v'(r) u_{vk}(r) for the k-points ks (default all)."""
+        """K's last step: P_c^{k+Q} v'(r) u_{vk}(r) (P_{c,v} for a metal) for the k-points ks
+        (default all)."""
         ks = range(self.nks) if ks is None else ks
         out = [basis.to_sphere(v[None] * self.ur[k], self.mkq[k], self.n) for k in ks]
-        return self.project_c(out, ks)
+        return self.project_weighted(out, ks)
 
     def apply_op(self, x, upper: bool):
         """The operator the recursions apply to one half of a batch: D + K on the upper

@@ -16,8 +16,7 @@ With the single k-point Gamma this is a plasmon pole,
 Occupations: one plane wave (G = 0) per k-point, k near Gamma, and Q = 0.75 b_1 past the
 zone boundary, so that the lowest plane wave at k+Q is k+Q-b_1 and every head transition
 k -> k+Q is open with a positive energy (D > 0, as the pseudo-Hermitian recursion needs).
-A Fermi-surface (metallic) gas needs fractional occupations, outside the insulator form
-of Sec. 2.
+The metallic gas (smeared occupations, Sec. 2.6) is pinned in test_oracle_metal.py.
 """
 import numpy as np
 import pytest

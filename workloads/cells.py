@@ -58,6 +58,8 @@ class SystemSpec:
     flavour: str = "ph"            # 'ph' pseudo-Hermitian | 'nh' non-Hermitian
     free_electron: bool = False    # V_ion = 0 and plane-wave occupations (Lindhard pins)
     symmetry: bool = False         # response k-points in the irreducible wedge of the small group of Q
+    smearing_ry: float = 0.0       # Gaussian smearing width of a metal's occupations, Ry (0: insulator)
+    electrons: float | None = None # valence electrons per cell of a metal (None: 2 nbnd, every band full)
     extra: dict = field(default_factory=dict)
 
     @property
@@ -74,7 +76,11 @@ class SystemSpec:
 
     @property
     def nelec(self) -> float:
-        return 2.0 * self.nbnd
+        return 2.0 * self.nbnd if self.electrons is None else float(self.electrons)
+
+    @property
+    def metal(self) -> bool:
+        return self.smearing_ry > 0.0
 
     @property
     def nproj(self) -> int:
@@ -147,6 +153,17 @@ def config_sc16(q_cart: np.ndarray | None = None) -> SystemSpec:
                       extra={"scf_tol": 1e-8})
 
 
+def config_metal(kmesh: tuple = (4, 4, 4)) -> SystemSpec:
+    """The two-atom cell of config_small with its bare local potential only (no repulsive s
+    channel: a semimetal), 8 valence electrons in 6 bands, Gaussian smearing 0.04 Ry, 10 Ry,
+    18^3 grid, Q = 0.1 (2pi/a) x, RPA+ALDA kernel, 300 pseudo-Hermitian steps."""
+    lat, tau = _diamond(A_LAT)
+    q = 0.1 * (2 * np.pi / A_LAT) * np.array([1.0, 0.0, 0.0])
+    return SystemSpec("fcc2metal_10ry_18", lat, tau, 4.0, 1.0, 10.0, 18, kmesh, 6, q,
+                      approx="tddft", steps=300, flavour="ph", s_core_ry=0.0,
+                      smearing_ry=0.04, electrons=8.0)
+
+
 def config_tiny(kb: bool = False, approx: str = "tddft") -> SystemSpec:
     """A cell small enough for brute-force Casida diagonalisation: 4 Ry, 12^3, 2x2x2 k."""
     lat, tau = _diamond(A_LAT)
@@ -174,7 +191,8 @@ def config_free_electron(nk: int = 6, ecut: float = 3.0, nfft: int = 12,
     return s
 
 
-CONFIGS = {"small": config_small, "kb": config_kb, "tiny": config_tiny, "cubic8": config_cubic8, "sc16": config_sc16}
+CONFIGS = {"small": config_small, "kb": config_kb, "tiny": config_tiny, "cubic8": config_cubic8, "sc16": config_sc16,
+           "metal": config_metal}
 
 
 def sphere(kcart: np.ndarray, bvec: np.ndarray, ecut_ry: float, guard: float = 1e-9) -> np.ndarray:

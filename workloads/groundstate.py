@@ -18,7 +18,7 @@ from dataclasses import dataclass
 
 import numpy as np
 import scipy.linalg as sla
-from scipy.special import dawsn
+from scipy.special import dawsn, erfc
 
 from .cells import (SystemSpec, fft_miller, grid_operations, irreducible_kpoints, kmesh_frac, small_group,
                     sphere)
@@ -155,26 +155,67 @@ def _lowest(spec, kcart, vbox, nbnd):
     return mil, e, v.T.copy()
 
 
-def _density(spec, pts, kw):
+# Occupations below F_MIN (or within F_MIN of one) are set to 0 (or 1): the response then
+# counts a band as partially occupied only where its weight is significant.
+F_MIN = 1e-12
+
+
+def occupations(eps: np.ndarray, kw: np.ndarray, nelec: float, sigma_ha: float) -> tuple[float, np.ndarray]:
+    """Gaussian smearing: f_vk = erfc((eps_vk - mu)/sigma)/2, with the Fermi level mu found by
+    bisection so that 2 sum_k w_k sum_v f_vk = nelec (sum_k w_k = 1).  eps: (nks, nbnd) Ha.
+    Returns (mu, f) with f clamped to exactly 0 or 1 within F_MIN of either."""
+    eps = np.asarray(eps, dtype=np.float64)
+    w = np.asarray(kw, dtype=np.float64)[:, None]
+
+    def count(mu):
+        return 2.0 * float(np.sum(w * 0.5 * erfc((eps - mu) / sigma_ha)))
+
+    lo, hi = float(eps.min()) - 20 * sigma_ha, float(eps.max()) + 20 * sigma_ha
+    if not count(lo) < nelec < count(hi):
+        raise ValueError("too few bands for the electron count")
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if count(mid) < nelec:
+            lo = mid
+        else:
+            hi = mid
+    mu = 0.5 * (lo + hi)
+    return mu, smeared(eps, mu, sigma_ha)
+
+
+def smeared(eps: np.ndarray, mu: float, sigma_ha: float) -> np.ndarray:
+    """erfc((eps - mu)/sigma)/2, clamped to exactly 0 or 1 within F_MIN of either."""
+    f = 0.5 * erfc((np.asarray(eps, dtype=np.float64) - mu) / sigma_ha)
+    f[f < F_MIN] = 0.0
+    f[f > 1.0 - F_MIN] = 1.0
+    return f
+
+
+def _density(spec, pts, kw, occ=None):
+    """2 sum_k w_k sum_v f_vk |psi_vk(r)|^2 / Omega (f = 1 without occupations)."""
     n = spec.nfft
     rho = np.zeros((n, n, n))
-    for (mil, e, c), w in zip(pts, kw):
+    for i, ((mil, e, c), w) in enumerate(zip(pts, kw)):
         grid = np.zeros((c.shape[0], n, n, n), dtype=np.complex128)
         idx = mil % n
         grid[:, idx[:, 0], idx[:, 1], idx[:, 2]] = c
         psi = np.fft.ifftn(grid, axes=(1, 2, 3)) * n ** 3
-        rho += 2.0 * w * np.sum(np.abs(psi) ** 2, axis=0)
+        a2 = np.abs(psi) ** 2
+        if occ is None:
+            rho += 2.0 * w * np.sum(a2, axis=0)
+        else:
+            rho += 2.0 * w * np.einsum("v,v...->...", occ[i], a2)
     return rho / spec.omega
 
 
-def _feg_states(spec, kcart):
-    """Free-electron orbitals: the nbnd lowest plane waves of sphere(k)."""
+def _feg_states(spec, kcart, nb):
+    """Free-electron orbitals: the nb lowest plane waves of sphere(k)."""
     mil = sphere(kcart, spec.bvec, spec.ecut_ry)
     kg = kcart[None, :] + mil @ spec.bvec
     e = 0.5 * np.einsum("ij,ij->i", kg, kg)
-    order = np.argsort(e, kind="stable")[: spec.nbnd]
-    c = np.zeros((spec.nbnd, len(mil)), dtype=np.complex128)
-    c[np.arange(spec.nbnd), order] = 1.0
+    order = np.argsort(e, kind="stable")[:nb]
+    c = np.zeros((nb, len(mil)), dtype=np.complex128)
+    c[np.arange(nb), order] = 1.0
     return mil, e[order], c
 
 
@@ -198,6 +239,9 @@ class Bundle:
     gap_min: float = 0.0       # min_k (eps_{nbnd+1,k+Q} - eps_{nbnd,k}) (Ha), positivity of D
     kweight: np.ndarray | None = None   # (nks,) star sizes of irreducible k-points (None: every k once)
     sym: np.ndarray | None = None       # (nsym,3,3) int: the small group of Q on the FFT grid (None: identity)
+    occ_k: np.ndarray | None = None     # (nks,nbnd) occupations f_vk in [0,1] of a metal (None: all 1)
+    occ_kq: np.ndarray | None = None    # (nks,nbnd) occupations of the states at k+Q
+    fermi: float = 0.0                  # Fermi level of a metal (Ha)
 
     @property
     def nks(self):
@@ -275,7 +319,10 @@ def scf(spec: SystemSpec, tol: float = 1e-11, maxiter: int = 80, verbose: bool =
         v = vion + hartree_r(spec, rho) + lda_vxc(rho)
         vbox = np.fft.fftn(v) / n ** 3
         pts = runner.map(_lowest_job, [(spec, k, vbox, spec.nbnd) for k in kc])
-        rout = _density(spec, pts, kw)
+        occ = None
+        if spec.metal:
+            occ = occupations(np.array([p[1] for p in pts]), kw, spec.nelec, spec.smearing_ry / 2)[1]
+        rout = _density(spec, pts, kw, occ)
         res = rout - rho
         err = np.sum(np.abs(res)) * spec.omega / n ** 3
         if verbose:
@@ -324,8 +371,8 @@ def build_bundle(spec: SystemSpec, verbose: bool = False) -> Bundle:
         v, rho, iters = _scf_cached(spec, verbose, runner)
         vbox = np.fft.fftn(v) / n ** 3
         if spec.free_electron:
-            res_k = [_feg_states(spec, k) for k in kc]
-            res_q = [_feg_states(spec, k) for k in kq]
+            res_k = [_feg_states(spec, k, spec.nbnd + 1) for k in kc]
+            res_q = [_feg_states(spec, k, spec.nbnd + 1) for k in kq]
             gap = 0.0
         else:
             out = runner.map(_lowest_job, [(spec, k, vbox, spec.nbnd + 1) for k in np.concatenate([kc, kq])])
@@ -334,6 +381,23 @@ def build_bundle(spec: SystemSpec, verbose: bool = False) -> Bundle:
     finally:
         runner.close()
     nb = spec.nbnd
+    occ_k = occ_kq = None
+    fermi = 0.0
+    if spec.metal:
+        # occupations on the response mesh from its own levels (the wedge's with star weights)
+        ek = np.array([r[1][:nb + 1] for r in res_k])
+        eq = np.array([r[1][:nb + 1] for r in res_q])
+        wk = np.ones(len(kc)) if kweight is None else np.asarray(kweight, dtype=np.float64)
+        fermi, _ = occupations(ek[:, :nb], wk / wk.sum(), spec.nelec, spec.smearing_ry / 2)
+        sig = spec.smearing_ry / 2
+        if np.any(smeared(ek[:, nb], fermi, sig) > 0) or np.any(smeared(eq[:, nb], fermi, sig) > 0):
+            raise ValueError("band nbnd+1 is occupied: more bands needed")
+        occ_k, occ_kq = smeared(ek[:, :nb], fermi, sig), smeared(eq[:, :nb], fermi, sig)
+        # every state left out at k+Q must lie above every occupied level at k (the
+        # transitions into them then have positive energies)
+        gap = float(eq[:, nb].min() - ek[:, :nb][occ_k > 0].max())
+        if gap <= 0:
+            raise ValueError("a state left out at k+Q lies below an occupied level")
     beta, dij = [], np.zeros(0)
     for k, r in zip(kq, res_q):
         b, dij = kb_projectors(spec, k, r[0])
@@ -344,7 +408,8 @@ def build_bundle(spec: SystemSpec, verbose: bool = False) -> Bundle:
                   u_kq=[np.ascontiguousarray(r[2][:nb]) for r in res_q],
                   eps_k=np.array([r[1][:nb] for r in res_k]),
                   eps_kq=np.array([r[1][:nb] for r in res_q]),
-                  vloc_r=v, rho_r=rho, beta_kq=beta, dij=dij, scf_iters=iters, gap_min=gap, kweight=kweight, sym=sym)
+                  vloc_r=v, rho_r=rho, beta_kq=beta, dij=dij, scf_iters=iters, gap_min=gap, kweight=kweight, sym=sym,
+                  occ_k=occ_k, occ_kq=occ_kq, fermi=fermi)
 
 
 def _scf_cached(spec: SystemSpec, verbose: bool, runner) -> tuple:
@@ -354,6 +419,7 @@ def _scf_cached(spec: SystemSpec, verbose: bool, runner) -> tuple:
          for k, v in spec.__dict__.items()
          if k not in ("steps", "flavour", "approx", "extra", "q_cart", "kmesh", "name", "scf_kmesh", "symmetry")}
     d["scf_mesh"] = list(spec.scf_kmesh or spec.kmesh)
+    _drop_defaults(d)
     key = hashlib.sha1(json.dumps(d, sort_keys=True, default=str).encode()).hexdigest()[:16]
     path = os.path.join(cache_dir(), f"scf_{key}.npz")
     if os.path.exists(path):
@@ -366,11 +432,20 @@ def _scf_cached(spec: SystemSpec, verbose: bool, runner) -> tuple:
     return v, rho, iters
 
 
+def _drop_defaults(d: dict) -> None:
+    """Insulators keep the cache keys they had before the metal options existed."""
+    if not d.get("smearing_ry"):
+        d.pop("smearing_ry", None)
+    if d.get("electrons") is None:
+        d.pop("electrons", None)
+
+
 def _spec_key(spec: SystemSpec) -> str:
     d = {k: (np.asarray(v).round(12).tolist() if isinstance(v, np.ndarray) else v)
          for k, v in spec.__dict__.items() if k not in ("steps", "flavour", "approx", "extra")}
     if not d.get("symmetry"):      # keys of full-mesh bundles as before the option existed
         d.pop("symmetry", None)
+    _drop_defaults(d)
     return hashlib.sha1(json.dumps(d, sort_keys=True, default=str).encode()).hexdigest()[:16]
 
 
@@ -391,6 +466,8 @@ def save_bundle(b: Bundle, path: str) -> None:
                 u_k=np.concatenate([u.T for u in b.u_k]), u_kq=np.concatenate([u.T for u in b.u_kq]))
     if b.kweight is not None:
         arrs.update(kweight=b.kweight, sym=b.sym)
+    if b.occ_k is not None:
+        arrs.update(occ_k=b.occ_k, occ_kq=b.occ_kq, fermi=b.fermi)
     np.savez(path, **arrs)
 
 
@@ -412,7 +489,10 @@ def load_bundle(spec: SystemSpec, path: str) -> Bundle:
                   u_kq=[np.ascontiguousarray(sl(z["u_kq"], sq, i).T) for i in range(nks)],
                   eps_k=z["eps_k"], eps_kq=z["eps_kq"], vloc_r=z["vloc_r"], rho_r=z["rho_r"],
                   beta_kq=beta, dij=z["dij"], scf_iters=int(z["scf_iters"]), gap_min=float(z["gap_min"]),
-                  kweight=z["kweight"] if "kweight" in z.files else None, sym=z["sym"] if "sym" in z.files else None)
+                  kweight=z["kweight"] if "kweight" in z.files else None, sym=z["sym"] if "sym" in z.files else None,
+                  occ_k=z["occ_k"] if "occ_k" in z.files else None,
+                  occ_kq=z["occ_kq"] if "occ_kq" in z.files else None,
+                  fermi=float(z["fermi"]) if "fermi" in z.files else 0.0)
 
 
 def bundle_digest(b: Bundle) -> str:
@@ -427,6 +507,8 @@ def bundle_digest(b: Bundle) -> str:
         list(b.u_k) + list(b.u_kq)
     if b.kweight is not None:
         arrays += [b.kweight, b.sym]
+    if b.occ_k is not None:
+        arrays += [b.eps_kq, b.occ_k, b.occ_kq]
     for a in arrays:
         a = np.ascontiguousarray(a)
         h.update(str(a.dtype).encode() + str(a.shape).encode())
