@@ -71,7 +71,8 @@ def _chain(b, precision, max_steps, stream, flavour="ph"):
     return ll.Chain(lattice=s.lattice, nfft=s.nfft, kcart=b.kcart, miller_k=b.miller_k, miller_kq=b.miller_kq,
                     u_k=b.u_k, u_kq=b.u_kq, eps_k=b.eps_k, vloc_r=b.vloc_r, rho_r=b.rho_r, beta_kq=b.beta_kq,
                     dij=b.dij, q_cart=s.q_cart, approx="tddft", flavour=flavour, precision=precision,
-                    max_steps=max_steps, stream=stream, kweight=b.kweight, sym=b.sym)
+                    max_steps=max_steps, stream=stream, kweight=b.kweight, sym=b.sym,
+                    **({} if b.occ_k is None else dict(occ_k=b.occ_k, occ_kq=b.occ_kq, eps_kq=b.eps_kq)))
 
 
 def _kb_wedge(b_full, stream, K, W):
@@ -174,6 +175,28 @@ def _small_cell(stream):
     return {"workload": "fcc2_10ry_18: 2-atom FCC, 10 Ry, 18^3, 4x4x4 k, 4 bands, RPA+ALDA, PH, FP64",
             "steps": 300, "steps_per_s": 300 / (ms / 1e3), "ms_per_step": ms / 300,
             "spectrum_ms": e0.elapsed_time(e1), "dtype": "f64"}
+
+
+def _metal_cell(stream, steps: int = 300, window: int = 80):
+    """The semimetal with smeared occupations (Sec. 2.6: two-atom cell with its bare local
+    potential, 10 Ry, 18^3, 4x4x4 k, 6 bands with fractional occupations, RPA+ALDA, PH):
+    FP32 and FP64 steps/s over 300 steps, the FP64 coefficients of the first 100 steps and the
+    FP32 loss function of the first 80 (the cell's FP32 window) against the oracle's golden
+    coefficients of the same bundle."""
+    import workloads as w
+    b = w.get_bundle(w.config_metal())
+    out = {"workload": "fcc2metal_10ry_18: 2-atom semimetal, Gaussian smearing 0.04 Ry, 10 Ry, 18^3, "
+                       "4x4x4 k, 6 bands, RPA+ALDA, PH", "steps": steps}
+    ref = _golden(b, "metal_ph", 100)
+    for prec in ("fp32", "fp64"):
+        ch, c, ms, _ = _time_chain(b, prec, steps, 5, stream)
+        ch.close()
+        out[prec] = {"steps_per_s": steps / (ms / 1e3), "ms_per_step": ms / steps}
+        if ref is not None and prec == "fp32":
+            out[prec]["loss_err_vs_oracle_80"] = _loss_err(c, ref, b, window)
+        if ref is not None and prec == "fp64":
+            out[prec]["coef_err_vs_oracle_100"] = float(np.max(np.abs(c[0][:100] - ref[0]) / np.abs(ref[0])))
+    return out
 
 
 def _step_flops(b) -> tuple[float, float]:
@@ -558,6 +581,7 @@ def main():
         small = _small_cell(stream)
     sc16 = None if args.headline_only else _sc16(stream)
     wedge = None if args.headline_only else _kb_wedge(b, stream, K, W)
+    metal = None if args.headline_only else _metal_cell(stream)
     # the spectrum check spans the first SPEC_WINDOW coefficients whatever K is: the chains run
     # on, untimed, to that many steps
     kt = len(c32[0])
@@ -662,7 +686,7 @@ def main():
                        "l2": "per-step working set ~0.6 GB > 129 MB L2 (no flush)", "parallelism": "replicas"},
             "fp64": None if args.headline_only else {"value": world * K / (ms64 / 1e3), "ms_per_step": ms64 / K,
                                                       "dtype": "f64"},
-            "nh_fp32": nh, "small_cell": small, "sc16": sc16, "kb_wedge": wedge,
+            "nh_fp32": nh, "small_cell": small, "sc16": sc16, "kb_wedge": wedge, "metal": metal,
             "speedup_fp32_vs_fp64": ms64 / ms32,
             "spectrum_err_fp32_vs_fp64": spec_err, "spectrum_window_steps": m,
             "spectrum_err_fp32_vs_fp64_timed_steps": spec_err_full, "spectrum_vs_oracle": vs_oracle,

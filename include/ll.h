@@ -89,7 +89,25 @@ typedef struct {
   const double* kweight;
   int nsym;
   const int* sym;
+  /* Metals by smearing (Sec. 2.6: the projector on empty states redefined, fractional
+   * occupations as weights in the band sums).  With occ_k (host, [nks][nbnd], each in [0, 1])
+   * the bands are the partially or fully occupied ones: occ_k[k][v] = f_vk weights band v of k
+   * in the response density (the library folds sqrt(f_vk) into u_k), occ_kq (host,
+   * [nks][nbnd]) holds the occupations f_m of the states u_kq and eps_kq (host, [nks][nbnd],
+   * Ha) their eigenvalues (u_kq must be eigenvectors of H_{k+Q}).  Each pair of levels is
+   * given to its direction of positive transition energy: per band v the projector on empty
+   * states keeps u_m with weight c_mv = max(1 - f_m/f_v, 0) (0 for f_v = 0, and 0 below
+   * LL_METAL_CMIN), the Lanczos vectors keep the states with c_mv > 0, and the scalar
+   * products carry the metric weight 1/c_mv on them.  Every state of k+Q beyond the nbnd given
+   * must lie above every occupied level of k.  The response is for Q + G != 0 (no Fermi-level
+   * shift).  NULL: an insulator (every band full).  Fused per-k path only (LL_EUNSUPPORTED
+   * where the bands of a k-point do not fit one CTA's shared memory).                       */
+  const double* occ_k;
+  const double* occ_kq;
+  const double* eps_kq;
 } ll_system_desc;
+
+#define LL_METAL_CMIN 1e-6
 
 enum { LL_WHERE_HOST = 0, LL_WHERE_DEVICE = 1 };
 
@@ -128,7 +146,10 @@ int ll_create_sharing(const ll_system_desc* desc, ll_handle* share, void* stream
  *   beta[i]  = b_1 (i = 0) or T_{i+1,i};   gamma[i] (complex) = b_1 or T_{i,i+1};
  *   z[i] (complex) = z_{i+1} = ((y, 0), v_{i+1}) (Eq. 31).
  * Any of alpha, beta, gamma, z may be NULL.  LL_ENOTPD / LL_EBREAKDOWN stop the chain;
- * steps_done then counts the steps whose coefficients are valid. */
+ * steps_done then counts the steps whose coefficients are valid.  A breakdown met only in
+ * forming the coefficient after the n_steps asked for (the Krylov space exhausted at exactly
+ * that length) returns LL_OK with every coefficient asked for; the chain stops, and the next
+ * call returns LL_EBREAKDOWN. */
 int ll_lanczos(ll_handle* h, int n_steps, double* alpha, double* beta, double* gamma, double* z, int* steps_done);
 
 /* Spectrum of a handle's own coefficients on the device (Eqs. 32-33, 5):

@@ -118,7 +118,10 @@ static inline std::vector<FiniteCheck> input_arrays(const ll_system_desc* d) {
           {d->kcart, 3L * d->nks, "kcart", false, false},    {d->u_k, 2 * nb * sk, "u_k", dv, true},
           {d->u_kq, 2 * nb * sq, "u_kq", dv, true},          {d->eps_k, (long)d->nks * nb, "eps_k", false, false},
           {d->vloc_r, n3, "vloc_r", dv, true},               {d->rho_r, n3, "rho_r", dv, true},
-          {d->beta_kq, 2 * np * sq, "beta_kq", dv, true},   {d->dij, np, "dij", false, false}};
+          {d->beta_kq, 2 * np * sq, "beta_kq", dv, true},   {d->dij, np, "dij", false, false},
+          {d->occ_k, d->occ_k ? (long)d->nks * nb : 0, "occ_k", false, false},
+          {d->occ_kq, (d->occ_k && d->occ_kq) ? (long)d->nks * nb : 0, "occ_kq", false, false},
+          {d->eps_kq, (d->occ_k && d->eps_kq) ? (long)d->nks * nb : 0, "eps_kq", false, false}};
 }
 
 // large_on_host: check the large arrays here too (the request loop refuses a malformed job at
@@ -240,7 +243,8 @@ template <int N, int MODE> struct BO {
 };
 
 // FNV-1a (64 bit) over the inputs that determine the u_{vk}(r) grids: the precision, the grid
-// side, the k-point and band counts, the spheres of k and the u_k coefficients (host arrays).
+// side, the k-point and band counts, the spheres of k, the u_k coefficients and the weights
+// folded into them (host arrays).
 static inline uint64_t ground_state_hash(const ll_system_desc* d) {
   uint64_t h = 1469598103934665603ull;
   auto feed = [&](const void* p, size_t n) {   // FNV-1a over 8-byte words, then the tail bytes
@@ -263,6 +267,7 @@ static inline uint64_t ground_state_hash(const ll_system_desc* d) {
   feed(d->miller_k, sizeof(int) * 3 * (size_t)sk);
   feed(d->u_k, sizeof(double) * 2 * (size_t)d->nbnd * sk);
   if (d->kweight) feed(d->kweight, sizeof(double) * (size_t)d->nks);   // folded into u_k
+  if (d->occ_k) feed(d->occ_k, sizeof(double) * (size_t)d->nks * d->nbnd);   // folded into u_k
   return h;
 }
 
@@ -323,6 +328,37 @@ class Chain : public ChainBase {
       }
       for (int k = 0; k < nks_; ++k) kscale_[k] = std::sqrt(d->kweight[k] * nks_ / sw);
     }
+    // a metal (Sec. 2.6): band weights sqrt(f_vk) folded into u_k, the projector and metric tables
+    rowscale_.assign((size_t)nks_ * nbnd_, 1.0);
+    for (int k = 0; k < nks_; ++k)
+      for (int v = 0; v < nbnd_; ++v) rowscale_[(size_t)k * nbnd_ + v] = kscale_[k];
+    metal_ = d->occ_k != nullptr;
+    if (metal_) {
+      if (!d->occ_kq || !d->eps_kq) { err = "a metal needs occ_kq and eps_kq"; return LL_EINVAL; }
+      for (long i = 0; i < (long)nks_ * nbnd_; ++i)
+        if (!(d->occ_k[i] >= 0.0 && d->occ_k[i] <= 1.0) || !(d->occ_kq[i] >= 0.0 && d->occ_kq[i] <= 1.0)) {
+          err = "occupations must lie in [0, 1]";
+          return LL_EINVAL;
+        }
+      const long sz = (long)nks_ * nbnd_ * nbnd_;
+      mtab_.assign(4 * sz, 0.0);
+      for (int k = 0; k < nks_; ++k)
+        for (int m = 0; m < nbnd_; ++m)
+          for (int v = 0; v < nbnd_; ++v) {
+            const double fv = d->occ_k[(long)k * nbnd_ + v], fm = d->occ_kq[(long)k * nbnd_ + m];
+            double c = fv > 0.0 ? std::max(1.0 - fm / fv, 0.0) : 0.0;
+            if (c < LL_METAL_CMIN) c = 0.0;
+            const double delta = d->eps_kq[(long)k * nbnd_ + m] - d->eps_k[(long)k * nbnd_ + v];
+            const long i = ((long)k * nbnd_ + m) * nbnd_ + v;
+            const double qh = c > 0.0 ? 1.0 - std::sqrt(c) : 0.0;
+            mtab_[i] = c > 0.0 ? qh : 1.0;                        // sp
+            mtab_[sz + i] = c > 0.0 ? (1.0 - c) * delta : 0.0;   // da
+            mtab_[2 * sz + i] = c > 0.0 ? 0.0 : 1.0;             // keep
+            mtab_[3 * sz + i] = qh;                               // qh
+          }
+      for (int k = 0; k < nks_; ++k)
+        for (int v = 0; v < nbnd_; ++v) rowscale_[(size_t)k * nbnd_ + v] *= std::sqrt(d->occ_k[(long)k * nbnd_ + v]);
+    }
     if (d->nsym < 0 || (d->nsym > 1 && !d->sym) || d->nsym > 48) { err = "bad symmetry operations"; return LL_EINVAL; }
     nsym_ = d->nsym > 1 ? d->nsym : 1;
     sym_host_.assign(9, 0);
@@ -338,6 +374,40 @@ class Chain : public ChainBase {
         has_identity |= m[0] == 1 && m[4] == 1 && m[8] == 1 && !m[1] && !m[2] && !m[3] && !m[5] && !m[6] && !m[7];
       }
       if (!has_identity) { err = "the symmetry operations lack the identity"; return LL_EINVAL; }
+    }
+    double b[3][3];
+    recip(d->lattice, b);
+    omega_ = fabs(d->lattice[0][0] * (d->lattice[1][1] * d->lattice[2][2] - d->lattice[1][2] * d->lattice[2][1]) -
+                  d->lattice[0][1] * (d->lattice[1][0] * d->lattice[2][2] - d->lattice[1][2] * d->lattice[2][0]) +
+                  d->lattice[0][2] * (d->lattice[1][0] * d->lattice[2][1] - d->lattice[1][1] * d->lattice[2][0]));
+    for (int a = 0; a < 3; ++a) q_[a] = d->q_cart[a];
+    const long n3 = (long)n * n * n;
+    const int pq = hq_.npw_pad, pk = hk_.npw_pad;
+    const long vq = (long)nks_ * nbnd_ * pq;  // one batch vector
+    nvec_ = (flavour_ == LL_FLAVOUR_NH) ? 2 : 1;
+
+    // Hartree kernel 4 pi / |Q + G|^2 / N^3 over the box, [m3][m2][m1]
+    std::vector<T> wh(n3);
+    for (int i3 = 0; i3 < n; ++i3)
+      for (int i2 = 0; i2 < n; ++i2)
+        for (int i1 = 0; i1 < n; ++i1) {
+          const int m1 = i1 < n / 2 ? i1 : i1 - n, m2 = i2 < n / 2 ? i2 : i2 - n, m3 = i3 < n / 2 ? i3 : i3 - n;
+          double g[3];
+          for (int a = 0; a < 3; ++a) g[a] = q_[a] + m1 * b[0][a] + m2 * b[1][a] + m3 * b[2][a];
+          const double g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+          if (!(g2 > 1e-20)) { err = "Q + G = 0 on the grid (Q is a reciprocal lattice vector)"; return LL_EINVAL; }
+          wh[((long)i3 * n + i2) * n + i1] = (T)(4.0 * 3.14159265358979323846 / g2 / (double)n3);
+        }
+    // kinetic 1/2 |k + Q + G|^2 on sphere(k+Q)
+    std::vector<T> kin((size_t)nks_ * pq, T(0));
+    for (int k = 0; k < nks_; ++k) {
+      const int* m = d->miller_kq + 3L * hq_.off[k];
+      for (int i = 0; i < hq_.npw[k]; ++i) {
+        double g[3];
+        for (int a = 0; a < 3; ++a)
+          g[a] = d->kcart[3 * k + a] + q_[a] + m[3 * i] * b[0][a] + m[3 * i + 1] * b[1][a] + m[3 * i + 2] * b[2][a];
+        kin[(size_t)k * pq + i] = (T)(0.5 * (g[0] * g[0] + g[1] * g[1] + g[2] * g[2]));
+      }
     }
     // The large arrays on the device: the caller's (where = LL_WHERE_DEVICE) or one staging copy
     // of the host arrays; finiteness is checked and the padded tables are built there.
@@ -397,40 +467,6 @@ class Chain : public ChainBase {
         return LL_EINVAL;
       }
     }
-    double b[3][3];
-    recip(d->lattice, b);
-    omega_ = fabs(d->lattice[0][0] * (d->lattice[1][1] * d->lattice[2][2] - d->lattice[1][2] * d->lattice[2][1]) -
-                  d->lattice[0][1] * (d->lattice[1][0] * d->lattice[2][2] - d->lattice[1][2] * d->lattice[2][0]) +
-                  d->lattice[0][2] * (d->lattice[1][0] * d->lattice[2][1] - d->lattice[1][1] * d->lattice[2][0]));
-    for (int a = 0; a < 3; ++a) q_[a] = d->q_cart[a];
-    const long n3 = (long)n * n * n;
-    const int pq = hq_.npw_pad, pk = hk_.npw_pad;
-    const long vq = (long)nks_ * nbnd_ * pq;  // one batch vector
-    nvec_ = (flavour_ == LL_FLAVOUR_NH) ? 2 : 1;
-
-    // Hartree kernel 4 pi / |Q + G|^2 / N^3 over the box, [m3][m2][m1]
-    std::vector<T> wh(n3);
-    for (int i3 = 0; i3 < n; ++i3)
-      for (int i2 = 0; i2 < n; ++i2)
-        for (int i1 = 0; i1 < n; ++i1) {
-          const int m1 = i1 < n / 2 ? i1 : i1 - n, m2 = i2 < n / 2 ? i2 : i2 - n, m3 = i3 < n / 2 ? i3 : i3 - n;
-          double g[3];
-          for (int a = 0; a < 3; ++a) g[a] = q_[a] + m1 * b[0][a] + m2 * b[1][a] + m3 * b[2][a];
-          const double g2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
-          if (!(g2 > 1e-20)) { err = "Q + G = 0 on the grid (Q is a reciprocal lattice vector)"; return LL_EINVAL; }
-          wh[((long)i3 * n + i2) * n + i1] = (T)(4.0 * 3.14159265358979323846 / g2 / (double)n3);
-        }
-    // kinetic 1/2 |k + Q + G|^2 on sphere(k+Q)
-    std::vector<T> kin((size_t)nks_ * pq, T(0));
-    for (int k = 0; k < nks_; ++k) {
-      const int* m = d->miller_kq + 3L * hq_.off[k];
-      for (int i = 0; i < hq_.npw[k]; ++i) {
-        double g[3];
-        for (int a = 0; a < 3; ++a)
-          g[a] = d->kcart[3 * k + a] + q_[a] + m[3 * i] * b[0][a] + m[3 * i + 1] * b[1][a] + m[3 * i + 2] * b[2][a];
-        kin[(size_t)k * pq + i] = (T)(0.5 * (g[0] * g[0] + g[1] * g[1] + g[2] * g[2]));
-      }
-    }
     // padded orbital tables and grids transposed to [j3][j2][j1]: built on the device from the
     // large arrays (the caller's device arrays or their staging copy) by k_pad_rows / k_grids_in
     const long bkq_len = nproj_ ? (long)nks_ * nproj_ * pq : 1;
@@ -468,6 +504,10 @@ class Chain : public ChainBase {
       // the chunked path also where the band groups are small: per-group CTAs would read the
       // projectors and U_{k+Q} once per group (32 times per k on the 16-atom cell)
       split_ = best == 0 || 4 * best < nbnd_ || (env && env[0] == '1' && env[1] == 0);
+      if (split_ && metal_) {
+        err = "a metal needs the bands of a k-point in one CTA (the fused per-k path)";
+        return LL_EUNSUPPORTED;
+      }
       nchunk_ = split_ ? (pq + kChunk - 1) / kChunk : 1;
       npk_ = split_ ? nchunk_ : ngrp_;
       // FP32 path: the split path's dot blocks on the tensor cores (tcproj.cuh) where their
@@ -495,6 +535,12 @@ class Chain : public ChainBase {
         (rc = alloc(&beta_, cap_ + 2)) || (rc = alloc(&gamma_, cap_ + 2)) || (rc = alloc(&z_, cap_ + 1)) ||
         (rc = alloc(&zpart_, (long)(cap_ + 1) * nzp)) || (rc = alloc(&err_, 2)) || (rc = alloc(&jdev_, 1)))
       return rc;
+    if (metal_) {
+      const long sz = (long)nks_ * nbnd_ * nbnd_;
+      if ((rc = alloc(&mc_, 4 * sz)) || (rc = alloc(&img_, nvec_ * vq)) || (rc = alloc(&zp_, nvec_ * sz))) return rc;
+      LL_CK(cudaMemcpyAsync(mc_, mtab_.data(), 4 * sz * sizeof(double), cudaMemcpyHostToDevice, st_));
+      md_ = MetalDev{mc_, mc_ + sz, mc_ + 2 * sz, mc_ + 3 * sz};
+    }
     {
       const char* g = getenv("LL_GRAPHS");
       use_graphs_ = use_graphs_ && !(g && g[0] == '0' && g[1] == 0);
@@ -512,10 +558,10 @@ class Chain : public ChainBase {
     {
       int *offk = nullptr, *offq = nullptr;
       double* ksc = nullptr;
-      if ((rc = alloc(&offk, nks_ + 1)) || (rc = alloc(&offq, nks_ + 1)) || (rc = alloc(&ksc, nks_))) return rc;
+      if ((rc = alloc(&offk, nks_ + 1)) || (rc = alloc(&offq, nks_ + 1)) || (rc = alloc(&ksc, (long)nks_ * nbnd_))) return rc;
       LL_CK(cudaMemcpyAsync(offk, hk_.off.data(), (nks_ + 1) * sizeof(int), cudaMemcpyHostToDevice, st_));
       LL_CK(cudaMemcpyAsync(offq, hq_.off.data(), (nks_ + 1) * sizeof(int), cudaMemcpyHostToDevice, st_));
-      LL_CK(cudaMemcpyAsync(ksc, kscale_.data(), nks_ * sizeof(double), cudaMemcpyHostToDevice, st_));
+      LL_CK(cudaMemcpyAsync(ksc, rowscale_.data(), (size_t)nks_ * nbnd_ * sizeof(double), cudaMemcpyHostToDevice, st_));
       k_pad_rows<T><<<dim3(nks_, nbnd_), 256, 0, st_>>>(large[0].p, offk, dk_.npw, nbnd_, hk_.npw_pad, ksc, uk_);
       k_pad_rows<T><<<dim3(nks_, nbnd_), 256, 0, st_>>>(large[1].p, offq, dq_.npw, nbnd_, pq, nullptr, ukq_);
       if (nproj_) k_pad_rows<T><<<dim3(nks_, nproj_), 256, 0, st_>>>(large[4].p, offq, dq_.npw, nproj_, pq, nullptr, bkq_);
@@ -563,9 +609,11 @@ class Chain : public ChainBase {
       LL_CK(cudaStreamSynchronize(st_));
       for (int* p : {mk, mq, ok, oq, nk, nq}) release(p);
     }
-    // y = P_c (u_k on sphere(k+Q))   (Eq. 28)
+    // y = P_c (u_k on sphere(k+Q))   (Eq. 28).  A metal: Q^-1 of the start P_{c,v} u_k (u_k with
+    // sqrt(f_v) folded in), i.e. Q P'_v u_k
     k_gather_y<T><<<nks_, 128, 0, st_>>>(nks_, nbnd_, pq, pk, map_, uk_, y_);
-    k_project<T><<<dim3(nks_, 1), 128, 0, st_>>>(nks_, nbnd_, pq, dq_.npw, ukq_, y_);
+    k_project<T><<<dim3(nks_, 1), 128, 0, st_>>>(nks_, nbnd_, pq, dq_.npw, ukq_, y_, md_.keep);
+    if (metal_) k_project<T><<<dim3(nks_, 1), 128, 0, st_>>>(nks_, nbnd_, pq, dq_.npw, ukq_, y_, md_.qh);
     LL_CK(cudaGetLastError());
     // u_{vk}(r) grids: columns of sphere(k), then the planes (unless a chain of the same ground
     // state lends its grids)
@@ -675,7 +723,7 @@ class Chain : public ChainBase {
           if ((rc = set_smem(k_nh_update<T>, smem_nh, err))) return rc;
           k_nh_update<T><<<dim3(nks_, ngrp_), 128, smem_nh, st_>>>(j, upper, nks_, nbnd_, bpc_, pq, dq_.npw, XV(),
                                                                    XW(), VpNH(), Wp(),
-                                                      Vc(), y_, ukq_, co, spart_);
+                                                      Vc(), y_, ukq_, co, spart_, md_.keep);
         }
         k_nh_normalize<T><<<nks_, 128, 0, st_>>>(j, nks_, nbnd_, pq, npk_, spart_, XV(), XW(), Vc(), VpNH(), Wc(),
                                                  Wp(), co, tol_);
@@ -711,7 +759,7 @@ class Chain : public ChainBase {
   }
   // launch counts of a replayed step (the same kernels as ph_step)
   void count_step(int j) {
-    prof_.count(LL_PROF_ZINV, split_ ? 4 : 2);
+    prof_.count(LL_PROF_ZINV, (split_ ? 4 : 2) + (metal_ ? 1 : 0));
     prof_.count(LL_PROF_UPDATE);
     prof_.count(LL_PROF_XY1);
     if (j % 2 == 1 && approx_ != LL_APPROX_IPA) {
@@ -752,7 +800,12 @@ class Chain : public ChainBase {
     LL_CK(cudaStreamSynchronize(st_));
     steps_ = queued_;
     int status = LL_OK;
-    if (herr[0] != DEV_OK) {
+    if (herr[0] != DEV_OK && herr[0] != DEV_TIMEOUT && herr[1] - 1 >= queued_) {
+      // the breakdown is that of the coefficient after the last one asked for (the
+      // non-Hermitian step forms beta_{j+1} with z_j): every coefficient asked for is valid;
+      // the chain stops, and the next call reports it
+      stopped_ = true;
+    } else if (herr[0] != DEV_OK) {
       steps_ = std::min(steps_, herr[1] - 1);
       queued_ = steps_;
       status = (herr[0] == DEV_NOTPD) ? LL_ENOTPD : (herr[0] == DEV_TIMEOUT ? LL_ETIMEOUT : LL_EBREAKDOWN);
@@ -866,10 +919,19 @@ class Chain : public ChainBase {
   int op(int nvec, const cplx<T>* in, cplx<T>* out, int dens_vec, std::string& err) {
     int rc;
     const int e0 = prof_.mark(st_);
-    if ((rc = launch_zinv(dq_, in, nvec))) { err = "zinv launch"; return rc; }
+    if ((rc = launch_zinv(dq_, metal_image(in, nvec), nvec))) { err = "zinv launch"; return rc; }
     prof_.count(LL_PROF_ZINV);
     prof_.span(LL_PROF_ZINV, e0, prof_.mark(st_));
     return op_rest(nvec, in, out, dens_vec, err);
+  }
+
+  // A metal: the image Q z of the batch vectors at `in` (and Z = U^H z) that the FFT pipeline
+  // reads in their place; an insulator: `in` itself.
+  const cplx<T>* metal_image(const cplx<T>* in, int nvec) {
+    if (!metal_) return in;
+    k_metal_image<T><<<dim3(nks_, nvec), 128, 0, st_>>>(nks_, nbnd_, hq_.npw_pad, dq_.npw, ukq_, in, img_, zp_, md_);
+    prof_.count(LL_PROF_ZINV);
+    return img_;
   }
 
   // everything after the axis-3 inverse FFT: planes, response potential, axis-3 forward FFT
@@ -909,8 +971,9 @@ class Chain : public ChainBase {
                         (size_t)std::max(nproj_, nbnd_) * bpc_ * sizeof(cplx<double>) + red_bytes(256);
     int rc;
     if ((rc = set_smem(k_zfwd_proj<T, N>, smem, err))) return rc;
-    k_zfwd_proj<T, N><<<dim3(nks_, nvec, ngrp_), 256, smem, st_>>>(dq_, nbnd_, bpc_, cbuf_, cb_ncol_, in, kin_, eps_,
-                                                                    ukq_, bkq_, dij_, nproj_, out, part_);
+    k_zfwd_proj<T, N><<<dim3(nks_, nvec, ngrp_), 256, smem, st_>>>(dq_, nbnd_, bpc_, cbuf_, cb_ncol_,
+                                                                    metal_ ? img_ : in, kin_, eps_, ukq_, bkq_,
+                                                                    dij_, nproj_, out, part_, md_, zp_);
     LL_CK(cudaGetLastError());
     return LL_OK;
   }
@@ -1043,8 +1106,8 @@ class Chain : public ChainBase {
     // the per-(k, band group) update, then the axis-3 inverse FFTs, one thread per column line
     if ((rc = set_smem(k_ph_update<T>, smem, err))) return rc;
     k_ph_update<T><<<dim3(nks_, ngrp_), 256, smem, st_>>>(jdev_, dq_, nbnd_, bpc_, part_, R(), X(), Vp(), y_, ukq_, co,
-                                                          tol_);
-    k_zinv<T, N><<<dim3(nks_, 1, zsplit()), 128, 0, st_>>>(dq_, R(), nbnd_, cbuf_, cb_ncol_);
+                                                          tol_, md_.keep);
+    k_zinv<T, N><<<dim3(nks_, 1, zsplit()), 128, 0, st_>>>(dq_, metal_image(R(), 1), nbnd_, cbuf_, cb_ncol_);
     LL_CK(cudaGetLastError());
     return LL_OK;
   }
@@ -1437,6 +1500,13 @@ class Chain : public ChainBase {
   std::vector<std::pair<void*, size_t>> ptrs_;   // every allocation and its size
   std::shared_ptr<void> ur_share_;               // the u_{vk}(r) grids, possibly shared
   std::vector<double> kscale_;                   // sqrt(w_k nks / sum w): folded into u_k
+  std::vector<double> rowscale_;                 // [nks][nbnd] kscale_ times sqrt(f_vk) (a metal)
+  bool metal_ = false;                           // occupations given (Sec. 2.6)
+  std::vector<double> mtab_;                     // the MetalDev tables on the host
+  double* mc_ = nullptr;                         // ... and on the device
+  MetalDev md_{nullptr, nullptr, nullptr, nullptr};
+  cplx<T>* img_ = nullptr;                       // the image Q z of the operator's input (a metal)
+  cplx<double>* zp_ = nullptr;                   // Z = U^H z of that input, [nvec][nks][nbnd][nbnd]
   std::vector<int> sym_host_;                    // small group of Q on the grid, [nsym][9]
   int nsym_ = 1;
   int* sym_ = nullptr;

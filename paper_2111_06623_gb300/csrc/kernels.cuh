@@ -517,17 +517,90 @@ __device__ __forceinline__ void subtract_projection(cplx<T>* x, const cplx<T>* u
   __syncthreads();
 }
 
-// x <- P_c x for every orbital of k (in place).  grid (nks, nvec), block 128.
+// Metals (Sec. 2.6; smeared occupations f).  With c_mv = max(1 - f_m/f_v, 0) the weight of the
+// projector on empty states P_{c,v} for the states m of k+Q and band v of k, the library
+// iterates on z = Q^-1 (sqrt(f_v) x), Q = P_{c,v}^{1/2} (weight sqrt(c_mv) on the states of
+// k+Q kept, 1 off them): there the operator D + Q W Q is symmetric (W: the Hartree-XC response
+// of the density of Q z with the weights sqrt(f_v) folded into u_k), so the recursions need no
+// metric, and the components along the kept states are not scaled down by sqrt(c) (in FP32 a
+// scaled-down component would carry rounding blown up by 1/sqrt(c) into the scalar products).
+// The image Q z feeds the FFT pipeline; the per-k projections restore Q^-1.  With Delta_mv =
+// eps_{m,k+Q} - eps_{vk}, four [nks][nbnd (m)][nbnd (v)] tables in double:
+//   sp   = 1 - sqrt(c) (1 where c = 0)  coefficient of S = U^H t in the operator's projection
+//   da   = [c > 0] (1 - c) Delta        coefficient of Z = U^H z there (D's component along m)
+//   keep = [c == 0]                     the projection P'_v of the Lanczos vectors
+//   qh   = [c > 0] (1 - sqrt(c))        the image: Q z = z - U (qh Z)
+// All null: an insulator.
+struct MetalDev {
+  const double* sp;
+  const double* da;
+  const double* keep;
+  const double* qh;
+};
+
+static __device__ __forceinline__ long metal_idx(int k, int m, int v, int nbnd) {
+  return ((long)k * nbnd + m) * nbnd + v;
+}
+
+// The sum of one double per thread over the block, in a fixed order (threads' values by warp,
+// then the warps in order); every thread gets it.  Ends synchronised.
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double wsum[32];
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w];
+  __syncthreads();
+  return t;
+}
+
+// x <- P_c x for every orbital of k (in place); with coef ([nks][nbnd][nbnd], m-major), the
+// component along u_m of band v is removed with weight coef[k][m][v] instead of 1.
+// grid (nks, nvec), block 128.
 template <typename T>
 __global__ void __launch_bounds__(128) k_project(int nks, int nbnd, int npw_pad, const int* __restrict__ npw,
-                                                 const cplx<T>* __restrict__ ukq, cplx<T>* __restrict__ x) {
+                                                 const cplx<T>* __restrict__ ukq, cplx<T>* __restrict__ x,
+                                                 const double* __restrict__ coef) {
   __shared__ cplx<double> cf[32 * 32];
   __shared__ double red[4 * 16];
   const int k = blockIdx.x, vec = blockIdx.y;
   const long base = ((long)vec * nks + k) * nbnd * npw_pad;
   const cplx<T>* uk = ukq + (long)k * nbnd * npw_pad;
   block_dots<T>(uk, npw_pad, x + base, npw_pad, npw[k], nbnd, nbnd, nullptr, cf, red);
+  if (coef) {
+    for (int i = threadIdx.x; i < nbnd * nbnd; i += blockDim.x) {
+      const double c = coef[(long)k * nbnd * nbnd + i];
+      cf[i] = mk(cf[i].x * c, cf[i].y * c);
+    }
+    __syncthreads();
+  }
   subtract_projection<T>(x + base, uk, cf, nbnd, nbnd, npw_pad);
+}
+
+// A metal's image of a batch vector z for the FFT pipeline: img = Q z = z - U (qh Z) and
+// zp = [c > 0] Z, Z = U^H z (double), per (vector, k).  grid (nks, nvec), block 128.
+template <typename T>
+__global__ void __launch_bounds__(128) k_metal_image(int nks, int nbnd, int npw_pad, const int* __restrict__ npw,
+                                                     const cplx<T>* __restrict__ ukq, const cplx<T>* __restrict__ z,
+                                                     cplx<T>* __restrict__ img, cplx<double>* __restrict__ zp,
+                                                     MetalDev md) {
+  __shared__ cplx<double> cf[32 * 32];
+  __shared__ double red[4 * 16];
+  const int k = blockIdx.x, vec = blockIdx.y;
+  const long base = ((long)vec * nks + k) * nbnd * npw_pad;
+  const cplx<T>* uk = ukq + (long)k * nbnd * npw_pad;
+  block_dots<T>(uk, npw_pad, z + base, npw_pad, npw[k], nbnd, nbnd, nullptr, cf, red);
+  for (int i = threadIdx.x; i < nbnd * nbnd; i += blockDim.x) {
+    const long ci = (long)k * nbnd * nbnd + i;
+    const cplx<double> v = cf[i];
+    const double kept = md.keep[ci] == 0.0 ? 1.0 : 0.0, q = md.qh[ci];
+    zp[(long)vec * nks * nbnd * nbnd + ci] = mk(v.x * kept, v.y * kept);
+    cf[i] = mk(v.x * q, v.y * q);
+  }
+  for (int i = threadIdx.x; i < nbnd * npw_pad; i += blockDim.x) img[base + i] = z[base + i];
+  __syncthreads();
+  subtract_projection<T>(img + base, uk, cf, nbnd, nbnd, npw_pad);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -562,8 +635,8 @@ __device__ __forceinline__ double block_mean(const double* p, int n, int stride 
 // replayed) for one band group of one k-point (P_c, the norm and z act band by
 // band, so groups of bpc bands are independent): beta_j from the ngrp partials per k of
 // Re(r_j^H X_j) (every block re-reduces them in the same order), the group's z_j partial,
-// r_{j+1} = P_c(X_j/beta_j - beta_j v_{j-1}) formed in shared memory and written to R,
-// v_j = r_j/beta_j.  The sphere columns of r_{j+1} are then inverse-FFT'd along axis 3 by
+// r_{j+1} = P_c(X_j/beta_j - beta_j v_{j-1}) formed in shared memory and written to R (a
+// metal: keep = MetalDev::keep, the projection P'_v), v_j = r_j/beta_j.  The sphere columns of r_{j+1} are then inverse-FFT'd along axis 3 by
 // k_zinv.  grid (nks, ngrp), block 256.  smem: r [bpc][npw_pad], S [nbnd*bpc] (double
 // complex), reduction scratch.
 template <typename T>
@@ -571,7 +644,7 @@ __global__ void __launch_bounds__(256) k_ph_update(const int* __restrict__ jdev,
                                                    const double* __restrict__ part, cplx<T>* __restrict__ R,
                                                    const cplx<T>* __restrict__ X, cplx<T>* __restrict__ Vp,
                                                    const cplx<T>* __restrict__ y, const cplx<T>* __restrict__ ukq,
-                                                   Coef co, double tol) {
+                                                   Coef co, double tol, const double* __restrict__ keep) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int j = *jdev, r_upper = (j % 2 == 0) ? 1 : 0;   // step index from the device counter
   const int npw_pad = s.npw_pad, nks = s.nks;
@@ -608,14 +681,44 @@ __global__ void __launch_bounds__(256) k_ph_update(const int* __restrict__ jdev,
   __syncthreads();
   const cplx<T>* uk = ukq + (long)k * nbnd * npw_pad;
   proj_dots<T>(uk, npw_pad, rs, npw_pad, np, nbnd, bpc, cf, red);
+  if (keep) {  // a metal: only the states with c_mv = 0 are removed
+    for (int i = threadIdx.x; i < nbnd * bpc; i += blockDim.x) {
+      const int m = i / bpc;
+      const double c = keep[metal_idx(k, m, grp * bpc + i - m * bpc, nbnd)];
+      cf[i] = mk(cf[i].x * c, cf[i].y * c);
+    }
+    __syncthreads();
+  }
   subtract_projection<T>(rs, uk, cf, nbnd, bpc, npw_pad);
   for (int i = threadIdx.x; i < bpc * npw_pad; i += blockDim.x) R[base + i] = rs[i];
+}
+
+// A metal's projection coefficients of the operator for one band group of k (kept out of line:
+// the insulators' kernel keeps its registers): cf <- sp S - da Z (Z = U^H z of the input, from
+// k_metal_image), so that the output's component along a kept u_m is sqrt(c) S + (1 - c)
+// Delta Z; returns the term sum qh Re(conj(Z) <u_m|X>) that turns the partial Re(Q z, X) the
+// kernel forms into Re(z, X) (to every thread).
+static __device__ __noinline__ double metal_operator_coefs(const MetalDev md, int k, int v0, int nbnd, int bpc,
+                                                    const cplx<double>* zp, cplx<double>* cf) {
+  double corr = 0.0;
+  for (int i = threadIdx.x; i < nbnd * bpc; i += blockDim.x) {
+    const int m = i / bpc;
+    const long ci = metal_idx(k, m, v0 + i - m * bpc, nbnd);
+    const cplx<double> sv = cf[i], zv = zp[ci];
+    const double p = md.sp[ci], d = md.da[ci];
+    const cplx<double> c = mk(p * sv.x - d * zv.x, p * sv.y - d * zv.y);
+    corr += md.qh[ci] * (zv.x * (sv.x - c.x) + zv.y * (sv.y - c.y));   // Re conj(Z) <u_m|X>
+    cf[i] = c;
+  }
+  return block_sum(corr);
 }
 
 // Last stage of the operator fused with the per-k projections, for one group of bpc bands of
 // one k-point (the kinetic, KB and P_c terms act band by band): forward FFT of the group's
 // columns along axis 3 and gather of the sphere (1/N^3), + (1/2|k+Q+G|^2 - eps_vk) x, + KB
-// sum_p beta_p D_p <beta_p|x>, then P_c, the output X and the group's partial Re(x^H X).
+// sum_p beta_p D_p <beta_p|x>, then P_c, the output X and the group's partial Re(x^H X)
+// (a metal: x is the image Q z, zp holds Z = U^H z per vector; the output is the operator
+// on z through the MetalDev tables, and the partial Re(z^H X)).
 // grid (nks, nvec, ngrp), block 256.  smem: x, t [bpc][npw_pad]; coefficients; scratch.
 template <typename T, int N>
 __global__ void __launch_bounds__(256, 2) k_zfwd_proj(SphereDev s, int nbnd, int bpc, const cplx<T>* __restrict__ cbuf,
@@ -623,7 +726,8 @@ __global__ void __launch_bounds__(256, 2) k_zfwd_proj(SphereDev s, int nbnd, int
                                                    const T* __restrict__ kin, const double* __restrict__ eps,
                                                    const cplx<T>* __restrict__ ukq, const cplx<T>* __restrict__ bkq,
                                                    const double* __restrict__ dij, int nproj,
-                                                   cplx<T>* __restrict__ xout, double* __restrict__ part) {
+                                                   cplx<T>* __restrict__ xout, double* __restrict__ part,
+                                                   MetalDev md, const cplx<double>* __restrict__ zp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int npw_pad = s.npw_pad, nks = s.nks;
   const int k = blockIdx.x, vec = blockIdx.y, grp = blockIdx.z, ngrp = gridDim.z;
@@ -679,23 +783,27 @@ __global__ void __launch_bounds__(256, 2) k_zfwd_proj(SphereDev s, int nbnd, int
     __syncthreads();
   }
   small_dots<T>(uk, npw_pad, ts, npw_pad, np, nbnd, bpc, nullptr, cf, red);
+  const double corr =
+      md.sp ? metal_operator_coefs(md, k, v0, nbnd, bpc, zp + (long)vec * nks * nbnd * nbnd, cf) : 0.0;
   subtract_projection<T>(ts, uk, cf, nbnd, bpc, npw_pad);
   for (int i = threadIdx.x; i < bpc * npw_pad; i += blockDim.x) xout[base + i] = ts[i];
   small_dots<T>(xs, 0, ts, 0, bpc * npw_pad, 1, 1, nullptr, cf, red);
-  if (threadIdx.x == 0) part[((long)vec * nks + k) * ngrp + grp] = cf[0].x;
+  if (threadIdx.x == 0) part[((long)vec * nks + k) * ngrp + grp] = cf[0].x + corr;
 }
 
 // Non-Hermitian step j after the two operator applications XV = L v_j, XW = L^dag w_j, for
 // one group of bpc bands of one k-point: v_hat = P_c(XV - gamma_j v_{j-1}), w_hat =
 // P_c(XW - conj(beta_j) w_{j-1}) (stored in XV, XW), the group's partials of s = (w_hat,
-// v_hat) and of z_j = (y, v_j).  grid (nks, ngrp), block 128.
+// v_hat) and of z_j = (y, v_j) (a metal: keep = MetalDev::keep, the projection P'_v).
+// grid (nks, ngrp), block 128.
 template <typename T>
 __global__ void __launch_bounds__(128) k_nh_update(int j, int upper, int nks, int nbnd, int bpc, int npw_pad,
                                                    const int* __restrict__ npw, cplx<T>* __restrict__ XV,
                                                    cplx<T>* __restrict__ XW, const cplx<T>* __restrict__ Vp,
                                                    const cplx<T>* __restrict__ Wp, const cplx<T>* __restrict__ Vc,
                                                    const cplx<T>* __restrict__ y, const cplx<T>* __restrict__ ukq,
-                                                   Coef co, cplx<double>* __restrict__ spart) {
+                                                   Coef co, cplx<double>* __restrict__ spart,
+                                                   const double* __restrict__ keep) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx<T>* vs = reinterpret_cast<cplx<T>*>(smem_raw);          // [bpc][npw_pad]
   cplx<T>* ws = vs + bpc * npw_pad;
@@ -720,10 +828,19 @@ __global__ void __launch_bounds__(128) k_nh_update(int j, int upper, int nks, in
   }
   __syncthreads();
   const cplx<T>* uk = ukq + (long)k * nbnd * npw_pad;
-  block_dots<T>(uk, npw_pad, vs, npw_pad, np, nbnd, bpc, nullptr, cf, red);
-  subtract_projection<T>(vs, uk, cf, nbnd, bpc, npw_pad);
-  block_dots<T>(uk, npw_pad, ws, npw_pad, np, nbnd, bpc, nullptr, cf, red);
-  subtract_projection<T>(ws, uk, cf, nbnd, bpc, npw_pad);
+  for (int h = 0; h < 2; ++h) {
+    cplx<T>* xs = h ? ws : vs;
+    block_dots<T>(uk, npw_pad, xs, npw_pad, np, nbnd, bpc, nullptr, cf, red);
+    if (keep) {  // a metal: P'_v, only the states with c_mv = 0 removed
+      for (int i = threadIdx.x; i < nbnd * bpc; i += blockDim.x) {
+        const int m = i / bpc;
+        const double c = keep[metal_idx(k, m, grp * bpc + i - m * bpc, nbnd)];
+        cf[i] = mk(cf[i].x * c, cf[i].y * c);
+      }
+      __syncthreads();
+    }
+    subtract_projection<T>(xs, uk, cf, nbnd, bpc, npw_pad);
+  }
   for (int i = threadIdx.x; i < bpc * npw_pad; i += blockDim.x) {
     XV[base + i] = vs[i];
     XW[base + i] = ws[i];
@@ -865,13 +982,15 @@ static __global__ void k_first_nonfinite(const double* __restrict__ p, long n, u
 }
 
 // Packed complex rows [k][row][npw[k]] (k blocks at nrow * off[k]) -> padded [k][row][npw_pad]
-// in T, zero on the padding.  grid (nks, nrow), block 256.
+// in T, zero on the padding, each row times rscale[k][row] when given.  grid (nks, nrow),
+// block 256.
 template <typename T>
 __global__ void k_pad_rows(const double* __restrict__ src, const int* __restrict__ off, const int* __restrict__ npw,
-                           int nrow, int npw_pad, const double* __restrict__ kscale, cplx<T>* __restrict__ dst) {
+                           int nrow, int npw_pad, const double* __restrict__ rscale, cplx<T>* __restrict__ dst) {
   const int k = blockIdx.x, r = blockIdx.y, n = npw[k];
   const double* s = src + 2 * ((long)nrow * off[k] + (long)r * n);
-  const double f = kscale ? kscale[k] : 1.0;   // sqrt of the k-point weight (u_k only)
+  // u_k only: sqrt of the k-point weight times sqrt of the band's occupation (a metal)
+  const double f = rscale ? rscale[(long)k * nrow + r] : 1.0;
   cplx<T>* d = dst + ((long)k * nrow + r) * npw_pad;
   for (int g = threadIdx.x; g < npw_pad; g += blockDim.x)
     d[g] = g < n ? mk((T)(f * s[2 * g]), (T)(f * s[2 * g + 1])) : czero<T>();

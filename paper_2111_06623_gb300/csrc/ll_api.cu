@@ -497,6 +497,7 @@ int ll_footprint(const ll_system_desc* d, size_t* bytes) {
   const size_t pairs = (size_t)(d->nproj + d->nbnd) * d->nbnd;
   b += (elem / 2) * (2 * n3 + (size_t)d->nks * pq) + 8 * n3 +
        40 * (size_t)(d->max_steps + 2) * (d->nks * npk + 2) + 48 * nvec * (size_t)d->nks * npk * pairs;
+  if (d->occ_k) b += 32 * (size_t)d->nks * d->nbnd * d->nbnd;   // the metal's projector tables
   *bytes = b;
   return LL_OK;
 }

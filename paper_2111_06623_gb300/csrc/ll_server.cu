@@ -39,7 +39,7 @@ struct Job {
   // deep copy of the system (dropped when the job ends)
   std::vector<double> kcart, u_k, u_kq, eps_k, vloc, rho, beta_kq, dij, omega;
   std::vector<int> npw_k, miller_k, npw_kq, miller_kq, sym;
-  std::vector<double> kweight;
+  std::vector<double> kweight, occ_k, occ_kq, eps_kq;
   ll_system_desc desc{};
   int n_steps = 0;
   double eta = 0.0;
@@ -393,6 +393,11 @@ int ll_submit(ll_server* s, const ll_job_desc* jd, uint64_t* job_id) {
   if (jd->n_omega > 0) copy_in(j->omega, jd->omega_ev, jd->n_omega);
   if (d->kweight) copy_in(j->kweight, d->kweight, (size_t)d->nks);
   if (d->nsym > 1 && d->sym) copy_in(j->sym, d->sym, 9 * (size_t)d->nsym);
+  if (d->occ_k) {
+    copy_in(j->occ_k, d->occ_k, (size_t)d->nks * d->nbnd);
+    if (d->occ_kq) copy_in(j->occ_kq, d->occ_kq, (size_t)d->nks * d->nbnd);
+    if (d->eps_kq) copy_in(j->eps_kq, d->eps_kq, (size_t)d->nks * d->nbnd);
+  }
   j->desc = *d;
   j->desc.kcart = j->kcart.data();
   j->desc.npw_k = j->npw_k.data();
@@ -409,6 +414,9 @@ int ll_submit(ll_server* s, const ll_job_desc* jd, uint64_t* job_id) {
   j->desc.where = LL_WHERE_HOST;
   j->desc.kweight = d->kweight ? j->kweight.data() : nullptr;
   j->desc.sym = (d->nsym > 1 && d->sym) ? j->sym.data() : nullptr;
+  j->desc.occ_k = d->occ_k ? j->occ_k.data() : nullptr;
+  j->desc.occ_kq = (d->occ_k && d->occ_kq) ? j->occ_kq.data() : nullptr;
+  j->desc.eps_kq = (d->occ_k && d->eps_kq) ? j->eps_kq.data() : nullptr;
   {
     std::string err;
     if (!ll::inputs_finite(&j->desc, err)) {

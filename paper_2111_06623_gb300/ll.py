@@ -40,6 +40,7 @@ class SystemDesc(C.Structure):
         ("rho_r", _dp), ("beta_kq", _dp), ("dij", _dp), ("approx", C.c_int), ("flavour", C.c_int),
         ("precision", C.c_int), ("max_steps", C.c_int), ("where", C.c_int),
         ("kweight", _dp), ("nsym", C.c_int), ("sym", _ip),
+        ("occ_k", _dp), ("occ_kq", _dp), ("eps_kq", _dp),
     ]
 
 
@@ -144,12 +145,13 @@ def _cat_complex(blocks) -> np.ndarray:
 
 def _make_desc(*, lattice, nfft, kcart, miller_k, miller_kq, u_k, u_kq, eps_k, vloc_r, rho_r, beta_kq=None,
                dij=None, q_cart, approx="tddft", flavour="ph", precision="fp64", max_steps=1000, kweight=None,
-               sym=None):
+               sym=None, occ_k=None, occ_kq=None, eps_kq=None):
     """An ll_system_desc and the arrays it points into (keep them alive while it is used).
 
     u_k, u_kq, beta_kq, vloc_r and rho_r are host arrays (u_k, u_kq, beta_kq as lists of
     per-k (rows, npw) arrays), or all of them CUDA tensors (torch) already in the packed layout
-    of ll_system_desc: the descriptor then points at device memory (where = LL_WHERE_DEVICE)."""
+    of ll_system_desc: the descriptor then points at device memory (where = LL_WHERE_DEVICE).
+    occ_k, occ_kq, eps_kq ((nks, nbnd) host arrays): the occupations and k+Q levels of a metal."""
     nks = len(miller_k)
     dev = _on_device(u_k)
     if dev:
@@ -169,6 +171,7 @@ def _make_desc(*, lattice, nfft, kcart, miller_k, miller_kq, u_k, u_kq, eps_k, v
                                  arrs=arrs, eps_k=eps_k, dij=dij, nbnd=nbnd, nproj=nproj, q_cart=q_cart,
                                  approx=approx, flavour=flavour, precision=precision, max_steps=max_steps)
         _set_symmetry(d, k, kweight, sym)
+        _set_occupations(d, k, occ_k, occ_kq, eps_kq)
         return d, k
     k = dict(
         kcart=np.ascontiguousarray(kcart, dtype=np.float64),
@@ -199,6 +202,7 @@ def _make_desc(*, lattice, nfft, kcart, miller_k, miller_kq, u_k, u_kq, eps_k, v
     d.max_steps = int(max_steps)
     d.where = LL_WHERE_HOST
     _set_symmetry(d, k, kweight, sym)
+    _set_occupations(d, k, occ_k, occ_kq, eps_kq)
     return d, k
 
 
@@ -211,6 +215,15 @@ def _set_symmetry(d, keep, kweight, sym):
     if sym is not None and len(sym) > 1:
         keep["sym"] = np.ascontiguousarray(sym, dtype=np.int32).reshape(-1)
         d.nsym, d.sym = len(sym), _i(keep["sym"])
+
+
+def _set_occupations(d, keep, occ_k, occ_kq, eps_kq):
+    """A metal's occupations at k and k+Q and the levels at k+Q (Sec. 2.6); None: an insulator."""
+    if occ_k is None:
+        return
+    for name, a in (("occ_k", occ_k), ("occ_kq", occ_kq), ("eps_kq", eps_kq)):
+        keep[name] = np.ascontiguousarray(a, dtype=np.float64)
+        setattr(d, name, _d(keep[name]))
 
 
 def _make_desc_device(*, lattice, nfft, kcart, miller_k, miller_kq, arrs, eps_k, dij, nbnd, nproj, q_cart, approx,

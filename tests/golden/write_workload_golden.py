@@ -6,6 +6,9 @@ Cases (the FP64 oracle, RPA + ALDA kernel, Sec. 2.5 recursions on the operators 
   kb_ph    two-atom cell + KB s/p projectors, 25 Ry, 32^3, 8x8x8 k, 4 bands: pseudo-Hermitian
   kb_nh    the same cell: non-Hermitian
   sc16_ph  sixteen-atom 2x2x2 supercell + KB, 30 Ry, 48^3, 4x4x4 k, 32 bands: pseudo-Hermitian
+  metal_ph the two-atom semimetal (bare local potential), smeared occupations (Sec. 2.6),
+           10 Ry, 18^3, 4x4x4 k, 6 bands: pseudo-Hermitian
+  metal_nh the same cell: non-Hermitian
 
 Each file holds b_1 and T_{j+1,j}, T_{j,j+1}, z_j per row and, in its header, the digest of
 the ground-state bundle it was computed on (workloads.bundle_digest): the GPU parity tests
@@ -32,6 +35,8 @@ CASES = {
     "kb_ph": (w.config_kb, "ph", 1000),
     "kb_nh": (w.config_kb, "nh", 1000),
     "sc16_ph": (w.config_sc16, "ph", 100),
+    "metal_ph": (w.config_metal, "ph", 300),
+    "metal_nh": (w.config_metal, "nh", 120),
 }
 
 

@@ -9,7 +9,15 @@ def chain_from_bundle(b, approx=None, flavour="ph", precision="fp64", max_steps=
                     u_k=b.u_k, u_kq=b.u_kq, eps_k=b.eps_k, vloc_r=b.vloc_r, rho_r=b.rho_r, beta_kq=b.beta_kq,
                     dij=b.dij, q_cart=s.q_cart, approx=approx or s.approx, flavour=flavour,
                     precision=precision, max_steps=max_steps, stream=stream,
-                    kweight=getattr(b, "kweight", None), sym=getattr(b, "sym", None))
+                    kweight=getattr(b, "kweight", None), sym=getattr(b, "sym", None),
+                    **metal_args(b))
+
+
+def metal_args(b):
+    """The occupations of a metal's bundle for the descriptor (nothing for an insulator)."""
+    if getattr(b, "occ_k", None) is None:
+        return {}
+    return dict(occ_k=b.occ_k, occ_kq=b.occ_kq, eps_kq=b.eps_kq)
 
 
 def rel_batch(a, b):

@@ -70,6 +70,28 @@ def test_device_inputs_refused(lib):
     assert rc == lib.LL_EINVAL and "not a device pointer" in lib._lib.ll_last_error().decode()
 
 
+@pytest.mark.parametrize("name,bad", [("u_k", np.nan), ("u_kq", np.inf), ("vloc_r", -np.inf), ("rho_r", np.nan),
+                                      ("beta_kq", np.nan)])
+def test_host_inputs_non_finite_refused(lib, name, bad):
+    """Host inputs: the large arrays are checked on the device after their staging copy."""
+    b = w.get_bundle(w.config_kb())
+    s = b.spec
+    args = dict(lattice=s.lattice, nfft=s.nfft, kcart=b.kcart, miller_k=list(b.miller_k),
+                miller_kq=list(b.miller_kq), u_k=b.u_k, u_kq=b.u_kq, eps_k=b.eps_k, vloc_r=b.vloc_r,
+                rho_r=b.rho_r, beta_kq=b.beta_kq, dij=b.dij, q_cart=s.q_cart, max_steps=4)
+    v = args[name]
+    if isinstance(v, list):
+        v = [x.copy() for x in v]
+        v[-1].flat[-1] = bad
+    else:
+        v = np.array(v, copy=True)
+        v.flat[v.size // 2] = bad
+    args[name] = v
+    with pytest.raises(lib.LLError) as e:
+        lib.Chain(**args)
+    assert e.value.code == lib.LL_EINVAL and f"non-finite value in {name}" in str(e.value)
+
+
 def test_request_loop_takes_device_inputs(lib):
     b = w.get_bundle(w.config_small())
     wgrid = np.linspace(0.0, 40.0, 401)

@@ -92,10 +92,14 @@ def test_rejects_bad_extrapolation(ll):
         ll.spectrum(b, g, g, 270.0, [0.06, 0, 0], w, 0.1, extrapolation="linear", m_total=100)
 
 
-@pytest.mark.parametrize("name,bad", [("u_k", np.nan), ("u_kq", np.inf), ("eps_k", np.nan), ("vloc_r", -np.inf),
-                                      ("rho_r", np.nan), ("kcart", np.nan), ("q_cart", np.nan),
-                                      ("beta_kq", np.nan), ("dij", np.inf)])
+@pytest.mark.parametrize("name,bad", [("eps_k", np.nan), ("kcart", np.nan), ("q_cart", np.nan), ("dij", np.inf)])
 def test_rejects_non_finite_input(ll, name, bad):
+    """The small host arrays are checked on the host before any device work (the large ones,
+    u_k, u_kq, vloc_r, rho_r and beta_kq, on the device once staged: a GPU test covers them)."""
+    _non_finite_refused(ll, name, bad)
+
+
+def _non_finite_refused(ll, name, bad):
     b = w.get_bundle(w.config_tiny())
     args = _desc_args(b)
     if name in ("beta_kq", "dij") and len(b.dij) == 0:
@@ -111,6 +115,18 @@ def test_rejects_non_finite_input(ll, name, bad):
     with pytest.raises(ll.LLError) as e:
         ll.Chain(**args)
     assert e.value.code == ll.LL_EINVAL and f"non-finite value in {name}" in str(e.value)
+
+
+def test_rejects_bad_occupations(ll):
+    """A metal's occupations and k+Q levels are host arrays checked before any device work."""
+    b = w.get_bundle(w.config_tiny())
+    args = _desc_args(b)
+    occ = np.ones_like(b.eps_k)
+    for extra, what in ((dict(occ_k=occ, occ_kq=occ, eps_kq=np.full_like(b.eps_kq, np.nan)), "non-finite value in eps_kq"),
+                        (dict(occ_k=occ * np.nan, occ_kq=occ, eps_kq=b.eps_kq), "non-finite value in occ_k")):
+        with pytest.raises(ll.LLError) as e:
+            ll.Chain(**args, **extra)
+        assert e.value.code == ll.LL_EINVAL and what in str(e.value)
 
 
 def test_footprint_bound_orders(ll):
