@@ -659,7 +659,7 @@ class Chain : public ChainBase {
     LL_CK(cudaStreamSynchronize(st_));
     steps_ = 0;
     queued_ = 0;
-    return LL_OK;
+    return oob_check(err);
   }
 
   int lanczos(int n, double* beta, double* gamma, double* z, int* done, std::string& err) override {
@@ -794,7 +794,24 @@ class Chain : public ChainBase {
     return LL_OK;
   }
 
+  // The bounds-checked build (-DLL_CHECK): LL_EINVAL when a kernel met an index outside its
+  // table's range since the library was loaded; the plain build: always LL_OK.
+  int oob_check(std::string& err) {
+#ifdef LL_CHECK
+    int line = 0;
+    LL_CK(cudaMemcpyFromSymbolAsync(&line, g_oob_line, sizeof(int), 0, cudaMemcpyDeviceToHost, st_));
+    LL_CK(cudaStreamSynchronize(st_));
+    if (line) {
+      err = "index out of bounds in a kernel (kernel source line " + std::to_string(line) + ")";
+      return LL_EINVAL;
+    }
+#endif
+    (void)err;
+    return LL_OK;
+  }
+
   int collect(double* beta, double* gamma, double* z, int* done, std::string& err) override {
+    if (int rc = oob_check(err)) return rc;
     int herr[2];
     LL_CK(cudaMemcpyAsync(herr, err_, sizeof(herr), cudaMemcpyDeviceToHost, st_));
     LL_CK(cudaStreamSynchronize(st_));
@@ -870,6 +887,7 @@ class Chain : public ChainBase {
     if ((rc = op(1, scratch_, scratch_ + vq, (upper && approx_ != LL_APPROX_IPA) ? 0 : -1, err))) return rc;
     LL_CK(cudaMemcpyAsync(h.data(), scratch_ + vq, vq * sizeof(cplx<T>), cudaMemcpyDeviceToHost, st_));
     LL_CK(cudaStreamSynchronize(st_));
+    if ((rc = oob_check(err))) return rc;
     unpad_batch(h, hq_, nbnd_, out);
     return LL_OK;
   }

@@ -52,4 +52,19 @@ struct FastDiv {
 // host turns it into an ll_status after the call.
 enum DevErr : int { DEV_OK = 0, DEV_NOTPD = 1, DEV_BREAKDOWN = 2, DEV_BOUNDS = 3, DEV_TIMEOUT = 4 };
 
+// Bounds-checked build (-DLL_CHECK, libll_check.so): every index the kernels take from a
+// sphere or map table is tested before its access; a failing test records the source line
+// in g_oob_line (the first one wins), the access is skipped, and the host reports
+// LL_EINVAL after the call.  The plain build compiles the tests away.
+#ifdef LL_CHECK
+static __device__ int g_oob_line;
+__device__ __forceinline__ bool ll_inb(bool ok, int line) {
+  if (!ok) atomicCAS(&g_oob_line, 0, line);
+  return ok;
+}
+#define LL_INB(cond) ::ll::ll_inb((cond), __LINE__)
+#else
+#define LL_INB(cond) true
+#endif
+
 }  // namespace ll

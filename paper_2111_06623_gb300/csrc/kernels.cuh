@@ -50,9 +50,10 @@ __global__ void __launch_bounds__(128) k_zinv(SphereDev s, const cplx<T>* __rest
 #pragma unroll
     for (int p = 0; p < N; ++p) {
       const int i = wrapn<N>(p - cl.z);
-      a[p] = (i < cl.w) ? src[i] : czero<T>();
+      a[p] = (i < cl.w && LL_INB(st >= 0 && st + i < s.npw_pad)) ? src[i] : czero<T>();
     }
     fft_line<T, N, +1>(a);
+    if (!LL_INB(c < cb_ncol)) continue;
     cplx<T>* dst = cbuf + o * (long)N * cb_ncol + c;
 #pragma unroll
     for (int p = 0; p < N; ++p) dst[(long)p * cb_ncol] = a[p];
@@ -171,7 +172,7 @@ __global__ void __launch_bounds__(128, N > 36 ? 2 : (MODE == XY_PASS1_DENS ? 3 :
 #pragma unroll
         for (int p = 0; p < N; ++p) {
           const int j = wrapn<N>(p - rw.z);
-          l[p] = (j < rw.w) ? cs[j] : czero<T>();
+          l[p] = (j < rw.w && LL_INB(rw.y >= 0 && rw.y + j < a.cb_ncol)) ? cs[j] : czero<T>();
         }
         fft_line<T, N, +1>(l);
         cplx<T>* ys = Ys + (b * s.nrow_max + r) * NP;
@@ -196,7 +197,7 @@ __global__ void __launch_bounds__(128, N > 36 ? 2 : (MODE == XY_PASS1_DENS ? 3 :
 #pragma unroll
         for (int p = 0; p < N; ++p) {
           const int r = wrapn<N>(p - m2min);
-          l[p] = (r < nr) ? Ys[(b * s.nrow_max + r) * NP + j1] : czero<T>();
+          l[p] = (r < nr && LL_INB(r < s.nrow_max)) ? Ys[(b * s.nrow_max + r) * NP + j1] : czero<T>();
         }
         fft_line<T, N, +1>(l);
         if (MODE == XY_STORE) {
@@ -219,7 +220,7 @@ __global__ void __launch_bounds__(128, N > 36 ? 2 : (MODE == XY_PASS1_DENS ? 3 :
 #pragma unroll
       for (int p = 0; p < N; ++p) {
         const int r = wrapn<N>(p - m2min);
-        if (r < nr) Ys[(b * s.nrow_max + r) * NP + j1] = l[p];
+        if (r < nr && LL_INB(r < s.nrow_max)) Ys[(b * s.nrow_max + r) * NP + j1] = l[p];
       }
     }
     __syncthreads();
@@ -239,7 +240,7 @@ __global__ void __launch_bounds__(128, N > 36 ? 2 : (MODE == XY_PASS1_DENS ? 3 :
 #pragma unroll
       for (int p = 0; p < N; ++p) {
         const int j = wrapn<N>(p - rw.z);
-        if (j < rw.w) cs[j] = l[p];
+        if (j < rw.w && LL_INB(rw.y >= 0 && rw.y + j < a.cb_ncol)) cs[j] = l[p];
       }
     }
     __syncthreads();
@@ -756,16 +757,18 @@ __global__ void __launch_bounds__(256, 2) k_zfwd_proj(SphereDev s, int nbnd, int
   for (int it = threadIdx.x; it < bpc * nc; it += blockDim.x) {
     const int v = it / nc, c = it - v * nc;
     const int4 cl = s.col[k * s.ncol_max + c];
+    if (!LL_INB(c < cb_ncol)) continue;
     const cplx<T>* src = cbuf + (o0 + v) * (long)N * cb_ncol + c;
     cplx<T> a[N];
 #pragma unroll
     for (int p = 0; p < N; ++p) a[p] = src[(long)p * cb_ncol];
     fft_line<T, N, -1>(a);
-    cplx<T>* dst = ts + v * npw_pad + s.colstart[k * s.ncol_max + c];
+    const int st = s.colstart[k * s.ncol_max + c];
+    cplx<T>* dst = ts + v * npw_pad + st;
 #pragma unroll
     for (int p = 0; p < N; ++p) {
       const int i = wrapn<N>(p - cl.z);
-      if (i < cl.w) dst[i] = dst[i] + a[p] * scale;
+      if (i < cl.w && LL_INB(st >= 0 && st + i < npw_pad)) dst[i] = dst[i] + a[p] * scale;
     }
   }
   __syncthreads();
@@ -942,7 +945,7 @@ __global__ void k_gather_y(int nks, int nbnd, int npw_pad_q, int npw_pad_k, cons
     const int v = i / npw_pad_q, g = i - v * npw_pad_q;
     const int m = map[(long)k * npw_pad_q + g];
     y[((long)k * nbnd + v) * npw_pad_q + g] =
-        (m >= 0) ? uk[((long)k * nbnd + v) * npw_pad_k + m] : czero<T>();
+        (m >= 0 && LL_INB(m < npw_pad_k)) ? uk[((long)k * nbnd + v) * npw_pad_k + m] : czero<T>();
   }
 }
 

@@ -166,6 +166,7 @@ __global__ void __launch_bounds__(kLines) k_sp_zfwd(SphereDev s, int nbnd, const
   const int v = it / nc, c = it - v * nc;
   const long o = ((long)vec * nks + k) * nbnd + v;
   const int4 cl = s.col[k * s.ncol_max + c];
+  if (!LL_INB(c < cb_ncol)) return;
   const cplx<T>* src = cbuf + o * (long)N * cb_ncol + c;
   cplx<T> a[N];
 #pragma unroll
@@ -180,7 +181,7 @@ __global__ void __launch_bounds__(kLines) k_sp_zfwd(SphereDev s, int nbnd, const
 #pragma unroll
   for (int p = 0; p < N; ++p) {
     const int i = wrapn<N>(p - cl.z);
-    if (i < cl.w) t[i] = x[i] * (kn[i] - ev) + a[p] * scale;
+    if (i < cl.w && LL_INB(st >= 0 && st + i < npw_pad)) t[i] = x[i] * (kn[i] - ev) + a[p] * scale;
   }
 }
 

@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(4 * N, (sizeof(T) == 4 ? (N > 36 ? 3 : 4) : 2)
 #pragma unroll
         for (int m = 0; m < H; ++m) {
           const int j = wrapn<N>(2 * m + h - rw.z);
-          l[m] = (j < rw.w) ? cs[j] : czero<T>();
+          l[m] = (j < rw.w && LL_INB(rw.y >= 0 && rw.y + j < a.cb_ncol)) ? cs[j] : czero<T>();
         }
         fft_pair_dit<T, H, +1>(l, h, pmask);
         cplx<T>* ys = Ys + (b * s.nrow_max + r) * NP + H * h;
@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(4 * N, (sizeof(T) == 4 ? (N > 36 ? 3 : 4) : 2)
 #pragma unroll
         for (int m = 0; m < H; ++m) {
           const int r = wrapn<N>(2 * m + h - m2min);
-          l[m] = (r < nr) ? Ys[(b * s.nrow_max + r) * NP + j1] : czero<T>();
+          l[m] = (r < nr && LL_INB(r < s.nrow_max)) ? Ys[(b * s.nrow_max + r) * NP + j1] : czero<T>();
         }
         fft_pair_dit<T, H, +1>(l, h, pmask);
         if (MODE == XY_STORE) {
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(4 * N, (sizeof(T) == 4 ? (N > 36 ? 3 : 4) : 2)
 #pragma unroll
       for (int m = 0; m < H; ++m) {
         const int r = wrapn<N>(2 * m + h - m2min);
-        if (r < nr) Ys[(b * s.nrow_max + r) * NP + j1] = l[m];
+        if (r < nr && LL_INB(r < s.nrow_max)) Ys[(b * s.nrow_max + r) * NP + j1] = l[m];
       }
     }
     __syncthreads();
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(4 * N, (sizeof(T) == 4 ? (N > 36 ? 3 : 4) : 2)
 #pragma unroll
       for (int m = 0; m < H; ++m) {
         const int j = wrapn<N>(2 * m + h - rw.z);
-        if (j < rw.w) cs[j] = l[m];
+        if (j < rw.w && LL_INB(rw.y >= 0 && rw.y + j < a.cb_ncol)) cs[j] = l[m];
       }
     }
     __syncthreads();

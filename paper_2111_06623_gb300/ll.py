@@ -13,7 +13,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libll.so")
+# LL_LIBRARY in the environment selects another build of the same library (the bounds-checked
+# libll_check.so of build_library(check=True)); default: the in-tree libll.so
+LIB_PATH = os.environ.get("LL_LIBRARY") or os.path.join(_HERE, "libll.so")
 
 LL_OK, LL_EINVAL, LL_ENOMEM, LL_EBREAKDOWN, LL_ENOTPD, LL_ETIMEOUT, LL_ECUDA = 0, 1, 2, 3, 4, 5, 6
 LL_PENDING, LL_ENOTFOUND, LL_EUNSUPPORTED, LL_ECANCELED = 7, 8, 9, 10
@@ -62,7 +64,7 @@ def _dev_ptr(t, what: str):
 
 def _load():
     if not os.path.exists(LIB_PATH):
-        raise ImportError(f"libll.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+        raise ImportError(f"the library is not built ({LIB_PATH}); run __graft_entry__.build()")
     lib = C.CDLL(LIB_PATH)
     vp = C.c_void_p
     sig = {
