@@ -7,6 +7,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <future>
+#include <thread>
 #include <array>
 #include <cmath>
 #include <map>
@@ -151,7 +153,9 @@ static inline bool build_sphere(int nks, const int* npw, const int* mil, int n, 
   h.npw_pad = round_up(maxnpw, 4);
   std::vector<std::vector<int4>> cols(nks), rows(nks);
   std::vector<std::vector<int>> starts(nks);
-  for (int k = 0; k < nks; ++k) {
+  std::vector<const char*> kerr(nks, nullptr);
+  // the tables of one sphere (independent per k: built on several host threads)
+  auto one = [&](int k) -> const char* {
     const int* m = mil + 3L * h.off[k];
     int lo[3] = {m[0], m[1], m[2]}, hi[3] = {m[0], m[1], m[2]};
     for (int i = 0; i < npw[k]; ++i) {
@@ -160,16 +164,16 @@ static inline bool build_sphere(int nks, const int* npw, const int* mil, int n, 
         const int* p = m + 3 * (i - 1);
         const int* q = m + 3 * i;
         const bool less = p[0] < q[0] || (p[0] == q[0] && (p[1] < q[1] || (p[1] == q[1] && p[2] < q[2])));
-        if (!less) { err = "Miller indices of a sphere are not strictly lexicographic"; return false; }
+        if (!less) return "Miller indices of a sphere are not strictly lexicographic";
       }
     }
     for (int a = 0; a < 3; ++a)
-      if (hi[a] - lo[a] >= n) { err = "a plane-wave sphere does not fit the FFT grid"; return false; }
+      if (hi[a] - lo[a] >= n) return "a plane-wave sphere does not fit the FFT grid";
     int i = 0;
     while (i < npw[k]) {
       int j = i;
       while (j < npw[k] && m[3 * j] == m[3 * i] && m[3 * j + 1] == m[3 * i + 1]) {
-        if (j > i && m[3 * j + 2] != m[3 * (j - 1) + 2] + 1) { err = "a sphere column is not a contiguous run"; return false; }
+        if (j > i && m[3 * j + 2] != m[3 * (j - 1) + 2] + 1) return "a sphere column is not a contiguous run";
         ++j;
       }
       cols[k].push_back(make_int4(m[3 * i], m[3 * i + 1], m[3 * i + 2], j - i));
@@ -194,14 +198,29 @@ static inline bool build_sphere(int nks, const int* npw, const int* mil, int n, 
     while (c < nc) {
       int d = c;
       while (d < nc && cols[k][d].y == cols[k][c].y) {
-        if (d > c && cols[k][d].x != cols[k][d - 1].x + 1) { err = "a sphere row is not a contiguous run"; return false; }
+        if (d > c && cols[k][d].x != cols[k][d - 1].x + 1) return "a sphere row is not a contiguous run";
         ++d;
       }
-      if (!rows[k].empty() && cols[k][c].y != rows[k].back().x + 1) { err = "sphere rows are not consecutive"; return false; }
+      if (!rows[k].empty() && cols[k][c].y != rows[k].back().x + 1) return "sphere rows are not consecutive";
       rows[k].push_back(make_int4(cols[k][c].y, c, cols[k][c].x, d - c));
       c = d;
     }
-    h.ncol_max = std::max(h.ncol_max, nc);
+    return nullptr;
+  };
+  const int nth = std::max(1, std::min({(int)std::thread::hardware_concurrency(), 16, nks / 32}));
+  if (nth > 1) {
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nth; ++t)
+      pool.emplace_back([&, t] {
+        for (int k = t; k < nks; k += nth) kerr[k] = one(k);
+      });
+    for (auto& th : pool) th.join();
+  } else {
+    for (int k = 0; k < nks; ++k) kerr[k] = one(k);
+  }
+  for (int k = 0; k < nks; ++k) {   // the first failing k-point's message, as a serial build gives
+    if (kerr[k]) { err = kerr[k]; return false; }
+    h.ncol_max = std::max(h.ncol_max, (int)cols[k].size());
     h.nrow_max = std::max(h.nrow_max, (int)rows[k].size());
   }
   h.ncol.resize(nks);
@@ -242,20 +261,32 @@ template <int N, int MODE> struct BO {
   static constexpr int v = (MODE == XY_PASS1_DENS || MODE == XY_PASS2) ? 256 / N : 384 / N;
 };
 
-// FNV-1a (64 bit) over the inputs that determine the u_{vk}(r) grids: the precision, the grid
+// An FNV-1a-style 64-bit hash over the inputs that determine the u_{vk}(r) grids: the precision, the grid
 // side, the k-point and band counts, the spheres of k, the u_k coefficients and the weights
 // folded into them (host arrays).
 static inline uint64_t ground_state_hash(const ll_system_desc* d) {
+  const uint64_t P = 1099511628211ull;
   uint64_t h = 1469598103934665603ull;
-  auto feed = [&](const void* p, size_t n) {   // FNV-1a over 8-byte words, then the tail bytes
+  // FNV-1a step over 8-byte words in four interleaved lanes (independent multiply chains),
+  // folded into h per array, then the tail words and bytes
+  auto feed = [&](const void* p, size_t n) {
     const unsigned char* c = static_cast<const unsigned char*>(p);
+    uint64_t l[4] = {h, h ^ 0x9e3779b97f4a7c15ull, h ^ 0xc2b2ae3d27d4eb4full, h ^ 0x165667b19e3779f9ull};
     size_t i = 0;
+    for (; i + 32 <= n; i += 32)
+      for (int q = 0; q < 4; ++q) {
+        uint64_t wv;
+        memcpy(&wv, c + i + 8 * q, 8);
+        l[q] = (l[q] ^ wv) * P;
+      }
+    h = l[0];
+    for (int q = 1; q < 4; ++q) h = (h ^ l[q]) * P;
     for (; i + 8 <= n; i += 8) {
       uint64_t wv;
       memcpy(&wv, c + i, 8);
-      h = (h ^ wv) * 1099511628211ull;
+      h = (h ^ wv) * P;
     }
-    for (; i < n; ++i) h = (h ^ c[i]) * 1099511628211ull;
+    for (; i < n; ++i) h = (h ^ c[i]) * P;
   };
   feed(&d->precision, sizeof(int));
   feed(&d->nfft, sizeof(int));
@@ -318,6 +349,9 @@ class Chain : public ChainBase {
     if (!inputs_finite(d, err, false)) return LL_EINVAL;
     if (d->where != LL_WHERE_HOST && d->where != LL_WHERE_DEVICE) { err = "bad where"; return LL_EINVAL; }
     const bool dev_in = d->where == LL_WHERE_DEVICE;
+    // the ground-state hash (host inputs) on another host thread while the device work runs
+    std::future<uint64_t> hash_f;
+    if (!dev_in) hash_f = std::async(std::launch::async, [d] { return ground_state_hash(d); });
     // k-point weights (stars of the small group of Q) and the group on the grid (Sec. 2.6)
     kscale_.assign(nks_, 1.0);
     if (d->kweight) {
@@ -459,7 +493,7 @@ class Chain : public ChainBase {
         }
       release(first);
     }
-    gs_hash_ = dev_in ? 0 : ground_state_hash(d);
+    gs_hash_ = dev_in ? 0 : hash_f.get();
     if (donor_) {
       if (dev_in) { err = "grids are shared between chains of host inputs only"; return LL_EINVAL; }
       if (gs_hash_ != donor_->gs_hash_ || donor_->N_ != N_ || donor_->nks_ != nks_ || donor_->nbnd_ != nbnd_) {

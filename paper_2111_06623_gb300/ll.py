@@ -141,7 +141,14 @@ def _i(a):
     return a.ctypes.data_as(_ip)
 
 
+def _is_packed(a) -> bool:
+    """A host array already in the descriptor's packed layout (1-D complex128, contiguous)."""
+    return isinstance(a, np.ndarray) and a.ndim == 1 and a.dtype == np.complex128 and a.flags.c_contiguous
+
+
 def _cat_complex(blocks) -> np.ndarray:
+    if _is_packed(blocks):
+        return blocks                      # used in place (no copy)
     return np.ascontiguousarray(np.concatenate([np.ascontiguousarray(b, dtype=np.complex128).ravel() for b in blocks]))
 
 
@@ -151,12 +158,17 @@ def _make_desc(*, lattice, nfft, kcart, miller_k, miller_kq, u_k, u_kq, eps_k, v
     """An ll_system_desc and the arrays it points into (keep them alive while it is used).
 
     u_k, u_kq, beta_kq, vloc_r and rho_r are host arrays (u_k, u_kq, beta_kq as lists of
-    per-k (rows, npw) arrays), or all of them CUDA tensors (torch) already in the packed layout
-    of ll_system_desc: the descriptor then points at device memory (where = LL_WHERE_DEVICE).
+    per-k (rows, npw) arrays, or each one 1-D complex128 array already in the packed layout of
+    ll_system_desc, used in place: pinned host memory then copies at full link speed), or all
+    of them CUDA tensors (torch) in the packed layout: the descriptor then points at device
+    memory (where = LL_WHERE_DEVICE).
     occ_k, occ_kq, eps_kq ((nks, nbnd) host arrays): the occupations and k+Q levels of a metal."""
     nks = len(miller_k)
     dev = _on_device(u_k)
     if dev:
+        nbnd = int(np.shape(eps_k)[1])
+        nproj = int(len(dij)) if dij is not None and beta_kq is not None else 0
+    elif _is_packed(u_k):
         nbnd = int(np.shape(eps_k)[1])
         nproj = int(len(dij)) if dij is not None and beta_kq is not None else 0
     else:
@@ -188,6 +200,10 @@ def _make_desc(*, lattice, nfft, kcart, miller_k, miller_kq, u_k, u_kq, eps_k, v
         beta_kq=_cat_complex(beta_kq) if nproj else np.zeros(2),
         dij=np.ascontiguousarray(dij if nproj else np.zeros(1), dtype=np.float64),
     )
+    sk, sq = int(k["npw_k"].sum()), int(k["npw_kq"].sum())
+    for name, rows, n in (("u_k", nbnd, sk), ("u_kq", nbnd, sq), ("beta_kq", nproj, sq)):
+        if (name != "beta_kq" or nproj) and k[name].size != rows * n:
+            raise ValueError(f"{name}: {k[name].size} coefficients, the spheres and rows need {rows * n}")
     d = SystemDesc()
     for i in range(3):
         for j in range(3):

@@ -51,6 +51,29 @@ def test_device_inputs_match_host_inputs(lib, cell, precision, flavour):
         assert np.array_equal(a, c)
 
 
+def test_packed_host_inputs_match_lists(lib):
+    """Host inputs already packed (pinned memory here) build the chain the per-k lists build."""
+    b = w.get_bundle(w.config_kb())
+    ref = chain_from_bundle(b, precision="fp32", max_steps=20).lanczos(20)
+    packed = {}
+    for name in ("u_k", "u_kq", "beta_kq"):
+        blocks = getattr(b, name)
+        n = sum(x.size for x in blocks)
+        t = torch.empty(2 * n, dtype=torch.float64, pin_memory=True)
+        a = t.numpy().view(np.complex128)
+        a[:] = np.concatenate([x.ravel() for x in blocks])
+        packed[name] = (a, t)
+    s = b.spec
+    ch = lib.Chain(lattice=s.lattice, nfft=s.nfft, kcart=b.kcart, miller_k=b.miller_k, miller_kq=b.miller_kq,
+                   u_k=packed["u_k"][0], u_kq=packed["u_kq"][0], eps_k=b.eps_k, vloc_r=b.vloc_r, rho_r=b.rho_r,
+                   beta_kq=packed["beta_kq"][0], dij=b.dij, q_cart=s.q_cart, approx=s.approx, precision="fp32",
+                   max_steps=20)
+    got = ch.lanczos(20)
+    ch.close()
+    for a, c in zip(got, ref):
+        assert np.array_equal(a, c)
+
+
 def test_device_inputs_refused(lib):
     b = w.get_bundle(w.config_small())
     sysd = _device_system(b, max_steps=4)

@@ -140,3 +140,15 @@ def test_footprint_bound_orders(ll):
     assert fp(flavour="ph") < fp(flavour="nh")
     kb = _desc_args(w.get_bundle(w.config_kb()))
     assert 1 << 20 < ll.footprint(**{**kb, "precision": "fp32", "max_steps": 1000}) < 8 << 30
+
+
+def test_packed_host_arrays_checked(ll):
+    """u_k, u_kq, beta_kq may come packed (1-D complex128 in the descriptor's layout, used in
+    place); a packed array of the wrong length is refused before the library is called."""
+    b = w.get_bundle(w.config_tiny())
+    args = _desc_args(b)
+    packed = np.concatenate([x.ravel() for x in b.u_k]).astype(np.complex128)
+    d, keep = ll._make_desc(**dict(args, u_k=packed))
+    assert keep["u_k"] is packed                     # no copy
+    with pytest.raises(ValueError):
+        ll._make_desc(**dict(args, u_k=packed[:-1]))
