@@ -537,7 +537,7 @@ def main():
                     help="cell of the timed chain with --headline-only (profiling); the benchmark line is the KB workload")
     ap.add_argument("--headline-only", action="store_true",
                     help="time the FP32 chain on the KB workload only (no other legs): for profiling")
-    ap.add_argument("--batch-small", type=int, default=16, help="chains of the two-atom cell in the many-Q batch")
+    ap.add_argument("--batch-small", type=int, default=64, help="chains of the two-atom cell in the many-Q batch")
     ap.add_argument("--batch-cubic", type=int, default=2, help="chains of the eight-atom cell in the many-Q batch")
     ap.add_argument("--batch-sc16", type=int, default=1, help="chains of the sixteen-atom cell in the batch (0 or 1)")
     args = ap.parse_args()

@@ -645,9 +645,9 @@ class Chain : public ChainBase {
     }
     // y = P_c (u_k on sphere(k+Q))   (Eq. 28).  A metal: Q^-1 of the start P_{c,v} u_k (u_k with
     // sqrt(f_v) folded in), i.e. Q P'_v u_k
-    k_gather_y<T><<<nks_, 128, 0, st_>>>(nks_, nbnd_, pq, pk, map_, uk_, y_);
-    k_project<T><<<dim3(nks_, 1), 128, 0, st_>>>(nks_, nbnd_, pq, dq_.npw, ukq_, y_, md_.keep);
-    if (metal_) k_project<T><<<dim3(nks_, 1), 128, 0, st_>>>(nks_, nbnd_, pq, dq_.npw, ukq_, y_, md_.qh);
+    k_gather_y<T><<<dim3(nks_, nbnd_), 128, 0, st_>>>(nks_, nbnd_, pq, pk, map_, uk_, y_);
+    k_project<T><<<dim3(nks_, 1, nbnd_), 128, 0, st_>>>(nks_, nbnd_, pq, dq_.npw, ukq_, y_, md_.keep);
+    if (metal_) k_project<T><<<dim3(nks_, 1, nbnd_), 128, 0, st_>>>(nks_, nbnd_, pq, dq_.npw, ukq_, y_, md_.qh);
     LL_CK(cudaGetLastError());
     // u_{vk}(r) grids: columns of sphere(k), then the planes (unless a chain of the same ground
     // state lends its grids)

@@ -557,8 +557,9 @@ __device__ __forceinline__ double block_sum(double v) {
 }
 
 // x <- P_c x for every orbital of k (in place); with coef ([nks][nbnd][nbnd], m-major), the
-// component along u_m of band v is removed with weight coef[k][m][v] instead of 1.
-// grid (nks, nvec), block 128.
+// component along u_m of band v is removed with weight coef[k][m][v] instead of 1.  The bands
+// of k are independent: grid (nks, nvec, nsplit) with nsplit dividing nbnd, each CTA taking
+// nbnd/nsplit of them.  block 128.
 template <typename T>
 __global__ void __launch_bounds__(128) k_project(int nks, int nbnd, int npw_pad, const int* __restrict__ npw,
                                                  const cplx<T>* __restrict__ ukq, cplx<T>* __restrict__ x,
@@ -566,17 +567,19 @@ __global__ void __launch_bounds__(128) k_project(int nks, int nbnd, int npw_pad,
   __shared__ cplx<double> cf[32 * 32];
   __shared__ double red[4 * 16];
   const int k = blockIdx.x, vec = blockIdx.y;
-  const long base = ((long)vec * nks + k) * nbnd * npw_pad;
+  const int nv = nbnd / gridDim.z, v0 = blockIdx.z * nv;
+  const long base = (((long)vec * nks + k) * nbnd + v0) * npw_pad;
   const cplx<T>* uk = ukq + (long)k * nbnd * npw_pad;
-  block_dots<T>(uk, npw_pad, x + base, npw_pad, npw[k], nbnd, nbnd, nullptr, cf, red);
+  block_dots<T>(uk, npw_pad, x + base, npw_pad, npw[k], nbnd, nv, nullptr, cf, red);
   if (coef) {
-    for (int i = threadIdx.x; i < nbnd * nbnd; i += blockDim.x) {
-      const double c = coef[(long)k * nbnd * nbnd + i];
+    for (int i = threadIdx.x; i < nbnd * nv; i += blockDim.x) {
+      const int m = i / nv;
+      const double c = coef[((long)k * nbnd + m) * nbnd + v0 + i - m * nv];
       cf[i] = mk(cf[i].x * c, cf[i].y * c);
     }
     __syncthreads();
   }
-  subtract_projection<T>(x + base, uk, cf, nbnd, nbnd, npw_pad);
+  subtract_projection<T>(x + base, uk, cf, nbnd, nv, npw_pad);
 }
 
 // A metal's image of a batch vector z for the FFT pipeline: img = Q z = z - U (qh Z) and
@@ -937,12 +940,12 @@ static __global__ void k_intersection_map(int nks, const int* __restrict__ off_k
 }
 
 // y_{vk}(G) = u_{vk}(G) where G is also in sphere(k), else 0 (projection follows).
+// grid (nks, nbnd), block 128.
 template <typename T>
 __global__ void k_gather_y(int nks, int nbnd, int npw_pad_q, int npw_pad_k, const int* __restrict__ map,
                            const cplx<T>* __restrict__ uk, cplx<T>* __restrict__ y) {
-  const int k = blockIdx.x;
-  for (int i = threadIdx.x; i < nbnd * npw_pad_q; i += blockDim.x) {
-    const int v = i / npw_pad_q, g = i - v * npw_pad_q;
+  const int k = blockIdx.x, v = blockIdx.y;
+  for (int g = threadIdx.x; g < npw_pad_q; g += blockDim.x) {
     const int m = map[(long)k * npw_pad_q + g];
     y[((long)k * nbnd + v) * npw_pad_q + g] =
         (m >= 0 && LL_INB(m < npw_pad_k)) ? uk[((long)k * nbnd + v) * npw_pad_k + m] : czero<T>();

@@ -173,3 +173,36 @@ def test_metal_occupations_checked(lib, metal):
     with pytest.raises(ll.LLError) as e:
         ll.Chain(**base, occ_k=bad, occ_kq=metal.occ_kq, eps_kq=metal.eps_kq)
     assert e.value.code == 1
+
+
+def test_metal_job_through_the_request_loop(lib, metal):
+    """A metal submitted to the request loop (occupations deep-copied at submit) beside an
+    insulator gives the chain's own coefficients, bit for bit."""
+    from .helpers import metal_args
+    n = 60
+    ref = chain_from_bundle(metal, precision="fp32", max_steps=n).lanczos(n)
+    small = w.get_bundle(w.config_small())
+    srv = lib.Server(hbm_budget_bytes=8 << 30, max_slots=2, chunk=16)
+
+    def system(b, **extra):
+        s = b.spec
+        return dict(lattice=s.lattice, nfft=s.nfft, kcart=b.kcart, miller_k=b.miller_k, miller_kq=b.miller_kq,
+                    u_k=b.u_k, u_kq=b.u_kq, eps_k=b.eps_k, vloc_r=b.vloc_r, rho_r=b.rho_r, beta_kq=b.beta_kq,
+                    dij=b.dij, q_cart=s.q_cart, approx=s.approx, precision="fp32", max_steps=n, **extra)
+
+    wgrid = np.linspace(0.0, 40.0, 401)
+    ids = [srv.submit(n, wgrid, 0.1, **system(metal, **metal_args(metal))), srv.submit(n, wgrid, 0.1, **system(small))]
+    import time
+    t0, res = time.time(), {}
+    while len(res) < 2:
+        for i in ids:
+            if i not in res:
+                st, r = srv.poll(i)
+                if st in (lib.JOB_DONE, lib.JOB_FAILED):
+                    res[i] = (st, r)
+        assert time.time() - t0 < 300
+        time.sleep(0.01)
+    srv.close()
+    st, out = res[ids[0]]
+    assert st == lib.JOB_DONE and out["steps_done"] == n, out.get("error")
+    assert np.array_equal(out["beta"], ref[0]) and np.array_equal(out["z"], ref[2])
