@@ -87,7 +87,7 @@ def test_metal_fp32_window():
     recursion: with rounding of FP32 size at every step the oracle's own loss function of the
     first 80 coefficients moves by less than 1e-3 (measured 1e-5 to 1e-4 over two noise seeds),
     that of the first 100 by more than 1e-3 (measured 4e-3 to 2e-2), so FP32 parity on this
-    cell is judged on the first 80 coefficients (for the insulating two-atom cell the same
+    cell is compared on the first 80 coefficients (for the insulating two-atom cell the same
     noise moves the 100-coefficient loss function by ~5e-4)."""
     from workloads.cells import config_metal
     b = w.get_bundle(config_metal())
