@@ -100,8 +100,8 @@ typedef struct {
    * LL_METAL_CMIN), the Lanczos vectors keep the states with c_mv > 0, and the scalar
    * products carry the metric weight 1/c_mv on them.  Every state of k+Q beyond the nbnd given
    * must lie above every occupied level of k.  The response is for Q + G != 0 (no Fermi-level
-   * shift).  NULL: an insulator (every band full).  Fused per-k path only (LL_EUNSUPPORTED
-   * where the bands of a k-point do not fit one CTA's shared memory).                       */
+   * shift).  NULL: an insulator (every band full).  Both per-k paths (fused, and split
+   * over plane-wave chunks with the tensor-core projections) take metals.                   */
   const double* occ_k;
   const double* occ_kq;
   const double* eps_kq;

@@ -538,10 +538,6 @@ class Chain : public ChainBase {
       // the chunked path also where the band groups are small: per-group CTAs would read the
       // projectors and U_{k+Q} once per group (32 times per k on the 16-atom cell)
       split_ = best == 0 || 4 * best < nbnd_ || (env && env[0] == '1' && env[1] == 0);
-      if (split_ && metal_) {
-        err = "a metal needs the bands of a k-point in one CTA (the fused per-k path)";
-        return LL_EUNSUPPORTED;
-      }
       nchunk_ = split_ ? (pq + kChunk - 1) / kChunk : 1;
       npk_ = split_ ? nchunk_ : ngrp_;
       // FP32 path: the split path's dot blocks on the tensor cores (tcproj.cuh) where their
@@ -571,7 +567,9 @@ class Chain : public ChainBase {
       return rc;
     if (metal_) {
       const long sz = (long)nks_ * nbnd_ * nbnd_;
-      if ((rc = alloc(&mc_, 4 * sz)) || (rc = alloc(&img_, nvec_ * vq)) || (rc = alloc(&zp_, nvec_ * sz))) return rc;
+      if ((rc = alloc(&mc_, 4 * sz)) || (rc = alloc(&img_, nvec_ * vq)) || (rc = alloc(&zp_, nvec_ * sz)) ||
+          (rc = alloc(&mcorr_, (long)nvec_ * nks_)))
+        return rc;
       LL_CK(cudaMemcpyAsync(mc_, mtab_.data(), 4 * sz * sizeof(double), cudaMemcpyHostToDevice, st_));
       md_ = MetalDev{mc_, mc_ + sz, mc_ + 2 * sz, mc_ + 3 * sz};
     }
@@ -751,7 +749,7 @@ class Chain : public ChainBase {
                                                                   tc_u2_ ? 0 : 1);
           if (tc_u2_ && (rc = tc_dots<TC_U2>(1, tc_nb_u_, nullptr, XV(), XW(), nullptr, sp_s_, err))) return rc;
           k_sp_nh_proj<T><<<dim3(nks_, nchunk_), 256, 0, st_>>>(nks_, nbnd_, pq, dq_.npw, nchunk_, XV(), XW(), ukq_,
-                                                                sp_s_, spart_);
+                                                                sp_s_, spart_, md_.keep);
           prof_.count(LL_PROF_UPDATE, 1);
         } else {
           if ((rc = set_smem(k_nh_update<T>, smem_nh, err))) return rc;
@@ -793,14 +791,14 @@ class Chain : public ChainBase {
   }
   // launch counts of a replayed step (the same kernels as ph_step)
   void count_step(int j) {
-    prof_.count(LL_PROF_ZINV, (split_ ? 4 : 2) + (metal_ ? 1 : 0));
+    prof_.count(LL_PROF_ZINV, (split_ ? 4 : 2) + (metal_ ? (split_ ? 3 : 1) : 0));
     prof_.count(LL_PROF_UPDATE);
     prof_.count(LL_PROF_XY1);
     if (j % 2 == 1 && approx_ != LL_APPROX_IPA) {
       prof_.count(LL_PROF_HXC, 3);
       prof_.count(LL_PROF_XY2);
     }
-    prof_.count(LL_PROF_ZFWD, split_ ? 4 : 1);
+    prof_.count(LL_PROF_ZFWD, split_ ? 4 + (metal_ ? 1 : 0) : 1);
   }
   int capture_step(int j, std::string& err) {
     cudaGraph_t g = nullptr;
@@ -971,7 +969,9 @@ class Chain : public ChainBase {
   int op(int nvec, const cplx<T>* in, cplx<T>* out, int dens_vec, std::string& err) {
     int rc;
     const int e0 = prof_.mark(st_);
-    if ((rc = launch_zinv(dq_, metal_image(in, nvec), nvec))) { err = "zinv launch"; return rc; }
+    const cplx<T>* zin = metal_image(in, nvec);
+    if (!zin) { err = "metal image launch"; return LL_ECUDA; }
+    if ((rc = launch_zinv(dq_, zin, nvec))) { err = "zinv launch"; return rc; }
     prof_.count(LL_PROF_ZINV);
     prof_.span(LL_PROF_ZINV, e0, prof_.mark(st_));
     return op_rest(nvec, in, out, dens_vec, err);
@@ -981,6 +981,23 @@ class Chain : public ChainBase {
   // reads in their place; an insulator: `in` itself.
   const cplx<T>* metal_image(const cplx<T>* in, int nvec) {
     if (!metal_) return in;
+    if (split_) {   // over plane-wave chunks: U^H z, the coefficients qh Z, img = z - U (qh Z)
+      const int pq = hq_.npw_pad;
+      const long vq = (long)nks_ * nbnd_ * pq;
+      cudaMemcpyAsync(img_, in, nvec * vq * sizeof(cplx<T>), cudaMemcpyDeviceToDevice, st_);
+      const size_t sm_d = (size_t)(2 * nbnd_) * kTileP * sizeof(cplx<T>);
+      const size_t sm_a = (size_t)nbnd_ * (nbnd_ + kSub) * sizeof(cplx<T>);
+      std::string e;
+      if (set_smem(k_sp_dots<T>, sm_d, e) || set_smem(k_sp_apply<T>, sm_a, e)) return nullptr;
+      k_sp_dots<T><<<dim3(nks_, nvec, nchunk_), 256, sm_d, st_>>>(nks_, nbnd_, pq, dq_.npw, nchunk_, 0, in, in, ukq_,
+                                                                  bkq_, sp_c_, sp_s_);
+      k_sp_coef<T><<<nks_ * nvec, 256, 0, st_>>>(nks_, nbnd_, nchunk_, 0, dij_, ub_, sp_c_, sp_s_, sp_coef_, 3, md_,
+                                                 zp_, nullptr);
+      k_sp_apply<T><<<dim3(nks_, nvec, nchunk_), 256, sm_a, st_>>>(nks_, nbnd_, pq, dq_.npw, nchunk_, 0, nullptr,
+                                                                   img_, ukq_, bkq_, sp_coef_, nullptr);
+      prof_.count(LL_PROF_ZINV, 3);
+      return img_;
+    }
     k_metal_image<T><<<dim3(nks_, nvec), 128, 0, st_>>>(nks_, nbnd_, hq_.npw_pad, dq_.npw, ukq_, in, img_, zp_, md_);
     prof_.count(LL_PROF_ZINV);
     return img_;
@@ -1006,7 +1023,7 @@ class Chain : public ChainBase {
       prof_.span(LL_PROF_XY2, e3, e2);
     }
     if ((rc = launch_zfwd_proj(nvec, in, out, err))) return rc;
-    prof_.count(LL_PROF_ZFWD, split_ ? 4 : 1);
+    prof_.count(LL_PROF_ZFWD, split_ ? 4 + (metal_ ? 1 : 0) : 1);
     prof_.span(LL_PROF_ZFWD, e2, prof_.mark(st_));
     return LL_OK;
   }
@@ -1098,6 +1115,7 @@ class Chain : public ChainBase {
   template <int N>
   int zfwd_split_n(int nvec, const cplx<T>* in, cplx<T>* out, std::string& err) {
     const int pq = hq_.npw_pad;
+    if (metal_) in = img_;   // a metal: the kinetic, KB and norm terms act on the image Q z
     const int lines = (nbnd_ * hq_.ncol_max + kLines - 1) / kLines;
     k_sp_zfwd<T, N><<<dim3(nks_, nvec, lines), kLines, 0, st_>>>(dq_, nbnd_, cbuf_, cb_ncol_, in, kin_, eps_, out);
     const size_t sm_d = (size_t)(std::max(nproj_, nbnd_) + nbnd_) * kTileP * sizeof(cplx<T>);
@@ -1113,13 +1131,15 @@ class Chain : public ChainBase {
       k_sp_dots<T><<<dim3(nks_, nvec, nchunk_), 256, sm_d, st_>>>(nks_, nbnd_, pq, dq_.npw, nchunk_, nproj_, in, out,
                                                                   ukq_, bkq_, sp_c_, sp_s_);
     }
-    k_sp_coef<T><<<nks_ * nvec, 256, sm_c, st_>>>(nks_, nbnd_, nchunk_, nproj_, dij_, ub_, sp_c_, sp_s_, sp_coef_);
+    k_sp_coef<T><<<nks_ * nvec, 256, sm_c, st_>>>(nks_, nbnd_, nchunk_, nproj_, dij_, ub_, sp_c_, sp_s_, sp_coef_,
+                                                  metal_ ? 1 : 0, md_, zp_, mcorr_);
     if (tc_ap_) {
       if ((rc = tc_apply(nvec, nproj_, in, out, part_, err))) return rc;
     } else {
       k_sp_apply<T><<<dim3(nks_, nvec, nchunk_), 256, sm_a, st_>>>(nks_, nbnd_, pq, dq_.npw, nchunk_, nproj_, in,
                                                                    out, ukq_, bkq_, sp_coef_, part_);
     }
+    if (metal_) k_sp_addcorr<<<1, 256, 0, st_>>>(nvec * nks_, nchunk_, mcorr_, part_);
     LL_CK(cudaGetLastError());
     return LL_OK;
   }
@@ -1137,14 +1157,17 @@ class Chain : public ChainBase {
     // then the axis-3 inverse FFTs over many CTAs per k
     const size_t sm_a = (size_t)nbnd_ * (nbnd_ + kSub) * sizeof(cplx<T>);
     if ((rc = set_smem(k_sp_apply<T>, sm_a, err))) return rc;
-    k_sp_coef<T><<<nks_, 256, 0, st_>>>(nks_, nbnd_, nchunk_, 0, dij_, ub_, sp_c_, sp_s_, sp_coef_);
+    k_sp_coef<T><<<nks_, 256, 0, st_>>>(nks_, nbnd_, nchunk_, 0, dij_, ub_, sp_c_, sp_s_, sp_coef_, metal_ ? 2 : 0,
+                                        md_);
     if (tc_ap_) {
       if ((rc = tc_apply(1, 0, nullptr, R(), nullptr, err))) return rc;
     } else {
       k_sp_apply<T><<<dim3(nks_, 1, nchunk_), 256, sm_a, st_>>>(nks_, nbnd_, pq, dq_.npw, nchunk_, 0, nullptr, R(),
                                                                 ukq_, bkq_, sp_coef_, nullptr);
     }
-    k_zinv<T, N><<<dim3(nks_, 1, zsplit()), 128, 0, st_>>>(dq_, R(), nbnd_, cbuf_, cb_ncol_);
+    const cplx<T>* rin = metal_image(R(), 1);
+    if (!rin) { err = "metal image launch"; return LL_ECUDA; }
+    k_zinv<T, N><<<dim3(nks_, 1, zsplit()), 128, 0, st_>>>(dq_, rin, nbnd_, cbuf_, cb_ncol_);
     LL_CK(cudaGetLastError());
     return LL_OK;
   }
@@ -1564,6 +1587,7 @@ class Chain : public ChainBase {
   MetalDev md_{nullptr, nullptr, nullptr, nullptr};
   cplx<T>* img_ = nullptr;                       // the image Q z of the operator's input (a metal)
   cplx<double>* zp_ = nullptr;                   // Z = U^H z of that input, [nvec][nks][nbnd][nbnd]
+  double* mcorr_ = nullptr;                      // the metal's norm term per (vector, k), split path
   std::vector<int> sym_host_;                    // small group of Q on the grid, [nsym][9]
   int nsym_ = 1;
   int* sym_ = nullptr;

@@ -208,12 +208,20 @@ __global__ void __launch_bounds__(256) k_sp_dots(int nks, int nbnd, int npw_pad,
 
 // Operator, last stage: the coefficients of one (vector, k), reduced over the chunks in a fixed
 // order: c = D o (B^H x) (nproj x nbnd) and S = U^H t + (U^H B) c (nbnd x nbnd), rounded to T
-// into coef[kv] = [c | S].  ub: U^H B per k, [nbnd][nproj] (double).  grid nks * nvec, block 256.
+// into coef[kv] = [c | S].  ub: U^H B per k, [nbnd][nproj] (double).  A metal (MetalDev,
+// kernels.cuh) turns S into the coefficients of its projections: kind 1 (the operator) sp S - da
+// Z with Z = zp[kv] from the image, and mcorr[kv] = sum qh Re(conj(Z) (S - C)), the term that
+// makes the norm partial of the image Re(z, X); kind 2 (the update) keep S; kind 3 (the image
+// Q z, S = U^H z) qh S, with zp[kv] = S on the kept states.  kind 0: S itself.
+// grid nks * nvec, block 256.
 template <typename T>
 __global__ void __launch_bounds__(256) k_sp_coef(int nks, int nbnd, int nchunk, int nproj,
                                                  const double* __restrict__ dij, const cplx<double>* __restrict__ ub,
                                                  const cplx<double>* __restrict__ cpart,
-                                                 const cplx<double>* __restrict__ spart, cplx<T>* __restrict__ coef) {
+                                                 const cplx<double>* __restrict__ spart, cplx<T>* __restrict__ coef,
+                                                 int kind = 0, MetalDev md = MetalDev{nullptr, nullptr, nullptr, nullptr},
+                                                 cplx<double>* __restrict__ zp = nullptr,
+                                                 double* __restrict__ mcorr = nullptr) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx<double>* cd = reinterpret_cast<cplx<double>*>(smem_raw);   // [nproj * nbnd]
   const long kv = blockIdx.x;
@@ -230,6 +238,7 @@ __global__ void __launch_bounds__(256) k_sp_coef(int nks, int nbnd, int nchunk, 
     out[p] = mk((T)(re * m), (T)(im * m));
   }
   __syncthreads();
+  double corr = 0.0;
   for (int p = threadIdx.x; p < nbnd * nbnd; p += blockDim.x) {
     double re = 0.0, im = 0.0;
     for (int cc = 0; cc < nchunk; ++cc) {
@@ -242,8 +251,36 @@ __global__ void __launch_bounds__(256) k_sp_coef(int nks, int nbnd, int nchunk, 
       re += a.x * d.x - a.y * d.y;
       im += a.x * d.y + a.y * d.x;
     }
+    if (kind == 1) {
+      const long mi = ((long)k * nbnd + w) * nbnd + v;
+      const cplx<double> z = zp[kv * nbnd * nbnd + p];
+      const double cr = md.sp[mi] * re - md.da[mi] * z.x, ci = md.sp[mi] * im - md.da[mi] * z.y;
+      corr += md.qh[mi] * (z.x * (re - cr) + z.y * (im - ci));
+      re = cr;
+      im = ci;
+    } else if (kind == 2) {
+      const double kp = md.keep[((long)k * nbnd + w) * nbnd + v];
+      re *= kp;
+      im *= kp;
+    } else if (kind == 3) {
+      const long mi = ((long)k * nbnd + w) * nbnd + v;
+      const double kept = md.keep[mi] == 0.0 ? 1.0 : 0.0, q = md.qh[mi];
+      zp[kv * nbnd * nbnd + p] = mk(re * kept, im * kept);
+      re *= q;
+      im *= q;
+    }
     out[nproj * nbnd + p] = mk((T)re, (T)im);
   }
+  if (kind == 1) {
+    corr = block_sum(corr);
+    if (threadIdx.x == 0) mcorr[kv] = corr;
+  }
+}
+
+// A metal's term of the norm partial (k_sp_coef, kind 1) added to the first chunk's partial of
+// each (vector, k).  grid 1, block 256.
+static __global__ void k_sp_addcorr(int nkv, int nchunk, const double* __restrict__ mcorr, double* __restrict__ part) {
+  for (int kv = threadIdx.x; kv < nkv; kv += blockDim.x) part[(long)kv * nchunk] += mcorr[kv];
 }
 
 // Operator, last stage, applied: t <- t + B c - U S (= P_c (t + B c)) on one chunk of plane
@@ -405,7 +442,8 @@ __global__ void __launch_bounds__(256) k_sp_nh_proj(int nks, int nbnd, int npw_p
                                                     int nchunk, cplx<T>* __restrict__ XV, cplx<T>* __restrict__ XW,
                                                     const cplx<T>* __restrict__ ukq,
                                                     const cplx<double>* __restrict__ spart2,
-                                                    cplx<double>* __restrict__ spart) {
+                                                    cplx<double>* __restrict__ spart,
+                                                    const double* __restrict__ keep = nullptr) {
   __shared__ cplx<T> Sv[32 * 32], Sw[32 * 32];
   __shared__ double sred[2][8];
   const int k = blockIdx.x, c = blockIdx.y;
@@ -417,8 +455,9 @@ __global__ void __launch_bounds__(256) k_sp_nh_proj(int nks, int nbnd, int npw_p
       vr += q[p].x; vi += q[p].y;
       wr += q[nn + p].x; wi += q[nn + p].y;
     }
-    Sv[p] = mk((T)vr, (T)vi);
-    Sw[p] = mk((T)wr, (T)wi);
+    const double kp = keep ? keep[(long)k * nn + p] : 1.0;   // a metal: P'_v
+    Sv[p] = mk((T)(vr * kp), (T)(vi * kp));
+    Sw[p] = mk((T)(wr * kp), (T)(wi * kp));
   }
   __syncthreads();
   const int g0 = c * kChunk, g1 = min(npw_pad, g0 + kChunk), n = g1 - g0;

@@ -27,6 +27,7 @@ CASES = [
     ("kb_fp32", "kb", "fp32", "ph", 10, {}),
     ("metal_fp32_nh", "metal", "fp32", "nh", 20, {}),
     ("metal_fp64_ph", "metal", "fp64", "ph", 40, {}),
+    ("metal_split_fp32_nh", "metal", "fp32", "nh", 20, {"LL_SPLIT_PERK": "1"}),
 ]
 
 SCRIPT = r"""

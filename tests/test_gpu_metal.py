@@ -153,12 +153,30 @@ def test_full_occupations_match_the_insulator(lib):
         assert np.max(np.abs(np.asarray(a) - np.asarray(c))) <= 1e-12 * np.max(np.abs(c))
 
 
-def test_metal_on_the_split_path_is_refused(lib, metal, monkeypatch):
-    """Metals run on the fused per-k path only: a forced split path is refused at create."""
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+@pytest.mark.parametrize("upper", [False, True])
+def test_single_application_metal_split_path(lib, metal, precision, tol, upper, monkeypatch):
+    """The split per-k path (forced; the large cells' path, tensor-core projections in FP32)
+    with the metal's image and coefficients formed over plane-wave chunks."""
     monkeypatch.setenv("LL_SPLIT_PERK", "1")
-    with pytest.raises(lib.LLError) as e:
-        chain_from_bundle(metal, max_steps=4)
-    assert e.value.code == 9
+    sys = System(metal)
+    ch = chain_from_bundle(metal, precision=precision, max_steps=4)
+    x = _rand(sys, 33)
+    got = ch.apply(_to_z(metal, sys, x), upper)
+    want = _to_z(metal, sys, sys.apply_op(x, upper))
+    assert rel_batch(got, want) < tol
+
+
+@pytest.mark.parametrize("flavour", ["ph", "nh"])
+def test_metal_split_path_coefficients(lib, metal, flavour, monkeypatch):
+    """Split path: the first 100 FP64 coefficients (1e-10) and the FP32 loss function of the
+    first 80 (1e-3) against the oracle, both recursions."""
+    monkeypatch.setenv("LL_SPLIT_PERK", "1")
+    ref = _oracle(metal, flavour)
+    got = chain_from_bundle(metal, flavour=flavour, max_steps=120).lanczos(120)
+    assert _coef_rel(got, ref, 100) < 1e-10
+    got32 = chain_from_bundle(metal, flavour=flavour, precision="fp32", max_steps=120).lanczos(120)
+    assert _loss_err(got32, ref, metal, m=80) < 1e-3
 
 
 def test_metal_occupations_checked(lib, metal):
