@@ -104,7 +104,16 @@ struct XYArgs {
   FastDiv f_pervec;            // orbital -> vector: o / (nks nbnd)
 };
 
-template <typename T, int N, int MODE>
+// Output pruning of the forward line transforms: with PR > 0 every sphere of the system has
+// |m| <= PR on all three axes, so only the points p <= PR and p >= N - PR of a forward line
+// are kept; with the stores of the other points gone at compile time, the compiler drops
+// the butterflies that only feed them.  PR = 0: every point.
+template <int N, int PR>
+__device__ __forceinline__ constexpr bool line_kept(int p) {
+  return PR == 0 || p <= PR || p >= N - PR;
+}
+
+template <typename T, int N, int MODE, int PR = 0>
 __global__ void __launch_bounds__(128, N > 36 ? 2 : (MODE == XY_PASS1_DENS ? 3 : 4)) k_xy(XYArgs a, cplx<T>* __restrict__ cbuf, const T* __restrict__ vloc,
                                                const cplx<T>* __restrict__ vpr, const cplx<T>* __restrict__ ur,
                                                cplx<T>* __restrict__ nprt, cplx<T>* __restrict__ grid_out) {
@@ -220,7 +229,7 @@ __global__ void __launch_bounds__(128, N > 36 ? 2 : (MODE == XY_PASS1_DENS ? 3 :
 #pragma unroll
       for (int p = 0; p < N; ++p) {
         const int r = wrapn<N>(p - m2min);
-        if (r < nr && LL_INB(r < s.nrow_max)) Ys[(b * s.nrow_max + r) * NP + j1] = l[p];
+        if (line_kept<N, PR>(p) && r < nr && LL_INB(r < s.nrow_max)) Ys[(b * s.nrow_max + r) * NP + j1] = l[p];
       }
     }
     __syncthreads();
@@ -240,7 +249,7 @@ __global__ void __launch_bounds__(128, N > 36 ? 2 : (MODE == XY_PASS1_DENS ? 3 :
 #pragma unroll
       for (int p = 0; p < N; ++p) {
         const int j = wrapn<N>(p - rw.z);
-        if (j < rw.w && LL_INB(rw.y >= 0 && rw.y + j < a.cb_ncol)) cs[j] = l[p];
+        if (line_kept<N, PR>(p) && j < rw.w && LL_INB(rw.y >= 0 && rw.y + j < a.cb_ncol)) cs[j] = l[p];
       }
     }
     __syncthreads();
@@ -724,7 +733,7 @@ static __device__ __noinline__ double metal_operator_coefs(const MetalDev md, in
 // (a metal: x is the image Q z, zp holds Z = U^H z per vector; the output is the operator
 // on z through the MetalDev tables, and the partial Re(z^H X)).
 // grid (nks, nvec, ngrp), block 256.  smem: x, t [bpc][npw_pad]; coefficients; scratch.
-template <typename T, int N>
+template <typename T, int N, int PR = 0>
 __global__ void __launch_bounds__(256, 2) k_zfwd_proj(SphereDev s, int nbnd, int bpc, const cplx<T>* __restrict__ cbuf,
                                                    int cb_ncol, const cplx<T>* __restrict__ xin,
                                                    const T* __restrict__ kin, const double* __restrict__ eps,
@@ -771,7 +780,7 @@ __global__ void __launch_bounds__(256, 2) k_zfwd_proj(SphereDev s, int nbnd, int
 #pragma unroll
     for (int p = 0; p < N; ++p) {
       const int i = wrapn<N>(p - cl.z);
-      if (i < cl.w && LL_INB(st >= 0 && st + i < npw_pad)) dst[i] = dst[i] + a[p] * scale;
+      if (line_kept<N, PR>(p) && i < cl.w && LL_INB(st >= 0 && st + i < npw_pad)) dst[i] = dst[i] + a[p] * scale;
     }
   }
   __syncthreads();

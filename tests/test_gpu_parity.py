@@ -382,3 +382,21 @@ def test_lane_pair_plane_pass_kb(lib, kb, precision, tol, monkeypatch):
     x = _rand(sys, 15)
     for upper in (False, True):
         assert rel_batch(ch.apply(x, upper), sys.apply_op(x, upper)) < tol
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_pruned_forward_lines_bit_identical(lib, kb, precision, monkeypatch):
+    """The forward line transforms pruned to the spheres' extent (|m| <= N/4: the points a
+    sphere keeps) give the unpruned kernels' results bit for bit: only transforms of points no
+    sphere keeps are dropped."""
+    sys = System(kb, "tddft")
+    x = _rand(sys, 14)
+    got = {}
+    for prune in ("1", "0"):
+        monkeypatch.setenv("LL_PRUNE", prune)
+        ch = chain_from_bundle(kb, precision=precision, max_steps=4)
+        got[prune] = (ch.apply(x, True), ch.apply(x, False))
+        ch.close()
+    for a, b in zip(got["1"], got["0"]):
+        for ak, bk in zip(a, b):
+            assert np.array_equal(ak, bk)
