@@ -140,6 +140,89 @@ __device__ __forceinline__ void fft_line(cplx<T> (&a)[N]) {
   }
 }
 
+// Input pruning.  A point p of a line whose sphere keeps only |m| <= PR (p <= PR or p >= N - PR)
+// is zero on input; the first pass knows these zeros at compile time (a value with a constant
+// flag) and skips every add whose operand is such a zero.  The arithmetic on the other values
+// is the dense pass's, operation for operation, so the result equals fft_line's (up to the
+// sign of exact zeros).
+template <typename T>
+struct ZC {
+  cplx<T> v;
+  bool z;   // known zero (compile time once inlined)
+};
+template <typename T>
+__device__ __forceinline__ ZC<T> zadd(ZC<T> a, ZC<T> b) {
+  if (a.z) return b;
+  if (b.z) return a;
+  return {a.v + b.v, false};
+}
+template <typename T>
+__device__ __forceinline__ ZC<T> zsub(ZC<T> a, ZC<T> b) {
+  if (b.z) return a;
+  if (a.z) return {mk(-b.v.x, -b.v.y), false};
+  return {a.v - b.v, false};
+}
+
+template <typename T, int R, int SIGN> struct ZDft;
+template <typename T, int SIGN> struct ZDft<T, 2, SIGN> {
+  static __device__ __forceinline__ void run(ZC<T>* v) {
+    const ZC<T> a = v[0], b = v[1];
+    v[0] = zadd(a, b);
+    v[1] = zsub(a, b);
+  }
+};
+template <typename T, int SIGN> struct ZDft<T, 4, SIGN> {
+  static __device__ __forceinline__ void run(ZC<T>* v) {
+    const ZC<T> a0 = zadd(v[0], v[2]), a1 = zsub(v[0], v[2]);
+    const ZC<T> b0 = zadd(v[1], v[3]), b1 = zsub(v[1], v[3]);
+    const ZC<T> jb1 = {(SIGN > 0) ? mk(-b1.v.y, b1.v.x) : mk(b1.v.y, -b1.v.x), b1.z};
+    v[0] = zadd(a0, b0);
+    v[2] = zsub(a0, b0);
+    v[1] = zadd(a1, jb1);
+    v[3] = zsub(a1, jb1);
+  }
+};
+template <typename T, int SIGN> struct ZDft<T, 3, SIGN> {   // all zero, or the dense DFT
+  static __device__ __forceinline__ void run(ZC<T>* v) {
+    if (v[0].z && v[1].z && v[2].z) return;
+    cplx<T> d[3] = {v[0].z ? czero<T>() : v[0].v, v[1].z ? czero<T>() : v[1].v, v[2].z ? czero<T>() : v[2].v};
+    Dft<T, 3, SIGN>::run(d);
+    for (int r = 0; r < 3; ++r) v[r] = {d[r], false};
+  }
+};
+
+// fft_line<T, N, SIGN> of a line that is zero outside |m| <= PR (PR = 0: fft_line itself).
+template <typename T, int N, int SIGN, int PR>
+__device__ __forceinline__ void fft_line_in(cplx<T> (&a)[N]) {
+  if constexpr (PR == 0) {
+    fft_line<T, N, SIGN>(a);
+  } else {
+    constexpr int R0 = Plan<N>::r[0], R1 = Plan<N>::r[1], R2 = Plan<N>::r[2];
+    cplx<T> b[N];
+#pragma unroll
+    for (int j = 0; j < N / R0; ++j) {   // first Stockham pass (Ns = 1: no twiddles)
+      ZC<T> v[R0];
+#pragma unroll
+      for (int r = 0; r < R0; ++r) {
+        const int i = j + r * (N / R0);
+        const bool kept = i <= PR || i >= N - PR;
+        v[r] = {kept ? a[i] : czero<T>(), !kept};
+      }
+      ZDft<T, R0, SIGN>::run(v);
+#pragma unroll
+      for (int r = 0; r < R0; ++r) b[j * R0 + r] = v[r].z ? czero<T>() : v[r].v;
+    }
+    if constexpr (Plan<N>::n == 2) {
+      stockham_pass<T, N, R1, R0, SIGN>(b, a);
+    } else {
+      stockham_pass<T, N, R1, R0, SIGN>(b, a);
+      stockham_pass<T, N, R2, R0 * R1, SIGN>(a, b);
+#pragma unroll
+      for (int i = 0; i < N; ++i) a[i] = b[i];
+    }
+  }
+}
+
 // A 2H-point FFT split over a lane pair (lanes l and l ^ 1 of a warp, h = l & 1), each lane
 // holding H points, with one radix-2 step exchanged through warp shuffles (mask: the pair).
 //   fft_pair_dit: in  a[m] = x[2m + h]    out a[k] = X[H h + k]   (decimation in time)

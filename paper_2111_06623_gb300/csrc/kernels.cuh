@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(128, N > 36 ? 2 : (MODE == XY_PASS1_DENS ? 3 :
           const int j = wrapn<N>(p - rw.z);
           l[p] = (j < rw.w && LL_INB(rw.y >= 0 && rw.y + j < a.cb_ncol)) ? cs[j] : czero<T>();
         }
-        fft_line<T, N, +1>(l);
+        fft_line_in<T, N, +1, (MODE == XY_STORE ? 0 : PR)>(l);
         cplx<T>* ys = Ys + (b * s.nrow_max + r) * NP;
 #pragma unroll
         for (int p = 0; p < N; ++p) ys[p] = l[p];
@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(128, N > 36 ? 2 : (MODE == XY_PASS1_DENS ? 3 :
           const int r = wrapn<N>(p - m2min);
           l[p] = (r < nr && LL_INB(r < s.nrow_max)) ? Ys[(b * s.nrow_max + r) * NP + j1] : czero<T>();
         }
-        fft_line<T, N, +1>(l);
+        fft_line_in<T, N, +1, (MODE == XY_STORE ? 0 : PR)>(l);
         if (MODE == XY_STORE) {
           cplx<T>* dst = grid_out + (long)o * N * plane + iz * plane + j1;
 #pragma unroll

@@ -386,9 +386,9 @@ def test_lane_pair_plane_pass_kb(lib, kb, precision, tol, monkeypatch):
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_pruned_forward_lines_bit_identical(lib, kb, precision, monkeypatch):
-    """The forward line transforms pruned to the spheres' extent (|m| <= N/4: the points a
-    sphere keeps) give the unpruned kernels' results bit for bit: only transforms of points no
-    sphere keeps are dropped."""
+    """The line transforms pruned to the spheres' extent (|m| <= N/4: forward lines keep only
+    the points a sphere keeps, inverse lines skip the adds of the zero inputs outside it) give
+    the unpruned kernels' results bit for bit."""
     sys = System(kb, "tddft")
     x = _rand(sys, 14)
     got = {}
