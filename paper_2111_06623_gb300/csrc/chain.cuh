@@ -346,15 +346,18 @@ class Chain : public ChainBase {
     if (!build_sphere(nks_, d->npw_kq, d->miller_kq, n, hq_, err)) return LL_EINVAL;
     for (int k = 0; k < nks_; ++k)
       if (d->npw_kq[k] < nbnd_ + 1) { err = "sphere smaller than the occupied manifold"; return LL_EINVAL; }
-    {   // the largest |m| of the k+Q spheres on any axis: the forward lines keep |m| <= N/4 only
+    {   // the largest |m| of the k+Q spheres on any axis picks the pruning bound of the lines:
+        // the tightest built level (tight_prune(N), then N/4) that holds every sphere
       int pmax = 0;
       for (int k = 0; k < nks_; ++k)
         for (int c = 0; c < hq_.ncol[k]; ++c) {
           const int4 cl = hq_.col[(size_t)k * hq_.ncol_max + c];
           pmax = std::max({pmax, std::abs(cl.x), std::abs(cl.y), std::abs(cl.z), std::abs(cl.z + cl.w - 1)});
         }
-      const char* pe = getenv("LL_PRUNE");   // 0: every forward line transform unpruned
-      prune_ = pmax <= n / 4 && !(pe && pe[0] == '0' && pe[1] == 0);
+      const char* pe = getenv("LL_PRUNE");   // 0: unpruned lines; 1: the N/4 level only
+      const bool off = pe && pe[0] == '0' && pe[1] == 0, wide = pe && pe[0] == '1' && pe[1] == 0;
+      const int tight = tight_prune(n);
+      prune_ = off ? 0 : (!wide && tight > 0 && pmax <= tight) ? tight : (pmax <= n / 4 ? n / 4 : 0);
     }
     if (!inputs_finite(d, err, false)) return LL_EINVAL;
     if (d->where != LL_WHERE_HOST && d->where != LL_WHERE_DEVICE) { err = "bad where"; return LL_EINVAL; }
@@ -1049,7 +1052,10 @@ class Chain : public ChainBase {
     const size_t smem = 2 * (size_t)bpc_ * hq_.npw_pad * sizeof(cplx<T>) +
                         (size_t)std::max(nproj_, nbnd_) * bpc_ * sizeof(cplx<double>) + red_bytes(256);
     int rc;
-    auto kern = prune_ ? k_zfwd_proj<T, N, N / 4> : k_zfwd_proj<T, N>;
+    auto kern = k_zfwd_proj<T, N>;
+    if constexpr (tight_prune(N) > 0)
+      if (prune_ == tight_prune(N)) kern = k_zfwd_proj<T, N, tight_prune(N)>;
+    if (prune_ == N / 4) kern = k_zfwd_proj<T, N, N / 4>;
     if ((rc = set_smem(kern, smem, err))) return rc;
     kern<<<dim3(nks_, nvec, ngrp_), 256, smem, st_>>>(dq_, nbnd_, bpc_, cbuf_, cb_ncol_,
                                                                     metal_ ? img_ : in, kin_, eps_, ukq_, bkq_,
@@ -1258,8 +1264,11 @@ class Chain : public ChainBase {
       const bool pair = xy_pair_ >= 0 ? xy_pair_ == 1 : (c.var >= 0 ? c.var == 1 : N == 48);
       if (pair) return xy_launch<N, MODE>(k_xyp<T, N, MODE>, 4 * N, 2, c.bo, s, norb, o_off, dens_vec, err);
     }
-    if constexpr (MODE != XY_STORE) {   // forward lines pruned to the spheres' extent
-      if (prune_) return xy_launch<N, MODE>(k_xy<T, N, MODE, N / 4>, 128, 128 / N, c.bo, s, norb, o_off, dens_vec, err);
+    if constexpr (MODE != XY_STORE) {   // lines pruned to the spheres' extent
+      if constexpr (tight_prune(N) > 0)
+        if (prune_ == tight_prune(N))
+          return xy_launch<N, MODE>(k_xy<T, N, MODE, tight_prune(N)>, 128, 128 / N, c.bo, s, norb, o_off, dens_vec, err);
+      if (prune_ == N / 4) return xy_launch<N, MODE>(k_xy<T, N, MODE, N / 4>, 128, 128 / N, c.bo, s, norb, o_off, dens_vec, err);
     }
     return xy_launch<N, MODE>(k_xy<T, N, MODE>, 128, 128 / N, c.bo, s, norb, o_off, dens_vec, err);
   }
@@ -1622,7 +1631,7 @@ class Chain : public ChainBase {
   bool split_ = false;      // per-k work split over chunks of plane waves (split.cuh)
   int xy_occ_reg_[4] = {0, 0, 0, 0};   // CTAs per SM the plane pass's registers allow, per mode
   int xy_pair_ = -1;                   // LL_XY_PAIR: 1 lane pairs for every even N, 0 never, -1 not forced
-  bool prune_ = false;                 // forward line transforms pruned to |m| <= N/4 (LL_PRUNE=0: never)
+  int prune_ = 0;                      // line transforms pruned to |m| <= prune_ (0: unpruned)
   struct XyChoice { int var; int bo; };    // plane-pass kernel (0 k_xy, 1 k_xyp) and orbital batch
   XyChoice xy_choice_[4] = {{-1, 0}, {-1, 0}, {-1, 0}, {-1, 0}};   // per mode; -1 / 0: the untuned default
   bool tc_op_ = false, tc_u_ = false, tc_u2_ = false;   // split-path dot blocks on the tensor cores

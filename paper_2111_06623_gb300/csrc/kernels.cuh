@@ -104,6 +104,10 @@ struct XYArgs {
   FastDiv f_pervec;            // orbital -> vector: o / (nks nbnd)
 };
 
+// The pruning bounds built besides N/4: 3N/16 at N = 32 (the spheres of a 25 Ry cutoff on the
+// two-atom cell reach |m| = 6), none elsewhere.
+__host__ __device__ constexpr int tight_prune(int n) { return n == 32 ? 3 * n / 16 : 0; }
+
 // Output pruning of the forward line transforms: with PR > 0 every sphere of the system has
 // |m| <= PR on all three axes, so only the points p <= PR and p >= N - PR of a forward line
 // are kept; with the stores of the other points gone at compile time, the compiler drops

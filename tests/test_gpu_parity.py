@@ -386,13 +386,17 @@ def test_lane_pair_plane_pass_kb(lib, kb, precision, tol, monkeypatch):
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_pruned_forward_lines_bit_identical(lib, kb, precision, monkeypatch):
-    """The line transforms pruned to the spheres' extent (|m| <= N/4: forward lines keep only
-    the points a sphere keeps, inverse lines skip the adds of the zero inputs outside it) give
-    the unpruned kernels' results bit for bit."""
+    """The line transforms pruned to the spheres' extent (forward lines keep only the points a
+    sphere keeps, inverse lines skip the adds of the zero inputs outside it) against the
+    unpruned kernels.  At the N/4 bound (LL_PRUNE=1) the results are the same bit for bit.  At
+    the tighter 3N/16 bound (the default here: the KB spheres reach |m| = 6 at N = 32) more
+    butterflies are dropped and the compiled code of the remaining ones rounds differently at
+    a few points (measured on GB300 in FP64), so that level is held to the single-application
+    tolerance of the oracle parity tests instead."""
     sys = System(kb, "tddft")
     x = _rand(sys, 14)
     got = {}
-    for prune in ("1", "0"):
+    for prune in ("", "1", "0"):
         monkeypatch.setenv("LL_PRUNE", prune)
         ch = chain_from_bundle(kb, precision=precision, max_steps=4)
         got[prune] = (ch.apply(x, True), ch.apply(x, False))
@@ -400,3 +404,7 @@ def test_pruned_forward_lines_bit_identical(lib, kb, precision, monkeypatch):
     for a, b in zip(got["1"], got["0"]):
         for ak, bk in zip(a, b):
             assert np.array_equal(ak, bk)
+    tol = 1e-12 if precision == "fp64" else 2e-5
+    for a, b in zip(got[""], got["0"]):
+        for ak, bk in zip(a, b):
+            assert np.max(np.abs(ak - bk)) <= tol * np.max(np.abs(bk))
