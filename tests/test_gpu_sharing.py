@@ -24,10 +24,19 @@ def lib():
 
 
 def _at_q(q):
+    """The small cell's ground state at another Q: the k+Q states of that Q, and the ground
+    state's own k-side (k-points, V_KS, n0, sphere(k), u_k, eps_k) taken from the base bundle, as one
+    user holding one ground state does.  (A bundle at another Q built on another machine than
+    the base bundle has its k-side states from that machine's LAPACK, different in the last
+    bits, which the library rightly refuses to share.)"""
+    base = w.get_bundle(w.config_small())
     spec = w.config_small()
     spec.q_cart = np.asarray(q, dtype=np.float64) * (2 * np.pi / w.A_LAT)
     spec.name = "fcc2_10ry_18_q" + "_".join("%+.3f" % c for c in q)
-    return w.get_bundle(spec)
+    b = w.get_bundle(spec)
+    for name in ("kfrac", "kcart", "vloc_r", "rho_r", "miller_k", "u_k", "eps_k"):
+        setattr(b, name, getattr(base, name))
+    return b
 
 
 def _system(b, **kw):
