@@ -30,3 +30,10 @@ def test_whole_job_rate_counts_every_rank():
 def test_source_digest_is_stable():
     assert bench.source_digest() == bench.source_digest()
     assert len(bench.source_digest()) == 16
+
+
+def test_committed_traffic_matches_the_sources():
+    """The DRAM bytes per launch in profiles/roofline_traffic.txt were captured on the plane
+    pass as it is now: a change to its code without a new capture fails here."""
+    t = bench.profiled_traffic()
+    assert t is not None and 3e8 < t < 4e8
